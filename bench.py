@@ -1,0 +1,355 @@
+#!/usr/bin/env python
+"""Benchmark: 640x480 frame-to-keyframe alignments per second (plain FP32 path).
+
+Workload: the seeded synthetic 300-frame 640x480 room sequence (30 Hz, <= 0.5 m/s,
+<= 30 deg/s; fx = fy = 525, cx = 319.5, cy = 239.5), tracked frame to keyframe
+on a 4-level pyramid with [10, 5, 5, 5] Gauss-Newton iterations (coarsest
+first), every frame fused into the keyframe, keyframe switch every 20 frames.
+One step = one frame through the whole hot path: the frame's pyramid, the
+constant-velocity guess, the IRLS alignment (robust scale + fused sweep + solve
+per iteration), the keyframe fusion (or switch) and the keyframe pyramid.
+
+value      frames (= 640x480 alignments) per second over all ranks, inputs
+           resident in HBM, each step timed with CUDA events on the tracker's
+           stream; L2 is flushed (a 512 MiB write) between steps, outside the
+           timed intervals.
+e2e        the same with every step's frame copied from pinned host memory and
+           its result struct read back to pinned host memory inside the step.
+roofline   the sweep kernel (or the kernel named by --roofline-kernel) timed
+           live with CUDA events around its launches inside the timed steps;
+           achieved = 16 B x pixels per launch / launch time.
+
+Multi-GPU: every rank tracks its own independent sequence (seed = rank), no
+collective on the data path ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "640x480 alignments/s at <=1e-5 rad pose err vs plain GPU form; % HBM roofline"
+UNIT = "alignments/s"
+W, H = 640, 480
+LEVELS, ITERS = 4, (5, 5, 5, 10)
+KF_EVERY = 20
+N_FRAMES = 300
+BYTES_PER_PX_ITER = 16          # I_A, W_A, I_B, W_B in FP32, each read once
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=120)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--roofline-kernel", choices=["sweep", "robust"], default="sweep")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = max(smax, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- peaks
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------- CPU baseline
+CPU_SNIPPET = r"""
+import json, os, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+import oracle as O
+from paper_1807_08271_gb300 import synth
+seq = synth.render_sequence(0, n_frames={nf})
+t0 = time.perf_counter()
+r = O.track_sequence(seq["I"], seq["W"], seq["K"], levels={levels}, iters={iters}, kf_every={kf})
+dt = time.perf_counter() - t0
+print(json.dumps({{"frames": {nf} - 1, "seconds": dt}}))
+"""
+
+
+def run_oracle_sample(n_frames: int) -> dict:
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[k] = "1"
+    code = CPU_SNIPPET.format(root=ROOT, nf=n_frames, levels=LEVELS, iters=tuple(ITERS), kf=KF_EVERY)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, check=True)
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+# ----------------------------------------------------------------------------- reference arm
+def reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n_timed = max(1, min(args.steps, 24))
+    r = run_oracle_sample(n_timed + 1)
+    value = r["frames"] / r["seconds"]
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": r["frames"], "warmup": 0, "ms_per_step": 1000.0 * r["seconds"] / r["frames"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_dict("oracle frames 1..%d of the sequence" % r["frames"]),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"frames 1..{r['frames']} of the 300-frame sequence, one thread (numpy float64)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def config_dict(extra=None):
+    d = {"workload": "synthetic 640x480 room sequence, 300 frames at 30 Hz; frame-to-keyframe alignment on a "
+                     "4-level pyramid [10,5,5,5] iterations, fusion of every frame, keyframe every 20 frames",
+         "width": W, "height": H, "levels": LEVELS, "iters_fine_to_coarse": list(ITERS),
+         "frames": N_FRAMES, "keyframe_every": KF_EVERY, "precision": "plain FP32 planes",
+         "l2": "flushed between steps (512 MiB write), outside the timed intervals"}
+    if extra:
+        d["note"] = extra
+    return d
+
+
+# ----------------------------------------------------------------------------- native arm
+def native(args):
+    import numpy as np
+    import torch
+
+    from paper_1807_08271_gb300 import rgbid as R
+    from paper_1807_08271_gb300 import synth
+    from paper_1807_08271_gb300.tracker import Tracker
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    seq = synth.render_sequence(seed=rank, n_frames=N_FRAMES)
+    dev = torch.device("cuda", local)
+    I_all = torch.from_numpy(seq["I"]).to(dev)
+    W_all = torch.from_numpy(seq["W"]).to(dev)
+    K = seq["K"]
+    I_host = torch.from_numpy(seq["I"]).pin_memory()
+    W_host = torch.from_numpy(seq["W"]).pin_memory()
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+
+    kern = R.KERNEL_SWEEP if args.roofline_kernel == "sweep" else R.KERNEL_ROBUST
+    per_step_launches = sum(ITERS[:LEVELS])
+    timer = R.KernelTimer(kern, per_step_launches * args.steps + 8)
+    trk = Tracker(W, H, K, levels=LEVELS, iters=ITERS, kf_every=KF_EVERY, max_frames=N_FRAMES + 1, device=dev)
+
+    launches = {"n": 0}
+
+    def kernels_in_step(k):
+        # pyramid (levels) + predict + init + 2 per iteration + fuse, or switch (compose + init_kf) + kf pyramid
+        n = LEVELS + 1 + 1 + 2 * per_step_launches + LEVELS
+        n += 2 if k % KF_EVERY == 0 else 1
+        return n
+
+    state = {"frame": 0}
+
+    def next_frame():
+        """Frame index for the next step; a new pass restarts tracking at frame 0."""
+        if state["frame"] >= N_FRAMES:
+            state["frame"] = 0
+        if state["frame"] == 0:
+            trk.k = 0
+            with torch.cuda.stream(stream):
+                trk.step(I_all[0], W_all[0], stream)
+            state["frame"] = 1
+        k = state["frame"]
+        state["frame"] += 1
+        return k
+
+    def run_steps(n, timed, e2e=False, res_host=None):
+        evs = []
+        for _ in range(n):
+            k = next_frame()
+            with torch.cuda.stream(stream):
+                if timed:
+                    flush.fill_(rank & 0xff)
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                if e2e:
+                    Ik = torch.empty((H, W), dtype=torch.float32, device=dev)
+                    Wk = torch.empty((H, W), dtype=torch.float32, device=dev)
+                    Ik.copy_(I_host[k], non_blocking=True)
+                    Wk.copy_(W_host[k], non_blocking=True)
+                    trk.step(Ik, Wk, stream)
+                    res_host.copy_(trk.res[0], non_blocking=True)
+                else:
+                    trk.step(I_all[k], W_all[k], stream)
+                if timed:
+                    e1.record(stream)
+                    evs.append((e0, e1))
+                    launches["n"] += kernels_in_step(k)
+        return evs
+
+    # warm-up (also builds the library on first use)
+    run_steps(args.warmup, timed=False)
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region
+    timer.attach(trk.params)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    evs = run_steps(args.steps, timed=True)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    trk.params.timing = None
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = float(sum(step_ms))
+    kern_ms = timer.total_ms()
+    kern_units = int(timer.t.units)
+    kern_count = int(timer.t.count)
+    gpu_launches = launches["n"]
+
+    # ---- end-to-end through host buffers
+    res_host = torch.empty(R.RESULT_BYTES, dtype=torch.uint8).pin_memory()
+    run_steps(2, timed=False, e2e=True, res_host=res_host)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    evs2 = run_steps(args.steps, timed=True, e2e=True, res_host=res_host)
+    torch.cuda.synchronize()
+    e2e_ms = float(sum(a.elapsed_time(b) for a, b in evs2))
+
+    # pose sanity: frames of the last pass vs ground truth
+    traj = trk.trajectory()
+    n_ok = trk.k
+    E = [np.linalg.inv(seq["T_wc"][0] @ traj[i]) @ seq["T_wc"][i] for i in range(1, n_ok)]
+    rot = max(float(np.arccos(np.clip((np.trace(e[:3, :3]) - 1) / 2, -1, 1))) for e in E) if E else 0.0
+
+    t = torch.tensor([total_ms, e2e_ms, kern_ms], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms, e2e_ms, kern_ms = t.tolist()
+    if rank != 0:
+        dist.destroy_process_group()
+        return
+    value = world * args.steps / (total_ms / 1000.0)
+    e2e_val = world * args.steps / (e2e_ms / 1000.0)
+    peak, peak_kind = measured_peaks()
+    units_per_launch = kern_units / max(kern_count, 1)
+    if args.roofline_kernel == "sweep":
+        alg_bytes = BYTES_PER_PX_ITER * kern_units
+        achieved = alg_bytes / (kern_ms / 1000.0) / 1e9 if kern_ms > 0 else 0.0
+    else:
+        alg_bytes = BYTES_PER_PX_ITER * kern_units
+        achieved = alg_bytes / (kern_ms / 1000.0) / 1e9 if kern_ms > 0 else 0.0
+    roofline = {"bound": "hbm", "kernel": args.roofline_kernel + "_kernel", "achieved": achieved, "peak": peak,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak if peak else None,
+                "traffic": None, "launches": kern_count, "units_per_launch": units_per_launch,
+                "kernel_ms_per_step": kern_ms / args.steps, "share_of_step": kern_ms / total_ms if total_ms else None}
+    cpu = None
+    if not args.no_cpu_baseline:
+        r = run_oracle_sample(7)
+        cpu = {"value": r["frames"] / r["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"frames 1..{r['frames']} of the sequence (align + fuse), one thread, numpy float64"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config_dict(),
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 2 * W * H * 4,
+                "d2h_bytes_per_step": R.RESULT_BYTES},
+        "roofline": roofline, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": gpu_launches,
+        "wall_s_timed": t_wall, "max_rot_err_vs_truth_rad": rot,
+    }
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference(args)
+    else:
+        native(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,237 @@
+/*
+ * rgbid.h - C ABI of the GB300 (sm_103a) library for RGBiD-SLAM's dense
+ * frame-to-keyframe alignment in inverse-depth parametrisation and keyframe
+ * fusion (Gutierrez-Gomez & Guerrero, arXiv 1807.08271).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Notation is the paper's: A (the reference, normally the keyframe) and B
+ *    (the current frame); a pose T = A_T_B is a row-major 4x4 double matrix
+ *    that maps B's coordinates into A's (X_A = R X_B + t).
+ *  - Images are row-major.  I is intensity in [0, 1]; W is inverse depth in
+ *    1/m with W == 0 (or any W <= 0, or NaN) meaning "no measurement" (a hole).
+ *    `pitch` arguments count ELEMENTS per row (>= width).
+ *  - Ownership: the caller allocates and owns every buffer (planes, pyramid
+ *    storage, workspace, results).  The library keeps no global state and
+ *    never allocates device memory.
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *    default stream).  Every call only enqueues work on that stream and
+ *    returns; results are valid once the stream reaches that point.
+ *  - Errors: argument errors are reported synchronously as the return value
+ *    (nothing is enqueued).  A failed kernel launch returns RGBID_ERR_CUDA.
+ *    Numerical outcomes (degenerate steps) are written to the result struct's
+ *    `status` field on the device.  No C++ exception crosses this ABI.
+ *  - All device pointers must be 16-byte aligned.
+ */
+#ifndef RGBID_H
+#define RGBID_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RGBID_MAX_LEVELS 6
+#define RGBID_MAX_SAMPLES 19200   /* N of the paper's systematic sample ("Error distribution and robust optimisation") */
+
+typedef enum {
+    RGBID_OK = 0,
+    RGBID_ERR_INVALID_ARG = 1,
+    RGBID_ERR_CUDA = 2,
+    RGBID_ERR_WORKSPACE = 3,     /* workspace / storage too small or misaligned */
+    RGBID_ERR_DEGENERATE = 4,    /* device status: a step was skipped (too few residuals or H not SPD) */
+    RGBID_ERR_TIMEOUT = 5,       /* device status: a bounded device-side wait gave up */
+    RGBID_ERR_UNSUPPORTED = 6
+} rgbid_status;
+
+/* Pinhole intrinsics (level 0 unless stated). */
+typedef struct {
+    double fx, fy, cx, cy;
+} rgbid_intrinsics;
+
+/* Storage precision of pyramid levels. */
+typedef enum {
+    RGBID_PLANES_F32 = 0,        /* (float I, float W) pairs: 8 bytes per pixel */
+    RGBID_PLANES_BF16_F16 = 1    /* (bf16 I, fp16 W) pairs: 4 bytes per pixel */
+} rgbid_precision;
+
+/* One pyramid level: an interleaved (I, W) plane in device memory. */
+typedef struct {
+    int width, height;
+    int pitch;                   /* pixels per row */
+    int pad_;
+    rgbid_intrinsics K;          /* intrinsics at this level */
+    void* IW;                    /* device pointer, layout per rgbid_precision */
+} rgbid_level;
+
+/* Pyramid descriptor (host struct; the pixel data lives in caller storage). */
+typedef struct {
+    int levels;
+    int precision;               /* rgbid_precision */
+    rgbid_level lv[RGBID_MAX_LEVELS];   /* index 0 = finest */
+} rgbid_pyramid;
+
+/* Optional per-kernel timing of rgbid_align: the library records the caller's
+ * CUDA events (cudaEvent_t passed as void*) on the call's stream immediately
+ * before and after every launch of the selected kernel, appending after the
+ * `count` pairs already used (at most `capacity`), and adds the algorithmic
+ * units those launches process to `units` (pixels of the level for the sweep,
+ * systematic-sample pixels for the robust-scale kernel). */
+typedef enum {
+    RGBID_KERNEL_SWEEP = 0,      /* fused warp + residual + Jacobian + weight + reduce (+ solve) */
+    RGBID_KERNEL_ROBUST = 1      /* systematic sample + (mu, sigma, nu) */
+} rgbid_kernel_id;
+
+typedef struct {
+    void** ev_start;             /* cudaEvent_t[capacity] */
+    void** ev_end;               /* cudaEvent_t[capacity] */
+    int capacity;
+    int kernel;                  /* rgbid_kernel_id */
+    int count;                   /* in/out: event pairs used so far */
+    int pad_;
+    long long units;             /* in/out: algorithmic units of the timed launches */
+} rgbid_timing;
+
+/* Alignment schedule and robust-estimation constants. */
+typedef struct {
+    int levels;                  /* levels used, coarse to fine (<= pyramid levels) */
+    int iters[RGBID_MAX_LEVELS]; /* Gauss-Newton iterations per level, index 0 = finest */
+    int scale_iters;             /* fixed-point iterations for (mu, sigma); default 10 */
+    int bisect_steps;            /* bisection halvings for nu; default 20 */
+    int sample_cap;              /* systematic sample size cap, 1..RGBID_MAX_SAMPLES; default 19200 */
+    int estimate_nu;             /* 1: bisection for nu per channel; 0: nu = nu0 */
+    int min_valid;               /* minimum count of valid residuals (I and W together) for a step */
+    int pad_;
+    double nu0, nu_lo, nu_hi;    /* 5, 2, 10; needs (nu_lo + nu_hi) >= 1.4 (nu_hi - nu_lo) */
+    rgbid_timing* timing;        /* optional kernel timing (NULL: none) */
+} rgbid_align_params;
+
+/* Result of an alignment (or of one evaluated step).  Lives in device memory
+ * (or mapped pinned host memory) and is written by the device. */
+typedef struct {
+    double T[16];                /* final A_T_B (for rgbid_eval_step: the input pose) */
+    double H[36];                /* normal matrix of the last step (full, symmetric) */
+    double g[6];                 /* sum w J^T r(p,0) of the last step; the step solves H xi = -g */
+    double mu[2], sigma[2], nu[2];  /* robust parameters of the last step: [I, W] */
+    double cost;                 /* sum w r^2 of the last step */
+    int n_valid[2];              /* residuals that passed mask_I / mask_W in the last step */
+    int iters_done;
+    int iters_skipped;           /* steps skipped as degenerate */
+    int status;                  /* rgbid_status: RGBID_OK or RGBID_ERR_DEGENERATE */
+    int pad_;
+} rgbid_align_result;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char* rgbid_status_string(int status);
+
+/* Fill `p` with the defaults: 3 levels, iters {5, 5, 10} (finest first),
+ * 10 scale iterations, 20 bisection steps, sample cap 19200, nu estimated,
+ * nu0 = 5, nu in [2, 10], min_valid 60. */
+void rgbid_default_params(rgbid_align_params* p);
+
+/* ---------------------------------------------------------------- pyramid
+ * Image pyramid ("Dense motion estimation", "Iterative optimisation": the
+ * maps are downsampled at each level and their gradients taken there).
+ * Level l+1 is the 2x2 box mean of level l (odd sizes drop the last
+ * row/column); W averages only its valid children and is 0 if none; the
+ * intrinsics follow f <- f/2, c <- (c + 0.5)/2 - 0.5.  Gradients are not
+ * stored: the alignment takes central differences on the fly.
+ */
+
+/* Bytes of caller storage needed for a pyramid. */
+size_t rgbid_pyramid_bytes(int width, int height, int levels, int precision);
+
+/* Build a pyramid from planar float I0/W0 (device, `pitch0` elements per row)
+ * into `storage` (device, >= rgbid_pyramid_bytes, 256-byte aligned) and fill
+ * the host descriptor `out`.  Levels need width, height >= 4.
+ * Errors: INVALID_ARG (sizes, levels, NULL pointers), WORKSPACE (storage). */
+int rgbid_build_pyramid(const float* I0, const float* W0, int pitch0, int width, int height,
+                        rgbid_intrinsics K0, int levels, int precision,
+                        void* storage, size_t storage_bytes, rgbid_pyramid* out, void* stream);
+
+/* ---------------------------------------------------------------- alignment
+ * Coarse-to-fine IRLS Gauss-Newton alignment ("Dense motion estimation"):
+ * per iteration B is warped towards A with the current estimate (inverse
+ * geometric warping, eq. 3d_registration), the Student-t location, scale and
+ * robustness (mu, sigma, nu) of the photometric and inverse-depth residuals
+ * are estimated on the <= 19200-pixel systematic sample, every pixel's
+ * residuals (eqs. res_int, res_depth), Jacobians and weights (eq.
+ * minimisationIRLS with the normal weight lambda_n) are reduced into H xi = -g,
+ * and T <- exp(xi)^-1 T with the decoupled SE(3) exponential.
+ */
+
+/* Workspace bytes needed by rgbid_align / rgbid_eval_step for this reference. */
+size_t rgbid_align_workspace_bytes(const rgbid_pyramid* ref, const rgbid_align_params* params);
+
+/* Align `cur` (B) to `ref` (A).  Both pyramids must have the same size,
+ * precision and intrinsics.  `T_init` is 16 doubles (row-major A_T_B): a host
+ * pointer read during the call when `T_init_on_device` is 0, a device pointer
+ * read by the first kernel when it is 1, or NULL for the identity.
+ * `workspace` (device, >= rgbid_align_workspace_bytes, 256-byte aligned) is
+ * scratch for the duration of the call.  `d_result` is device memory written
+ * by the device; on a degenerate step the pose is kept, iters_skipped grows
+ * and status becomes RGBID_ERR_DEGENERATE.  Calls sharing a workspace must
+ * not overlap on the device. */
+int rgbid_align(const rgbid_pyramid* ref, const rgbid_pyramid* cur,
+                const double* T_init, int T_init_on_device,
+                const rgbid_align_params* params, void* workspace, size_t workspace_bytes,
+                rgbid_align_result* d_result, void* stream);
+
+/* One step at a fixed pose and level, for inspection and parity testing.
+ * `T` (host, 16 doubles) is the pose; `robust` (host, 6 doubles
+ * mu_I, sigma_I, nu_I, mu_W, sigma_W, nu_W) fixes the robust parameters, or
+ * NULL estimates them on the sample as rgbid_align does.  Optional device
+ * outputs of width*height elements of that level (row-major, pitch = width):
+ * r_I, r_W (residuals r(p, 0), 0 where masked out), mask_I, mask_W (0/1).
+ * `d_result` receives H, g, cost, n_valid and the robust parameters used;
+ * its pose is `T` and no update is applied. */
+int rgbid_eval_step(const rgbid_pyramid* ref, const rgbid_pyramid* cur, int level,
+                    const double* T, const double* robust, const rgbid_align_params* params,
+                    void* workspace, size_t workspace_bytes,
+                    float* r_I, float* r_W, uint8_t* mask_I, uint8_t* mask_W,
+                    rgbid_align_result* d_result, void* stream);
+
+/* ---------------------------------------------------------------- fusion
+ * Keyframe fusion ("Keyframe fusion", section "RGB-ID SLAM system"): every
+ * keyframe pixel with W_kf > 0 is warped into frame k with T_kf_k = kf_T_k
+ * (inverse geometric warping); where the four bilinear taps of W_k are valid,
+ * both depths are positive and |W_k(p_k) - w_k| < 3 sigma_W (the visibility
+ * test of "Dense frame covisibility ratio"), W_kf <- (W_kf C_kf + C_k W_k*) /
+ * (C_kf + C_k) and C_kf <- C_kf + C_k, with W_k^* the transferred inverse depth
+ * and C_k = (d W_k^* / d W_k(p_k))^-2.  With `fuse_intensity` the intensity is
+ * averaged with the same weights.  Planes are float, updated in place.
+ * `T_kf_k` (16 doubles) and `sigma_W` (1 double) are host pointers read during
+ * the call when `params_on_device` is 0, or device pointers read by the kernel
+ * when it is 1 (e.g. &d_result->T and &d_result->sigma[1] of the alignment).
+ */
+int rgbid_fuse_keyframe(float* I_kf, float* W_kf, float* C_kf, int pitch_kf,
+                        const float* I_k, const float* W_k, int pitch_k,
+                        int width, int height, rgbid_intrinsics K,
+                        const double* T_kf_k, const double* sigma_W, int params_on_device,
+                        int fuse_intensity, void* stream);
+
+/* Initialise a keyframe from a frame: I_kf = I_k, W_kf = W_k, C_kf = 1. */
+int rgbid_init_keyframe(float* I_kf, float* W_kf, float* C_kf, int pitch_kf,
+                        const float* I_k, const float* W_k, int pitch_k,
+                        int width, int height, void* stream);
+
+/* ---------------------------------------------------------------- tracking helper
+ * Constant-velocity initial guess of the tracking front-end ("Camera
+ * tracking"): rf_T_k(0) = rf_T_{k-1} (rf_T_{k-2})^-1 rf_T_{k-1}, computed on the
+ * device so that a sequence can be enqueued without host round trips.
+ * All three pointers are device arrays of 16 doubles; `T_km2` may equal
+ * `T_km1` (no motion model yet). */
+int rgbid_predict_pose(const double* T_km1, const double* T_km2, double* T_out, void* stream);
+
+/* Pose composition on the device: T_out = A^-1 B when `invert_A` is 1, else
+ * A B (rigid transforms; the inverse is [R^T, -R^T t]).  Device arrays of 16
+ * doubles; T_out may alias B but not A. */
+int rgbid_compose_pose(const double* A, int invert_A, const double* B, double* T_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RGBID_H */

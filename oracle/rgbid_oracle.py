@@ -490,3 +490,49 @@ def fuse(I_kf, W_kf, C_kf, I_k, W_k, K, T, sigma_W: float, fuse_intensity: bool 
     C_new = np.where(gate, denom, C_kf)
     return I_new, W_new, C_new, gate
 
+
+
+# ----------------------------------------------------------------------------- tracking front-end
+def track_sequence(I_frames, W_frames, K, levels: int = 4, iters=(5, 5, 5, 10), kf_every: int = 20,
+                   fuse_intensity: bool = True, n_frames: int | None = None):
+    """Frame-to-keyframe tracking with fusion ("Camera tracking", "Keyframe fusion").
+
+    Frame 0 initialises the keyframe (C_kf = 1).  Frame k is aligned to the
+    keyframe from the constant-velocity guess kf_T_k(0) = kf_T_{k-1} (kf_T_{k-2})^-1
+    kf_T_{k-1}; every ``kf_every`` frames the aligned frame becomes the new
+    keyframe (reading R15), otherwise it is fused into the keyframe with the
+    final sigma_W of its alignment (reading R14).  Returns dict(T_world [n,4,4]
+    camera-to-world with frame 0 at the identity, results (per-frame align
+    dicts), keyframe=(I, W, C) at the end)."""
+    P = AlignParams(levels=levels, iters=tuple(iters))
+    n = len(I_frames) if n_frames is None else n_frames
+    I_kf = np.asarray(I_frames[0], dtype=np.float64).copy()
+    W_kf = np.asarray(W_frames[0], dtype=np.float64).copy()
+    C_kf = np.ones_like(W_kf)
+    kfp = build_pyramid(I_kf, W_kf, K, levels)
+    T1 = np.eye(4)
+    T2 = np.eye(4)
+    T_wkf = np.eye(4)
+    T_world = [np.eye(4)]
+    results = []
+    for k in range(1, n):
+        cur = build_pyramid(I_frames[k], W_frames[k], K, levels)
+        T_init = T1 @ se3_inv(T2) @ T1
+        r = align(kfp, cur, T_init, P)
+        results.append(r)
+        Tk = r["T"]
+        T_world.append(T_wkf @ Tk)
+        if k % kf_every == 0:
+            T2 = se3_inv(Tk) @ T1
+            T1 = np.eye(4)
+            T_wkf = T_wkf @ Tk
+            I_kf = np.asarray(I_frames[k], dtype=np.float64).copy()
+            W_kf = np.asarray(W_frames[k], dtype=np.float64).copy()
+            C_kf = np.ones_like(W_kf)
+        else:
+            I_kf, W_kf, C_kf, _ = fuse(I_kf, W_kf, C_kf, I_frames[k], W_frames[k], K, Tk, r["robust"]["sigma"][1],
+                                       fuse_intensity)
+            T2 = T1
+            T1 = Tk
+        kfp = build_pyramid(I_kf, W_kf, K, levels)
+    return dict(T_world=np.stack(T_world), results=results, keyframe=(I_kf, W_kf, C_kf))

@@ -1,0 +1,849 @@
+// Dense IRLS alignment kernels and the rgbid_align / rgbid_eval_step entry points.
+//
+// Per Gauss-Newton iteration two kernels run on the caller's stream:
+//   robust_kernel  one thread-block cluster: warps the <= 19200 systematic
+//                  sample pixels with the current pose, then estimates the
+//                  Student-t (mu, sigma) at nu0 by the lagged-weight fixed
+//                  point and nu by bisection on the robustness equation, with
+//                  every reduction done across the cluster through distributed
+//                  shared memory ("Error distribution and robust optimisation").
+//   sweep_kernel   the whole level: warp, residuals, Jacobians, weights and the
+//                  per-block reduction of the 27 normal-equation terms (plus
+//                  cost and counts); the last block to finish sums the block
+//                  partials in a fixed order (compensated FP32), solves
+//                  H xi = -g by a Jacobi-scaled Cholesky and applies
+//                  T <- exp(xi)^-1 T to the FP64 pose ("Iterative optimisation").
+#include <cooperative_groups.h>
+#include <cstdio>
+#include <cstring>
+
+#include "rgbid_device.cuh"
+#include "rgbid_util.h"
+
+namespace cg = cooperative_groups;
+
+namespace rgbid {
+
+constexpr int kRobustNT = 256;      // threads per CTA of the robust-scale cluster
+constexpr int kRobustMaxNV = 96;    // widest cluster reduction (the Chebyshev sums of both channels)
+constexpr int kSweepNT = 256;       // 8 warps
+constexpr int kSweepRowsPerWarp = 4;
+constexpr int kTileW = 32;
+constexpr int kTileH = 8 * kSweepRowsPerWarp;
+
+struct InitArgs {
+    AlignState* st;
+    rgbid_align_result* res;
+    const double* T_dev;     // device pose or null
+    double T_val[16];        // host pose (used when T_dev is null)
+    int use_fixed;
+    float fixed[6];          // mu_I, sigma_I, nu_I, mu_W, sigma_W, nu_W
+};
+
+struct RobustArgs {
+    LevelDev A, B;
+    AlignState* st;
+    int s, nsx, nsamp;
+    int scale_iters, bisect_steps, estimate_nu;
+    float nu0;
+    double nu_lo, nu_hi;
+};
+
+struct SweepArgs {
+    LevelDev A, B;
+    AlignState* st;
+    float* partials;
+    rgbid_align_result* res;
+    int update;
+    int min_valid;
+    float* r_I;
+    float* r_W;
+    uint8_t* m_I;
+    uint8_t* m_W;
+};
+
+// ---------------------------------------------------------------- init
+__global__ void init_kernel(InitArgs a) {
+    AlignState* st = a.st;
+    __shared__ double T[16];
+    if (threadIdx.x < 16) {
+        T[threadIdx.x] = a.T_dev ? a.T_dev[threadIdx.x] : a.T_val[threadIdx.x];
+        st->T[threadIdx.x] = T[threadIdx.x];
+        a.res->T[threadIdx.x] = T[threadIdx.x];
+    }
+    __syncwarp();
+    warp_make_pose(T, &st->wp);
+    if (threadIdx.x != 0) return;
+    st->counter = 0u;
+    st->status = RGBID_OK;
+    st->iters_done = 0;
+    st->iters_skipped = 0;
+    st->timeouts = 0;
+    if (a.use_fixed) {
+        for (int c = 0; c < 2; ++c) {
+            st->rob.mu[c] = a.fixed[3 * c + 0];
+            st->rob.sigma[c] = a.fixed[3 * c + 1];
+            st->rob.nu[c] = a.fixed[3 * c + 2];
+            st->rob.ok[c] = a.fixed[3 * c + 1] >= 1e-12f;
+        }
+    }
+    rgbid_align_result* r = a.res;
+    for (int i = 0; i < 36; ++i) r->H[i] = 0.0;
+    for (int i = 0; i < 6; ++i) r->g[i] = 0.0;
+    for (int c = 0; c < 2; ++c) { r->mu[c] = 0.0; r->sigma[c] = 0.0; r->nu[c] = 0.0; r->n_valid[c] = 0; }
+    r->cost = 0.0;
+    r->iters_done = 0;
+    r->iters_skipped = 0;
+    r->status = RGBID_OK;
+}
+
+// ---------------------------------------------------------------- robust scale (cluster)
+// All cluster-wide sums use the same fixed combine tree (warp butterfly, then
+// a shuffle tree over the 8 warps of a CTA, then a shuffle tree over the CTAs
+// of the cluster with compensated (TwoSum) pairs), so every thread of every
+// CTA sees bit-identical totals and takes identical branches.
+
+__device__ __forceinline__ F2 shfl_f2(const F2& v, int off) {
+    return F2{__shfl_xor_sync(0xffffffffu, v.hi, off), __shfl_xor_sync(0xffffffffu, v.lo, off)};
+}
+
+template <int CL>
+struct ClusterSum {
+    float (*red_w)[kRobustMaxNV];     // per-warp partials [8][NV]
+    float2 (*red_cta)[kRobustMaxNV];  // per-CTA compensated partials, double-buffered [2][NV]
+    float* out;                       // [NV] cluster totals
+    int buf;
+
+    // v: per-thread partials of NV values (NV <= 8: one per warp-sum; NV = 96: three
+    // reduce-scatter chunks).  On return out[0..NV) holds the cluster totals.
+    template <int NV>
+    __device__ __forceinline__ void run(cg::cluster_group& cl, float (&v)[NV]) {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        if constexpr (NV <= 8) {
+#pragma unroll
+            for (int j = 0; j < NV; ++j) {
+                const float x = warp_sum(v[j]);
+                if (lane == 0) red_w[warp][j] = x;
+            }
+        } else {
+            static_assert(NV % 32 == 0, "chunks of 32");
+#pragma unroll
+            for (int c = 0; c < NV / 32; ++c) {
+                float chunk[32];
+#pragma unroll
+                for (int i = 0; i < 32; ++i) chunk[i] = v[c * 32 + i];
+                red_w[warp][c * 32 + lane] = warp_reduce_scatter32(chunk);
+            }
+        }
+        __syncthreads();
+        // CTA level: warp w combines values j = w, w + 8, ... over the 8 warps (lanes 0..7)
+        for (int j = warp; j < NV; j += kRobustNT / 32) {
+            F2 t{lane < kRobustNT / 32 ? red_w[lane & 7][j] : 0.f, 0.f};
+#pragma unroll
+            for (int off = 1; off < kRobustNT / 32; off <<= 1) t.add(shfl_f2(t, off));
+            if (lane == 0) red_cta[buf][j] = make_float2(t.hi, t.lo);
+        }
+        cl.sync();
+        // cluster level: lane r < CL reads CTA r's pair; a shuffle tree combines them
+        for (int j = warp; j < NV; j += kRobustNT / 32) {
+            F2 t{0.f, 0.f};
+            if (lane < CL) {
+                const float2* rem = cl.map_shared_rank(&red_cta[buf][0], lane);
+                const float2 p = rem[j];
+                t = F2{p.x, p.y};
+            }
+#pragma unroll
+            for (int off = 1; off < CL; off <<= 1) t.add(shfl_f2(t, off));
+            if (lane == 0) out[j] = t.value();
+        }
+        __syncthreads();
+        buf ^= 1;
+    }
+};
+
+// c(nu) = -psi(nu/2) + ln(nu/2) + psi((nu+1)/2) - ln((nu+1)/2) + 1 (eq. robustnessValue),
+// written as D(nu) + 1 - ln(1 + 1/nu) with D(nu) = psi(y + 1/2) - psi(y), y = nu/2.
+// D uses the recurrence psi(z) = psi(z + 1) - 1/z six times (each difference
+// 1/(y+j) - 1/(y+j+1/2) = 0.5/((y+j)(y+j+1/2)) taken in product form) and the
+// asymptotic series of psi (Abramowitz & Stegun 6.3.5, 6.3.18) for the
+// difference at z = y + 6, so no term cancels in FP32.
+__device__ __forceinline__ float nu_const_f(float nu) {
+    const float y = 0.5f * nu;
+    float acc = 0.f;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        const float z = y + (float)j;
+        acc += __fdividef(0.5f, z * (z + 0.5f));
+    }
+    const float z = y + 6.f, zh = z + 0.5f;
+    const float iz2 = __fdividef(1.f, z * z), ih2 = __fdividef(1.f, zh * zh);
+    // psi(zh) - psi(z) = ln(zh/z) - 1/(2 zh) + 1/(2 z) - sum_k B_2k/(2k) (zh^-2k - z^-2k)
+    auto tail = [](float i2) {
+        return i2 * (1.f / 12.f - i2 * (1.f / 120.f - i2 * (1.f / 252.f - i2 * (1.f / 240.f))));
+    };
+    const float asym = log1pf(__fdividef(0.5f, z)) + __fdividef(0.25f, z * zh) - (tail(ih2) - tail(iz2));
+    return (asym + acc) + 1.f - log1pf(__fdividef(1.f, nu));
+}
+
+// Chebyshev form of the sample sums of eq. robustnessValue.  With
+// nu = m + h tau (tau in [-1, 1] over [nu_lo, nu_hi]) and alpha_i = (m + x_i^2)/h > 1:
+//   ln(nu + x_i^2)  = ln h + ln(beta_i/2) + 2 sum_k (-1)^(k+1) q_i^k / k T_k(tau)
+//   1/(nu + x_i^2)  = (gamma_i / h) (1 + 2 sum_k (-1)^k q_i^k T_k(tau))
+// with beta = alpha + sqrt(alpha^2 - 1), q = 1/beta, gamma = 1/sqrt(alpha^2 - 1)
+// (the classical expansions of ln(alpha + tau) and 1/(alpha + tau)).  One cluster
+// reduction of the power sums P_k = sum q^k, G_k = sum gamma q^k and sum ln(beta/2)
+// then gives f(nu) at any nu without revisiting the samples; truncating at K
+// terms errs by < q_max^(K+1) per sample (q_max = 0.382 for [2, 10], K = 20).
+constexpr int kChebK = 20;
+constexpr int kChebVals = 2 * kChebK + 2;      // SL, P_1..P_K, G_0..G_K per channel
+
+struct ChebSums {
+    float n, SL, P[kChebK + 1], G[kChebK + 1];   // P[0] unused
+};
+
+// f(nu) from the Chebyshev sums (FP32, Clenshaw).
+__device__ __forceinline__ float nu_equation_cheb(const ChebSums& S, float nu, float m, float h) {
+    const float tau = (nu - m) / h;
+    const float t2 = 2.f * tau;
+    // A(tau) = sum_k a_k T_k, a_k = 2 (-1)^(k+1) P_k / k ; B(tau) = G_0 + sum_k b_k T_k, b_k = 2 (-1)^k G_k
+    float a1 = 0.f, a2 = 0.f, b1 = 0.f, b2 = 0.f;
+#pragma unroll
+    for (int k = kChebK; k >= 1; --k) {
+        const float sgn = (k & 1) ? 1.f : -1.f;
+        const float ak = sgn * 2.f * S.P[k] / (float)k;
+        const float bk = -sgn * 2.f * S.G[k];
+        const float an = fmaf(t2, a1, ak - a2);
+        const float bn = fmaf(t2, b1, bk - b2);
+        a2 = a1; a1 = an;
+        b2 = b1; b1 = bn;
+    }
+    const float A = fmaf(tau, a1, -a2);            // Clenshaw end with c_0 = 0
+    const float B = fmaf(tau, b1, S.G[0] - b2);
+    // f = n [c(nu) + ln(nu + 1) - ln h] - SL - A - (nu + 1) B / h
+    const float base = S.n * (nu_const_f(nu) + logf(nu + 1.f) - logf(h)) - S.SL;
+    return base - A - (nu + 1.f) * B / h;
+}
+
+template <int PREC, int CL>
+__global__ void __launch_bounds__(kRobustNT) robust_kernel(RobustArgs a) {
+    constexpr int MAXS = (RGBID_MAX_SAMPLES + CL * kRobustNT - 1) / (CL * kRobustNT);
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    __shared__ float red_w[kRobustNT / 32][kRobustMaxNV];
+    __shared__ float2 red_cta[2][kRobustMaxNV];
+    __shared__ float tot[kRobustMaxNV];
+    __shared__ WarpPose sh_wp;
+    __shared__ float nu_out[2];
+    if (threadIdx.x == 0) sh_wp = a.st->wp;
+    __syncthreads();
+    const WarpPose wp = sh_wp;
+
+    // ---- systematic sample residuals r(p, 0) (NaN = masked out)
+    float rs[2][MAXS];
+    const int gt = rank * kRobustNT + (int)threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < MAXS; ++k) {
+        const int i = gt + k * (CL * kRobustNT);
+        rs[0][k] = __int_as_float(0x7fc00000);
+        rs[1][k] = __int_as_float(0x7fc00000);
+        if (i < a.nsamp) {
+            const int sy = i / a.nsx, sx = i - sy * a.nsx;
+            PixelTerms o;
+            eval_pixel<PREC, false>(a.A, a.B, wp, sx * a.s, sy * a.s, o);
+            if (o.mI) rs[0][k] = o.rI;
+            if (o.mW) rs[1][k] = o.rW;
+        }
+    }
+
+    ClusterSum<CL> R{red_w, red_cta, tot, 0};
+    // ---- counts and mean square -> sigma0 (mu0 = 0)
+    {
+        float v4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k < MAXS; ++k) {
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const float r = rs[c][k];
+                if (r == r) { v4[2 * c] += 1.f; v4[2 * c + 1] = fmaf(r, r, v4[2 * c + 1]); }
+            }
+        }
+        R.run(cl, v4);
+    }
+    const float n[2] = {tot[0], tot[2]};
+    float mu[2] = {0.f, 0.f};
+    float sig[2];
+    bool live[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        sig[c] = n[c] > 0.f ? sqrtf(tot[2 * c + 1] / n[c]) : 0.f;
+        live[c] = n[c] > 0.f && sig[c] >= 1e-12f;
+    }
+
+    // ---- (mu, sigma) fixed point at nu0 with lagged weights:
+    //      mu <- sum w r / sum w ; sigma^2 <- sum w (r - mu_new)^2 / n, with d = r - mu_old
+    //      sum w (r - mu_new)^2 = S2 - S1^2 / S0.
+    const float nu0 = a.nu0;
+    for (int it = 0; it < a.scale_iters; ++it) {
+        if (!live[0] && !live[1]) break;
+        float v6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const float m = mu[c];
+            const float s2 = sig[c] * sig[c];
+            const float s2nu = s2 * nu0;
+            const float num = (nu0 + 1.f) * s2;
+#pragma unroll
+            for (int k = 0; k < MAXS; ++k) {
+                const float r = rs[c][k];
+                if (r == r) {
+                    const float d = r - m;
+                    const float w = __fdividef(num, fmaf(d, d, s2nu));   // omega((r - mu)/sigma, nu0)
+                    v6[3 * c] += w;
+                    v6[3 * c + 1] = fmaf(w, d, v6[3 * c + 1]);
+                    v6[3 * c + 2] = fmaf(w * d, d, v6[3 * c + 2]);
+                }
+            }
+        }
+        R.run(cl, v6);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            if (!live[c]) continue;
+            const float S0 = tot[3 * c], S1 = tot[3 * c + 1], S2 = tot[3 * c + 2];
+            const float delta = S1 / S0;
+            mu[c] += delta;
+            const float var = fmaf(-S1, delta, S2) / n[c];
+            sig[c] = var > 0.f ? sqrtf(var) : 0.f;
+            if (!(sig[c] >= 1e-12f)) live[c] = false;
+        }
+    }
+    bool ok[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) ok[c] = n[c] > 0.f && sig[c] >= 1e-12f;
+
+    // ---- nu by bisection on eq. robustnessValue, f(nu) = n c(nu) + sum_i (ln w_i - w_i)
+    float nu[2] = {nu0, nu0};
+    const bool do_nu = a.estimate_nu && (ok[0] || ok[1]);
+    const float lo0 = (float)a.nu_lo, hi0 = (float)a.nu_hi;
+    const float m = 0.5f * (lo0 + hi0), h = 0.5f * (hi0 - lo0);
+    if (do_nu) {
+        float v[96];
+#pragma unroll
+        for (int i = 0; i < 96; ++i) v[i] = 0.f;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            if (!ok[c]) continue;
+            const float is = 1.f / sig[c];
+#pragma unroll
+            for (int k = 0; k < MAXS; ++k) {
+                const float x = (rs[c][k] - mu[c]) * is;
+                if (x == x) {
+                    const float al = __fdividef(fmaf(x, x, m), h);
+                    const float s2 = fmaf(al, al, -1.f);
+                    const float gam = rsqrtf(s2);
+                    const float be = fmaf(s2, gam, al);
+                    const float q = __fdividef(1.f, be);
+                    float* V = v + c * kChebVals;
+                    V[0] += logf(0.5f * be);
+                    V[1 + kChebK] += gam;              // G_0
+                    float qk = q;
+#pragma unroll
+                    for (int kk = 1; kk <= kChebK; ++kk) {
+                        V[kk] += qk;                   // P_k
+                        V[1 + kChebK + kk] = fmaf(gam, qk, V[1 + kChebK + kk]);   // G_k
+                        qk *= q;
+                    }
+                }
+            }
+        }
+        R.run(cl, v);
+    }
+    cl.sync();   // every remote read of this CTA's shared memory is complete
+    if (rank != 0) return;
+
+    if (do_nu && threadIdx.x < 64) {
+        // warp c solves channel c: endpoint tests, then 31-point sections that
+        // replay 5 bisection halvings each (same midpoints, same decisions)
+        const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        float nuc = nu0;
+        if (ok[c]) {
+            ChebSums S;
+            S.n = n[c];
+            S.SL = tot[c * kChebVals];
+            S.P[0] = 0.f;
+#pragma unroll
+            for (int k = 1; k <= kChebK; ++k) S.P[k] = tot[c * kChebVals + k];
+#pragma unroll
+            for (int k = 0; k <= kChebK; ++k) S.G[k] = tot[c * kChebVals + 1 + kChebK + k];
+            const float fend = nu_equation_cheb(S, lane == 0 ? hi0 : lo0, m, h);
+            const float fhi = __shfl_sync(0xffffffffu, fend, 0);
+            const float flo = __shfl_sync(0xffffffffu, fend, 1);
+            if (fhi >= 0.f) {
+                nuc = hi0;
+            } else if (flo <= 0.f) {
+                nuc = lo0;
+            } else {
+                float lo = lo0, hi = hi0;
+                int left = a.bisect_steps;
+                while (left > 0) {
+                    const int st = left < 5 ? left : 5;
+                    const int np = 1 << st;             // sub-intervals this round
+                    const float step = (hi - lo) / (float)np;
+                    const float xj = fmaf((float)(lane + 1), step, lo);
+                    const float fj = (lane + 1 < np) ? nu_equation_cheb(S, xj, m, h) : 0.f;
+                    const unsigned pos = __ballot_sync(0xffffffffu, (lane + 1 < np) && fj > 0.f);
+                    int jl = 0, jh = np;
+                    for (int s = 0; s < st; ++s) {
+                        const int jm = (jl + jh) >> 1;
+                        if ((pos >> (jm - 1)) & 1u) jl = jm; else jh = jm;
+                    }
+                    const float nlo = fmaf((float)jl, step, lo), nhi = fmaf((float)jh, step, lo);
+                    lo = nlo;
+                    hi = nhi;
+                    left -= st;
+                }
+                nuc = 0.5f * (lo + hi);
+            }
+        }
+        if (lane == 0) nu_out[c] = nuc;
+    }
+    __syncthreads();
+    if (do_nu) {
+        nu[0] = nu_out[0];
+        nu[1] = nu_out[1];
+        if (ok[0] && ok[1]) nu[0] = fmaxf(nu[0], nu[1]);
+    }
+    if (threadIdx.x == 0) {
+        RobustParams& rp = a.st->rob;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            rp.mu[c] = mu[c];
+            rp.sigma[c] = sig[c];
+            rp.nu[c] = nu[c];
+            rp.ok[c] = ok[c] ? 1 : 0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- sweep + solve
+__device__ __forceinline__ void accumulate(float (&acc)[kSlots], const float (&J)[6], float w, float r) {
+    float wj[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) wj[i] = w * J[i];
+    int s = 0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+#pragma unroll
+        for (int j = i; j < 6; ++j) { acc[s] = fmaf(wj[i], J[j], acc[s]); ++s; }
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) acc[kSlotG + i] = fmaf(wj[i], r, acc[kSlotG + i]);
+    acc[kSlotCost] = fmaf(w * r, r, acc[kSlotCost]);
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(kSweepNT) sweep_kernel(SweepArgs a) {
+    __shared__ float red[kSweepNT / 32][kSlots];
+    __shared__ F2 fin[kSweepNT / 32][kSlots];
+    __shared__ float tot[kSlots];
+    __shared__ bool am_last;
+    __shared__ WarpPose sh_wp;
+    __shared__ RobustParams sh_rob;
+    if (threadIdx.x == 0) { sh_wp = a.st->wp; sh_rob = a.st->rob; }
+    __syncthreads();
+    const WarpPose wp = sh_wp;
+    const RobustParams rob = sh_rob;
+
+    float acc[kSlots];
+#pragma unroll
+    for (int i = 0; i < kSlots; ++i) acc[i] = 0.f;
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int u = blockIdx.x * kTileW + lane;
+    const bool wantI = rob.ok[0] != 0, wantW = rob.ok[1] != 0;
+#pragma unroll 1
+    for (int r = 0; r < kSweepRowsPerWarp; ++r) {
+        const int v = blockIdx.y * kTileH + warp * kSweepRowsPerWarp + r;
+        if (u >= a.A.w || v >= a.A.h) continue;
+        PixelTerms o;
+        eval_pixel<PREC, true>(a.A, a.B, wp, u, v, o);
+        if (a.r_I) {
+            const int oi = v * a.A.w + u;
+            a.r_I[oi] = o.mI ? o.rI : 0.f;
+            a.r_W[oi] = o.mW ? o.rW : 0.f;
+            a.m_I[oi] = o.mI ? 1 : 0;
+            a.m_W[oi] = o.mW ? 1 : 0;
+        }
+        if (o.mI) {
+            acc[kSlotNI] += 1.f;
+            if (wantI) accumulate(acc, o.JI, robust_weight(o.rI, rob.mu[0], rob.sigma[0], rob.nu[0]), o.rI);
+        }
+        if (o.mW) {
+            acc[kSlotNW] += 1.f;
+            if (wantW) accumulate(acc, o.JW, o.lam * robust_weight(o.rW, rob.mu[1], rob.sigma[1], rob.nu[1]), o.rW);
+        }
+    }
+
+    // block reduction: warp reduce-scatter, then warp 0 sums the 8 warps
+    const float mine = warp_reduce_scatter32(acc);
+    red[warp][lane] = mine;
+    __syncthreads();
+    const int nblocks = gridDim.x * gridDim.y;
+    const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+    if (warp == 0) {
+        float s = 0.f;
+#pragma unroll
+        for (int w = 0; w < kSweepNT / 32; ++w) s += red[w][lane];
+        a.partials[(size_t)bid * kSlots + lane] = s;
+        __threadfence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned ticket = atomicAdd(&a.st->counter, 1u);
+        am_last = (ticket == (unsigned)(nblocks - 1));
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+
+    // ---- last block: fixed-order compensated sum of the block partials
+    {
+        // warp w sums blocks w, w + 8, ...; loads are issued in batches of 24 so
+        // that their L2 latencies overlap
+        constexpr int kBatch = 24;
+        constexpr int kStride = kSweepNT / 32;
+        F2 acc2{0.f, 0.f};
+        for (int b0 = warp; b0 < nblocks; b0 += kBatch * kStride) {
+            float vals[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                const int b = b0 + u * kStride;
+                vals[u] = b < nblocks ? __ldcg(a.partials + (size_t)b * kSlots + lane) : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) acc2.add(vals[u]);
+        }
+        fin[warp][lane] = acc2;
+    }
+    __syncthreads();
+    if (warp != 0) return;
+    F2 t2{0.f, 0.f};
+#pragma unroll
+    for (int w = 0; w < kSweepNT / 32; ++w) t2.add(fin[w][lane]);
+    const float totf = t2.value();
+    tot[lane] = totf;
+    AlignState* st = a.st;
+    rgbid_align_result* res = a.res;
+    // results (double) written by the lanes in parallel
+    {
+        const double td = (double)t2.hi + (double)t2.lo;
+        if (lane < 21) {
+            int i = 0, rem = lane;
+            while (rem >= 6 - i) { rem -= 6 - i; ++i; }
+            const int j = i + rem;
+            res->H[i * 6 + j] = td;
+            res->H[j * 6 + i] = td;
+        } else if (lane < 27) {
+            res->g[lane - kSlotG] = td;
+        } else if (lane == kSlotCost) {
+            res->cost = td;
+        } else if (lane == kSlotNI) {
+            res->n_valid[0] = (int)totf;
+        } else if (lane == kSlotNW) {
+            res->n_valid[1] = (int)totf;
+        } else if (lane == 30) {
+            res->mu[0] = st->rob.mu[0]; res->mu[1] = st->rob.mu[1];
+            res->sigma[0] = st->rob.sigma[0]; res->sigma[1] = st->rob.sigma[1];
+            res->nu[0] = st->rob.nu[0]; res->nu[1] = st->rob.nu[1];
+        }
+    }
+    __syncwarp();
+    if (lane == 0) st->counter = 0u;
+    if (!a.update) return;
+    __shared__ float xi_sh[6];
+    __shared__ int ok_sh;
+    if (lane == 0) {
+        float H[36], rhs[6], xi[6];
+        int s = 0;
+        for (int i = 0; i < 6; ++i)
+            for (int j = i; j < 6; ++j) { H[i * 6 + j] = tot[s]; H[j * 6 + i] = tot[s]; ++s; }
+        for (int i = 0; i < 6; ++i) rhs[i] = -tot[kSlotG + i];
+        const int nI = (int)tot[kSlotNI], nW = (int)tot[kSlotNW];
+        bool ok = (nI + nW) >= a.min_valid && cholesky_solve6_f(H, rhs, xi);
+        for (int i = 0; i < 6; ++i) xi_sh[i] = ok ? xi[i] : 0.f;
+        ok_sh = ok ? 1 : 0;
+    }
+    __syncwarp();
+    const bool ok = ok_sh != 0;
+    if (ok) {
+        float xi[6];
+        for (int i = 0; i < 6; ++i) xi[i] = xi_sh[i];
+        warp_apply_update(xi, st->T);
+        warp_make_pose(st->T, &st->wp);
+    }
+    __syncwarp();
+    if (lane < 16) res->T[lane] = st->T[lane];
+    if (lane == 0) {
+        if (!ok) {
+            st->iters_skipped += 1;
+            st->status = RGBID_ERR_DEGENERATE;
+        }
+        st->iters_done += 1;
+        res->iters_done = st->iters_done;
+        res->iters_skipped = st->iters_skipped;
+        res->status = st->status;
+    }
+}
+
+// ---------------------------------------------------------------- host side
+static LevelDev level_dev(const rgbid_level& L) {
+    LevelDev d;
+    d.IW = L.IW;
+    d.w = L.width;
+    d.h = L.height;
+    d.pitch = L.pitch;
+    d.pad = 0;
+    d.fx = (float)L.K.fx;
+    d.fy = (float)L.K.fy;
+    d.cx = (float)L.K.cx;
+    d.cy = (float)L.K.cy;
+    d.ifx = (float)(1.0 / L.K.fx);
+    d.ify = (float)(1.0 / L.K.fy);
+    return d;
+}
+
+static int sample_stride(int w, int h, int cap) {
+    int s = 1;
+    while ((long long)((w + s - 1) / s) * ((h + s - 1) / s) > cap) ++s;
+    return s;
+}
+
+static int sweep_blocks(int w, int h) { return ((w + kTileW - 1) / kTileW) * ((h + kTileH - 1) / kTileH); }
+
+static size_t workspace_bytes_for(int w0, int h0) {
+    return align_up(sizeof(AlignState), 256) + align_up((size_t)sweep_blocks(w0, h0) * kSlots * sizeof(float), 256);
+}
+
+static int check_pyramids(const rgbid_pyramid* ref, const rgbid_pyramid* cur, const rgbid_align_params* p) {
+    if (!ref || !cur || !p) return RGBID_ERR_INVALID_ARG;
+    if (ref->levels < 1 || ref->levels > RGBID_MAX_LEVELS || cur->levels < ref->levels) return RGBID_ERR_INVALID_ARG;
+    if (p->levels < 1 || p->levels > ref->levels) return RGBID_ERR_INVALID_ARG;
+    if (ref->precision != cur->precision) return RGBID_ERR_INVALID_ARG;
+    if (ref->precision != RGBID_PLANES_F32 && ref->precision != RGBID_PLANES_BF16_F16) return RGBID_ERR_UNSUPPORTED;
+    if (p->sample_cap < 1 || p->sample_cap > RGBID_MAX_SAMPLES) return RGBID_ERR_INVALID_ARG;
+    if (p->scale_iters < 0 || p->bisect_steps < 0 || p->bisect_steps > 60) return RGBID_ERR_INVALID_ARG;
+    if (!(p->nu_lo > 0.0) || !(p->nu_hi > p->nu_lo) || !(p->nu0 > 0.0)) return RGBID_ERR_INVALID_ARG;
+    // the Chebyshev form of the robustness equation needs alpha_min = (lo + hi)/(hi - lo) >= 1.4
+    if (p->nu_lo + p->nu_hi < 1.4 * (p->nu_hi - p->nu_lo)) return RGBID_ERR_UNSUPPORTED;
+    for (int l = 0; l < p->levels; ++l) {
+        const rgbid_level& a = ref->lv[l];
+        const rgbid_level& b = cur->lv[l];
+        if (p->iters[l] < 0) return RGBID_ERR_INVALID_ARG;
+        if (!a.IW || !b.IW) return RGBID_ERR_INVALID_ARG;
+        if (a.width != b.width || a.height != b.height || a.width < 4 || a.height < 4) return RGBID_ERR_INVALID_ARG;
+        if (a.pitch < a.width || b.pitch < b.width) return RGBID_ERR_INVALID_ARG;
+        if (a.K.fx != b.K.fx || a.K.fy != b.K.fy || a.K.cx != b.K.cx || a.K.cy != b.K.cy) return RGBID_ERR_INVALID_ARG;
+        if (!(a.K.fx > 0.0) || !(a.K.fy > 0.0)) return RGBID_ERR_INVALID_ARG;
+    }
+    return RGBID_OK;
+}
+
+template <int PREC, int CL>
+static cudaError_t launch_robust_cl(const RobustArgs& ra, cudaStream_t stream) {
+    if (CL > 8) {
+        cudaError_t e = cudaFuncSetAttribute(robust_kernel<PREC, CL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CL, 1, 1);
+    cfg.blockDim = dim3(kRobustNT, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, robust_kernel<PREC, CL>, ra);
+}
+
+// 16-CTA clusters (non-portable) where the device can schedule them, else 8.
+// The answer is a fixed property of the device, cached per device ordinal.
+template <int PREC>
+static cudaError_t launch_robust(const RobustArgs& ra, cudaStream_t stream) {
+    static int cached[64];     // 0 = unknown, 8 or 16
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int cl = (dev >= 0 && dev < 64) ? cached[dev] : 0;
+    if (cl == 0) {
+        cl = 8;
+        if (cudaFuncSetAttribute(robust_kernel<PREC, 16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+            cudaSuccess) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(16, 1, 1);
+            cfg.blockDim = dim3(kRobustNT, 1, 1);
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = 16;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            int nclusters = 0;
+            if (cudaOccupancyMaxActiveClusters(&nclusters, robust_kernel<PREC, 16>, &cfg) == cudaSuccess &&
+                nclusters > 0)
+                cl = 16;
+        }
+        (void)cudaGetLastError();
+        if (dev >= 0 && dev < 64) cached[dev] = cl;
+    }
+    return cl == 16 ? launch_robust_cl<PREC, 16>(ra, stream) : launch_robust_cl<PREC, 8>(ra, stream);
+}
+
+template <int PREC>
+static cudaError_t launch_sweep(const SweepArgs& sa, cudaStream_t stream) {
+    dim3 grid((sa.A.w + kTileW - 1) / kTileW, (sa.A.h + kTileH - 1) / kTileH);
+    sweep_kernel<PREC><<<grid, kSweepNT, 0, stream>>>(sa);
+    return cudaGetLastError();
+}
+
+static cudaError_t launch_robust_any(int prec, const RobustArgs& ra, cudaStream_t s) {
+    return prec == RGBID_PLANES_F32 ? launch_robust<RGBID_PLANES_F32>(ra, s) : launch_robust<RGBID_PLANES_BF16_F16>(ra, s);
+}
+static cudaError_t launch_sweep_any(int prec, const SweepArgs& sa, cudaStream_t s) {
+    return prec == RGBID_PLANES_F32 ? launch_sweep<RGBID_PLANES_F32>(sa, s) : launch_sweep<RGBID_PLANES_BF16_F16>(sa, s);
+}
+
+static RobustArgs robust_args(const rgbid_pyramid* ref, const rgbid_pyramid* cur, int l, const rgbid_align_params* p,
+                              AlignState* st) {
+    RobustArgs ra;
+    ra.A = level_dev(ref->lv[l]);
+    ra.B = level_dev(cur->lv[l]);
+    ra.st = st;
+    ra.s = sample_stride(ra.A.w, ra.A.h, p->sample_cap);
+    ra.nsx = (ra.A.w + ra.s - 1) / ra.s;
+    ra.nsamp = ra.nsx * ((ra.A.h + ra.s - 1) / ra.s);
+    ra.scale_iters = p->scale_iters;
+    ra.bisect_steps = p->bisect_steps;
+    ra.estimate_nu = p->estimate_nu;
+    ra.nu0 = (float)p->nu0;
+    ra.nu_lo = p->nu_lo;
+    ra.nu_hi = p->nu_hi;
+    return ra;
+}
+
+}  // namespace rgbid
+
+using namespace rgbid;
+
+extern "C" size_t rgbid_align_workspace_bytes(const rgbid_pyramid* ref, const rgbid_align_params* params) {
+    (void)params;
+    if (!ref || ref->levels < 1) return 0;
+    return workspace_bytes_for(ref->lv[0].width, ref->lv[0].height);
+}
+
+extern "C" int rgbid_align(const rgbid_pyramid* ref, const rgbid_pyramid* cur, const double* T_init, int T_init_on_device,
+                           const rgbid_align_params* params, void* workspace, size_t workspace_bytes,
+                           rgbid_align_result* d_result, void* stream_) {
+    int st_chk = check_pyramids(ref, cur, params);
+    if (st_chk != RGBID_OK) return st_chk;
+    if (!d_result) return RGBID_ERR_INVALID_ARG;
+    if (!workspace || ((uintptr_t)workspace & 255u) || workspace_bytes < rgbid_align_workspace_bytes(ref, params))
+        return RGBID_ERR_WORKSPACE;
+    cudaStream_t stream = (cudaStream_t)stream_;
+    AlignState* st = (AlignState*)workspace;
+    float* partials = (float*)((char*)workspace + align_up(sizeof(AlignState), 256));
+
+    InitArgs ia;
+    memset(&ia, 0, sizeof(ia));
+    ia.st = st;
+    ia.res = d_result;
+    ia.T_dev = (T_init && T_init_on_device) ? T_init : nullptr;
+    for (int i = 0; i < 16; ++i) ia.T_val[i] = (i % 5 == 0) ? 1.0 : 0.0;
+    if (T_init && !T_init_on_device)
+        for (int i = 0; i < 16; ++i) ia.T_val[i] = T_init[i];
+    init_kernel<<<1, 32, 0, stream>>>(ia);
+    if (cudaGetLastError() != cudaSuccess) return RGBID_ERR_CUDA;
+
+    for (int l = params->levels - 1; l >= 0; --l) {
+        RobustArgs ra = robust_args(ref, cur, l, params, st);
+        SweepArgs sa;
+        memset(&sa, 0, sizeof(sa));
+        sa.A = ra.A;
+        sa.B = ra.B;
+        sa.st = st;
+        sa.partials = partials;
+        sa.res = d_result;
+        sa.update = 1;
+        sa.min_valid = params->min_valid;
+        rgbid_timing* tm = params->timing;
+        for (int it = 0; it < params->iters[l]; ++it) {
+            const bool tr = tm && tm->kernel == RGBID_KERNEL_ROBUST && tm->count < tm->capacity;
+            if (tr && cudaEventRecord((cudaEvent_t)tm->ev_start[tm->count], stream) != cudaSuccess) return RGBID_ERR_CUDA;
+            if (launch_robust_any(ref->precision, ra, stream) != cudaSuccess) return RGBID_ERR_CUDA;
+            if (tr) {
+                if (cudaEventRecord((cudaEvent_t)tm->ev_end[tm->count], stream) != cudaSuccess) return RGBID_ERR_CUDA;
+                tm->count += 1;
+                tm->units += ra.nsamp;
+            }
+            const bool ts = tm && tm->kernel == RGBID_KERNEL_SWEEP && tm->count < tm->capacity;
+            if (ts && cudaEventRecord((cudaEvent_t)tm->ev_start[tm->count], stream) != cudaSuccess) return RGBID_ERR_CUDA;
+            if (launch_sweep_any(ref->precision, sa, stream) != cudaSuccess) return RGBID_ERR_CUDA;
+            if (ts) {
+                if (cudaEventRecord((cudaEvent_t)tm->ev_end[tm->count], stream) != cudaSuccess) return RGBID_ERR_CUDA;
+                tm->count += 1;
+                tm->units += (long long)sa.A.w * sa.A.h;
+            }
+        }
+    }
+    return RGBID_OK;
+}
+
+extern "C" int rgbid_eval_step(const rgbid_pyramid* ref, const rgbid_pyramid* cur, int level, const double* T,
+                               const double* robust, const rgbid_align_params* params, void* workspace,
+                               size_t workspace_bytes, float* r_I, float* r_W, uint8_t* mask_I, uint8_t* mask_W,
+                               rgbid_align_result* d_result, void* stream_) {
+    if (!params || !T || !d_result) return RGBID_ERR_INVALID_ARG;
+    rgbid_align_params p = *params;
+    if (level < 0 || level >= RGBID_MAX_LEVELS) return RGBID_ERR_INVALID_ARG;
+    if (p.levels < level + 1) p.levels = level + 1;
+    int st_chk = check_pyramids(ref, cur, &p);
+    if (st_chk != RGBID_OK) return st_chk;
+    const bool any_out = r_I || r_W || mask_I || mask_W;
+    if (any_out && !(r_I && r_W && mask_I && mask_W)) return RGBID_ERR_INVALID_ARG;
+    if (!workspace || ((uintptr_t)workspace & 255u) || workspace_bytes < rgbid_align_workspace_bytes(ref, &p))
+        return RGBID_ERR_WORKSPACE;
+    cudaStream_t stream = (cudaStream_t)stream_;
+    AlignState* st = (AlignState*)workspace;
+    float* partials = (float*)((char*)workspace + align_up(sizeof(AlignState), 256));
+
+    InitArgs ia;
+    memset(&ia, 0, sizeof(ia));
+    ia.st = st;
+    ia.res = d_result;
+    for (int i = 0; i < 16; ++i) ia.T_val[i] = T[i];
+    if (robust) {
+        ia.use_fixed = 1;
+        for (int i = 0; i < 6; ++i) ia.fixed[i] = (float)robust[i];
+    }
+    init_kernel<<<1, 32, 0, stream>>>(ia);
+    if (cudaGetLastError() != cudaSuccess) return RGBID_ERR_CUDA;
+    RobustArgs ra = robust_args(ref, cur, level, &p, st);
+    if (!robust && launch_robust_any(ref->precision, ra, stream) != cudaSuccess) return RGBID_ERR_CUDA;
+    SweepArgs sa;
+    memset(&sa, 0, sizeof(sa));
+    sa.A = ra.A;
+    sa.B = ra.B;
+    sa.st = st;
+    sa.partials = partials;
+    sa.res = d_result;
+    sa.update = 0;
+    sa.min_valid = p.min_valid;
+    sa.r_I = r_I;
+    sa.r_W = r_W;
+    sa.m_I = mask_I;
+    sa.m_W = mask_W;
+    if (launch_sweep_any(ref->precision, sa, stream) != cudaSuccess) return RGBID_ERR_CUDA;
+    return RGBID_OK;
+}

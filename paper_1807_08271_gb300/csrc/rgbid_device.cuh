@@ -1,0 +1,373 @@
+// Device-side building blocks shared by the rgbid kernels (sm_103a).
+//
+// Per-pixel arithmetic is FP32.  The warp is written as an offset from the
+// pixel itself: with q = K^-1 p, X_A = q / W_A and T = [R, t],
+//   X_B = R^T (X_A - t) = (q + d) / W_A,   d = (R^T - I) q - W_A R^T t,
+// so p_B - p = (fx (d_x - a d_z), fy (d_y - b d_z)) / (1 + d_z) with
+// q = (a, b, 1).  The flow is small, so it keeps full FP32 relative precision
+// where the absolute coordinate u_B (up to ~1300) would lose ~1e-4 px.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cstdint>
+
+#include "rgbid.h"
+
+namespace rgbid {
+
+constexpr int kSlots = 32;         // reduction slots: H (21) | g (6) | cost | n_I | n_W | 2 spare
+constexpr int kSlotG = 21;
+constexpr int kSlotCost = 27;
+constexpr int kSlotNI = 28;
+constexpr int kSlotNW = 29;
+
+// Pose in the form the per-pixel warp consumes.
+struct WarpPose {
+    float E[9];     // R^T - I, row-major
+    float s[3];     // R^T t
+    float R2[3];    // third row of R
+    float tz;       // t_z
+};
+
+// Robust parameters consumed by the weights (per channel: mu, sigma^2 * nu, nu + 1, ok).
+struct RobustParams {
+    float mu[2];
+    float sigma[2];
+    float nu[2];
+    int ok[2];
+};
+
+struct LevelDev {
+    const void* IW;
+    int w, h, pitch, pad;
+    float fx, fy, cx, cy, ifx, ify;
+};
+
+// Device-resident state of one alignment (lives at the start of the workspace).
+struct AlignState {
+    double T[16];           // current estimate A_T_B
+    WarpPose wp;            // FP32 warp parameters of T
+    RobustParams rob;       // robust parameters of the current iteration
+    unsigned int counter;   // last-block ticket of the sweep
+    int status;
+    int iters_done;
+    int iters_skipped;
+    int timeouts;
+    int pad[3];
+};
+
+// ---------------------------------------------------------------- pixel loads
+template <int PREC>
+struct Pix;
+
+template <>
+struct Pix<RGBID_PLANES_F32> {
+    static __device__ __forceinline__ float2 load(const void* base, int idx) {
+        return __ldg(reinterpret_cast<const float2*>(base) + idx);
+    }
+};
+
+template <>
+struct Pix<RGBID_PLANES_BF16_F16> {
+    static __device__ __forceinline__ float2 load(const void* base, int idx) {
+        uint32_t raw = __ldg(reinterpret_cast<const unsigned int*>(base) + idx);
+        __nv_bfloat16 i = __ushort_as_bfloat16((unsigned short)(raw & 0xffffu));
+        __half w = __ushort_as_half((unsigned short)(raw >> 16));
+        return make_float2(__bfloat162float(i), __half2float(w));
+    }
+};
+
+// ---------------------------------------------------------------- per-pixel terms
+struct PixelTerms {
+    float rI, rW;        // residuals r(p, 0)
+    float JI[6], JW[6];  // Jacobians (translation first)
+    float lam;           // normal weight lambda_n
+    bool mI, mW;         // masks
+};
+
+// Evaluate one pixel p = (u, v) of A: warp, residuals and (if WANT_J) Jacobians.
+// Follows eqs. 3d_registration, res_int, res_depth and DeltaX of the paper.
+template <int PREC, bool WANT_J>
+__device__ __forceinline__ void eval_pixel(const LevelDev& A, const LevelDev& B, const WarpPose& wp,
+                                           int u, int v, PixelTerms& o) {
+    o.mI = false;
+    o.mW = false;
+    o.rI = 0.f;
+    o.rW = 0.f;
+    if (u < 1 || v < 1 || u > A.w - 2 || v > A.h - 2) return;      // no central gradient on the border
+    const int idx = v * A.pitch + u;
+    const float2 c = Pix<PREC>::load(A.IW, idx);
+    const float WA = c.y;
+    if (!(WA > 0.f)) return;
+    const float a = ((float)u - A.cx) * A.ifx;
+    const float b = ((float)v - A.cy) * A.ify;
+    // d = (R^T - I) q - W_A R^T t
+    const float dx = fmaf(wp.E[0], a, fmaf(wp.E[1], b, wp.E[2])) - WA * wp.s[0];
+    const float dy = fmaf(wp.E[3], a, fmaf(wp.E[4], b, wp.E[5])) - WA * wp.s[1];
+    const float dz = fmaf(wp.E[6], a, fmaf(wp.E[7], b, wp.E[8])) - WA * wp.s[2];
+    const float mz = 1.f + dz;                       // Z_B * W_A
+    if (!(mz > 0.f)) return;
+    const float imz = 1.f / mz;
+    const float du = A.fx * fmaf(-a, dz, dx) * imz;  // u_B - u
+    const float dv = A.fy * fmaf(-b, dz, dy) * imz;  // v_B - v
+    const float fdu = floorf(du), fdv = floorf(dv);
+    if (!(fabsf(fdu) < 1.0e7f && fabsf(fdv) < 1.0e7f)) return;
+    const int x0 = u + (int)fdu, y0 = v + (int)fdv;
+    if (x0 < 0 || y0 < 0 || x0 > B.w - 2 || y0 > B.h - 2) return;
+    const float ax = du - fdu, ay = dv - fdv;
+    const int bi = y0 * B.pitch + x0;
+    const float2 t00 = Pix<PREC>::load(B.IW, bi);
+    const float2 t10 = Pix<PREC>::load(B.IW, bi + 1);
+    const float2 t01 = Pix<PREC>::load(B.IW, bi + B.pitch);
+    const float2 t11 = Pix<PREC>::load(B.IW, bi + B.pitch + 1);
+    const float itop = fmaf(ax, t10.x - t00.x, t00.x);
+    const float ibot = fmaf(ax, t11.x - t01.x, t01.x);
+    const float IBw = fmaf(ay, ibot - itop, itop);
+    o.mI = true;
+    o.rI = IBw - c.x;
+
+    // neighbours for central differences
+    const float2 nl = Pix<PREC>::load(A.IW, idx - 1);
+    const float2 nr = Pix<PREC>::load(A.IW, idx + 1);
+    const float2 nu = Pix<PREC>::load(A.IW, idx - A.pitch);
+    const float2 nd = Pix<PREC>::load(A.IW, idx + A.pitch);
+
+    float WBw = 0.f;
+    bool okW = (t00.y > 0.f) && (t10.y > 0.f) && (t01.y > 0.f) && (t11.y > 0.f) &&
+               (nl.y > 0.f) && (nr.y > 0.f) && (nu.y > 0.f) && (nd.y > 0.f);
+    if (okW) {
+        const float wtop = fmaf(ax, t10.y - t00.y, t00.y);
+        const float wbot = fmaf(ax, t11.y - t01.y, t01.y);
+        const float WBp = fmaf(ay, wbot - wtop, wtop);
+        // W_B^gamma = 1 / e_z^T (R K^-1 p_B / W_B(p_B) + t) = W_B(p_B) / (R_2 . q_B + t_z W_B(p_B))
+        const float qbx = a + du * A.ifx;
+        const float qby = b + dv * A.ify;
+        const float den = fmaf(wp.R2[0], qbx, fmaf(wp.R2[1], qby, wp.R2[2])) + wp.tz * WBp;
+        okW = den > 0.f;
+        if (okW) {
+            WBw = WBp / den;
+            o.rW = WBw - WA;
+        }
+    }
+    o.mW = okW;
+    if (!WANT_J) return;
+
+    // g~_I = grad I_A (K - p e_z^T) = (gx fx, gy fy, -(gx fx a + gy fy b))
+    const float gIx = 0.5f * (nr.x - nl.x) * A.fx;
+    const float gIy = 0.5f * (nd.x - nu.x) * A.fy;
+    const float gIz = -fmaf(gIx, a, gIy * b);
+    // J_I = (W_A g~_I, q x g~_I)
+    o.JI[0] = WA * gIx;
+    o.JI[1] = WA * gIy;
+    o.JI[2] = WA * gIz;
+    o.JI[3] = fmaf(b, gIz, -gIy);          // q = (a, b, 1)
+    o.JI[4] = fmaf(-a, gIz, gIx);
+    o.JI[5] = fmaf(a, gIy, -b * gIx);
+    if (okW) {
+        const float gWx = 0.5f * (nr.y - nl.y) * A.fx;
+        const float gWy = 0.5f * (nd.y - nu.y) * A.fy;
+        const float gWz0 = -fmaf(gWx, a, gWy * b);
+        const float gWz = gWz0 + WBw;      // + W_B^gamma e_z
+        o.JW[0] = WA * gWx;
+        o.JW[1] = WA * gWy;
+        o.JW[2] = WA * gWz;
+        o.JW[3] = fmaf(b, gWz, -gWy);
+        o.JW[4] = fmaf(-a, gWz, gWx);
+        o.JW[5] = fmaf(a, gWy, -b * gWx);
+        // lambda_n = 1 / (|n_u| |q|), n_u = g~_W / W_A + e_z  (n_u . q = 1)
+        const float iW = 1.f / WA;
+        const float nx = gWx * iW, ny = gWy * iW, nz = fmaf(gWz0, iW, 1.f);
+        const float nn = fmaf(nx, nx, fmaf(ny, ny, nz * nz));
+        const float qq = fmaf(a, a, fmaf(b, b, 1.f));
+        o.lam = rsqrtf(nn * qq);
+    } else {
+        o.lam = 0.f;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) o.JW[k] = 0.f;
+    }
+}
+
+// Student-t weight omega(x, nu) / sigma^2 = (nu + 1) / (nu sigma^2 + (r - mu)^2).
+__device__ __forceinline__ float robust_weight(float r, float mu, float sig, float nu) {
+    const float d = r - mu;
+    return __fdividef(nu + 1.f, fmaf(d, d, nu * sig * sig));
+}
+
+// ---------------------------------------------------------------- reductions
+// Butterfly reduce-scatter: 32 per-lane values in, lane l returns the warp sum of value l.
+__device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32]) {
+    const unsigned lane = threadIdx.x & 31u;
+#pragma unroll
+    for (int n = 16; n >= 1; n >>= 1) {
+        const bool upper = (lane & (unsigned)n) != 0u;
+#pragma unroll
+        for (int i = 0; i < n; ++i) {
+            const float send = upper ? v[i] : v[i + n];
+            const float keep = upper ? v[i + n] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, n);
+        }
+    }
+    return v[0];
+}
+
+__device__ __forceinline__ float warp_sum(float x) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+__device__ __forceinline__ double warp_sum_d(double x) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// ---------------------------------------------------------------- compensated sums
+// Knuth TwoSum accumulation of floats: the pair (hi, lo) carries the rounding error.
+struct F2 {
+    float hi, lo;
+    __device__ __forceinline__ void add(float b) {
+        const float s = hi + b;
+        const float bp = s - hi;
+        const float e = (hi - (s - bp)) + (b - bp);
+        hi = s;
+        lo += e;
+    }
+    __device__ __forceinline__ void add(const F2& o) {
+        add(o.hi);
+        lo += o.lo;
+    }
+    __device__ __forceinline__ float value() const { return hi + lo; }
+};
+
+// ---------------------------------------------------------------- 6x6 solve (FP32, Jacobi-scaled)
+// Solve H xi = rhs for SPD H.  H is first scaled to unit diagonal (S = D H D,
+// D = diag(H)^-1/2), then factorised S = L L^T by Cholesky.  Returns false if
+// a diagonal entry or pivot is not positive.
+__device__ __forceinline__ bool cholesky_solve6_f(const float H[36], const float rhs[6], float xi[6]) {
+    float D[6], L[36], y[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        if (!(H[i * 6 + i] > 0.f)) return false;
+        D[i] = rsqrtf(H[i * 6 + i]);
+    }
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        float d = H[j * 6 + j] * D[j] * D[j];
+#pragma unroll
+        for (int k = 0; k < j; ++k) d = fmaf(-L[j * 6 + k], L[j * 6 + k], d);
+        if (!(d > 1e-7f)) return false;
+        const float r = rsqrtf(d);
+        L[j * 6 + j] = d * r;
+#pragma unroll
+        for (int i = j + 1; i < 6; ++i) {
+            float t = H[i * 6 + j] * D[i] * D[j];
+#pragma unroll
+            for (int k = 0; k < j; ++k) t = fmaf(-L[i * 6 + k], L[j * 6 + k], t);
+            L[i * 6 + j] = t * r;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        float t = rhs[i] * D[i];
+#pragma unroll
+        for (int k = 0; k < i; ++k) t = fmaf(-L[i * 6 + k], y[k], t);
+        y[i] = t / L[i * 6 + i];
+    }
+#pragma unroll
+    for (int i = 5; i >= 0; --i) {
+        float t = y[i];
+#pragma unroll
+        for (int k = i + 1; k < 6; ++k) t = fmaf(-L[k * 6 + i], xi[k], t);
+        xi[i] = t / L[i * 6 + i];
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) xi[i] *= D[i];
+    return true;
+}
+
+// ---------------------------------------------------------------- warp-parallel pose arithmetic (double)
+// FP64 on this part runs at ~1/64 of the FP32 rate with ~64-cycle latency, so
+// the 4x4 pose products are spread over the lanes of one warp (one dependent
+// chain of <= 4 FP64 operations per lane).
+
+// out = warp pose of T (all 32 lanes call; T and out may be in shared or global memory).
+__device__ __forceinline__ void warp_make_pose(const double* T, WarpPose* out) {
+    const int lane = threadIdx.x & 31;
+    if (lane < 9) {
+        const int i = lane / 3, j = lane % 3;
+        out->E[lane] = (float)(T[j * 4 + i] - (i == j ? 1.0 : 0.0));
+    } else if (lane < 12) {
+        const int i = lane - 9;
+        out->s[i] = (float)(T[0 * 4 + i] * T[3] + T[1 * 4 + i] * T[7] + T[2 * 4 + i] * T[11]);
+    } else if (lane < 15) {
+        out->R2[lane - 12] = (float)T[8 + lane - 12];
+    } else if (lane == 15) {
+        out->tz = (float)T[11];
+    }
+}
+
+// T <- exp(xi)^-1 T with the decoupled exponential exp(xi) = [exp([theta]x), v; 0, 1]
+// (Rodrigues with (1 - cos)/theta^2).  Called by all 32 lanes of one warp;
+// xi is uniform across the warp; T is read and written in place (12 lanes write).
+__device__ __forceinline__ void warp_apply_update(const float xi[6], double* T) {
+    const int lane = threadIdx.x & 31;
+    const float tx = xi[3], ty = xi[4], tz = xi[5];
+    const float t2 = fmaf(tx, tx, fmaf(ty, ty, tz * tz));
+    float A, B;
+    if (t2 < 1e-8f) {
+        A = 1.f - t2 * (1.f / 6.f);
+        B = 0.5f - t2 * (1.f / 24.f);
+    } else {
+        const float t = sqrtf(t2);
+        float sn, cs;
+        sincosf(t, &sn, &cs);
+        A = sn / t;
+        // 1 - cos t = 2 sin^2(t/2) avoids cancellation
+        const float sh = sinf(0.5f * t);
+        B = 2.f * sh * sh / t2;
+    }
+    // Mi = exp(xi)^-1 = [R^T, -R^T v], R = I + A [th]x + B ([th][th]^T - t2 I), row i of R^T = column i of R
+    double Tn = 0.0;
+    if (lane < 12) {
+        const int i = lane / 4, j = lane % 4;
+        const double th[3] = {(double)tx, (double)ty, (double)tz};
+        const double Ad = A, Bd = B, t2d = (double)tx * tx + (double)ty * ty + (double)tz * tz;
+        double Rt[3];   // row i of R^T = (R_0i, R_1i, R_2i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            double cross = 0.0;    // ([th]x)_ki
+            if (k == 0 && i == 1) cross = -th[2];
+            if (k == 0 && i == 2) cross = th[1];
+            if (k == 1 && i == 0) cross = th[2];
+            if (k == 1 && i == 2) cross = -th[0];
+            if (k == 2 && i == 0) cross = -th[1];
+            if (k == 2 && i == 1) cross = th[0];
+            Rt[k] = (k == i ? 1.0 : 0.0) + Ad * cross + Bd * (th[k] * th[i] - (k == i ? t2d : 0.0));
+        }
+        Tn = Rt[0] * T[0 * 4 + j] + Rt[1] * T[1 * 4 + j] + Rt[2] * T[2 * 4 + j];
+        if (j == 3) Tn -= Rt[0] * (double)xi[0] + Rt[1] * (double)xi[1] + Rt[2] * (double)xi[2];
+    }
+    __syncwarp();
+    if (lane < 12) T[lane] = Tn;
+    __syncwarp();
+}
+
+// digamma by the recurrence psi(x) = psi(x + 1) - 1/x up to x >= 6 followed by the
+// asymptotic series psi(x) ~ ln x - 1/(2x) - sum_k B_2k / (2k x^2k)
+// (Abramowitz & Stegun 6.3.5 and 6.3.18).
+__device__ __forceinline__ double digamma_d(double x) {
+    double acc = 0.0;
+    while (x < 6.0) {
+        acc -= 1.0 / x;
+        x += 1.0;
+    }
+    const double ix = 1.0 / x, ix2 = ix * ix;
+    // B2/2 = 1/12, B4/4 = -1/120, B6/6 = 1/252, B8/8 = -1/240, B10/10 = 1/132, B12/12 = -691/32760
+    const double series = ix2 * (1.0 / 12.0 - ix2 * (1.0 / 120.0 - ix2 * (1.0 / 252.0 - ix2 * (1.0 / 240.0 - ix2 * (1.0 / 132.0 - ix2 * (691.0 / 32760.0))))));
+    return acc + log(x) - 0.5 * ix - series;
+}
+
+}  // namespace rgbid

@@ -1,0 +1,232 @@
+// Keyframe fusion ("Keyframe fusion", section "RGB-ID SLAM system"), keyframe
+// initialisation, and the small pose helpers of the tracking front-end.
+//
+// Fusion warps every keyframe pixel with W_kf > 0 into frame k by the inverse
+// geometric warping (eq. 3d_registration with the pixel offset form of the
+// alignment kernels), applies the visibility test of "Dense frame
+// covisibility ratio" (|W_k(p_k) - w_k| < 3 sigma_W with w_k the keyframe
+// point's inverse depth in frame k) and updates the weighted means in place:
+//   W_kf <- (W_kf C_kf + C_k W_k*) / (C_kf + C_k),  C_kf <- C_kf + C_k,
+// with W_k* = W_k(p_k) / (R_2 . K^-1 p_k + t_z W_k(p_k)) the transferred
+// inverse depth and C_k = (dW_k*/dW_k)^-2 = (R_2 . K^-1 p_k + t_z W_k)^4 / (R_2 . K^-1 p_k)^2.
+#include <cstdint>
+#include <cstring>
+
+#include "rgbid_device.cuh"
+#include "rgbid_util.h"
+
+namespace rgbid {
+
+struct FuseArgs {
+    float* I_kf;
+    float* W_kf;
+    float* C_kf;
+    const float* I_k;
+    const float* W_k;
+    int pitch_kf, pitch_k, w, h;
+    float fx, fy, cx, cy, ifx, ify;
+    const double* T_dev;       // device pose (kf_T_k) or null
+    const double* sigma_dev;   // device sigma_W or null
+    double T_val[16];
+    double sigma_val;
+    int fuse_intensity;
+};
+
+__global__ void __launch_bounds__(256) fuse_kernel(FuseArgs a) {
+    __shared__ WarpPose sh_wp;
+    __shared__ float sh_gate;
+    __shared__ double sh_T[16];
+    if (threadIdx.y == 0) {           // warp 0 derives the FP32 warp pose from the FP64 pose
+        const double* T = a.T_dev ? a.T_dev : a.T_val;
+        if (threadIdx.x < 16) sh_T[threadIdx.x] = T[threadIdx.x];
+        __syncwarp();
+        warp_make_pose(sh_T, &sh_wp);
+        if (threadIdx.x == 0) sh_gate = (float)(3.0 * (a.sigma_dev ? *a.sigma_dev : a.sigma_val));
+    }
+    __syncthreads();
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    const int v = blockIdx.y * blockDim.y + threadIdx.y;
+    if (u >= a.w || v >= a.h) return;
+    const WarpPose& wp = sh_wp;
+    const size_t o = (size_t)v * a.pitch_kf + u;
+    const float Wkf = a.W_kf[o];
+    if (!(Wkf > 0.f)) return;
+    const float qa = ((float)u - a.cx) * a.ifx;
+    const float qb = ((float)v - a.cy) * a.ify;
+    const float dx = fmaf(wp.E[0], qa, fmaf(wp.E[1], qb, wp.E[2])) - Wkf * wp.s[0];
+    const float dy = fmaf(wp.E[3], qa, fmaf(wp.E[4], qb, wp.E[5])) - Wkf * wp.s[1];
+    const float dz = fmaf(wp.E[6], qa, fmaf(wp.E[7], qb, wp.E[8])) - Wkf * wp.s[2];
+    const float mz = 1.f + dz;                      // Z_k W_kf
+    if (!(mz > 0.f)) return;
+    const float imz = 1.f / mz;
+    const float du = a.fx * fmaf(-qa, dz, dx) * imz;
+    const float dv = a.fy * fmaf(-qb, dz, dy) * imz;
+    const float fdu = floorf(du), fdv = floorf(dv);
+    if (!(fabsf(fdu) < 1.0e7f && fabsf(fdv) < 1.0e7f)) return;
+    const int x0 = u + (int)fdu, y0 = v + (int)fdv;
+    if (x0 < 0 || y0 < 0 || x0 > a.w - 2 || y0 > a.h - 2) return;
+    const float ax = du - fdu, ay = dv - fdv;
+    const size_t bi = (size_t)y0 * a.pitch_k + x0;
+    const float w00 = __ldg(a.W_k + bi), w10 = __ldg(a.W_k + bi + 1);
+    const float w01 = __ldg(a.W_k + bi + a.pitch_k), w11 = __ldg(a.W_k + bi + a.pitch_k + 1);
+    if (!(w00 > 0.f && w10 > 0.f && w01 > 0.f && w11 > 0.f)) return;
+    const float wtop = fmaf(ax, w10 - w00, w00), wbot = fmaf(ax, w11 - w01, w01);
+    const float Wkp = fmaf(ay, wbot - wtop, wtop);
+    const float wB = Wkf * imz;                     // 1 / Z_k of the keyframe point
+    if (!(fabsf(Wkp - wB) < sh_gate)) return;
+    const float qbx = qa + du * a.ifx, qby = qb + dv * a.ify;
+    const float ar = fmaf(wp.R2[0], qbx, fmaf(wp.R2[1], qby, wp.R2[2]));   // e_z^T R K^-1 p_k
+    const float den = fmaf(wp.tz, Wkp, ar);
+    if (!(den > 0.f)) return;
+    const float Wstar = Wkp / den;
+    const float den2 = den * den;
+    const float Ck = __fdividef(den2 * den2, ar * ar);
+    const float C = a.C_kf[o];
+    const float inv = 1.f / (C + Ck);
+    a.W_kf[o] = (Wkf * C + Ck * Wstar) * inv;
+    if (a.fuse_intensity) {
+        const float i00 = __ldg(a.I_k + bi), i10 = __ldg(a.I_k + bi + 1);
+        const float i01 = __ldg(a.I_k + bi + a.pitch_k), i11 = __ldg(a.I_k + bi + a.pitch_k + 1);
+        const float itop = fmaf(ax, i10 - i00, i00), ibot = fmaf(ax, i11 - i01, i01);
+        const float Ik = fmaf(ay, ibot - itop, itop);
+        a.I_kf[o] = (a.I_kf[o] * C + Ck * Ik) * inv;
+    }
+    a.C_kf[o] = C + Ck;
+}
+
+__global__ void init_keyframe_kernel(float* I_kf, float* W_kf, float* C_kf, int pitch_kf, const float* I_k,
+                                     const float* W_k, int pitch_k, int w, int h) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    const int v = blockIdx.y * blockDim.y + threadIdx.y;
+    if (u >= w || v >= h) return;
+    const size_t o = (size_t)v * pitch_kf + u, s = (size_t)v * pitch_k + u;
+    I_kf[o] = I_k[s];
+    W_kf[o] = W_k[s];
+    C_kf[o] = 1.f;
+}
+
+// rf_T_k(0) = rf_T_{k-1} (rf_T_{k-2})^-1 rf_T_{k-1} ("Camera tracking": constant velocity)
+__device__ void rigid_inverse(const double* A, double* Ai) {
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) Ai[i * 4 + j] = A[j * 4 + i];
+        Ai[i * 4 + 3] = -(A[0 * 4 + i] * A[3] + A[1 * 4 + i] * A[7] + A[2 * 4 + i] * A[11]);
+    }
+    Ai[12] = 0.0; Ai[13] = 0.0; Ai[14] = 0.0; Ai[15] = 1.0;
+}
+
+__device__ void rigid_mul(const double* A, const double* B, double* C) {
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 4; ++j) {
+            double s = A[i * 4 + 0] * B[0 * 4 + j] + A[i * 4 + 1] * B[1 * 4 + j] + A[i * 4 + 2] * B[2 * 4 + j];
+            if (j == 3) s += A[i * 4 + 3];
+            C[i * 4 + j] = s;
+        }
+    C[12] = 0.0; C[13] = 0.0; C[14] = 0.0; C[15] = 1.0;
+}
+
+__global__ void predict_pose_kernel(const double* T1, const double* T2, double* out) {
+    if (threadIdx.x != 0) return;
+    double a[16], b[16], i2[16], m[16], r[16];
+    for (int i = 0; i < 16; ++i) { a[i] = T1[i]; b[i] = T2[i]; }
+    rigid_inverse(b, i2);
+    rigid_mul(a, i2, m);
+    rigid_mul(m, a, r);
+    for (int i = 0; i < 16; ++i) out[i] = r[i];
+}
+
+__global__ void compose_pose_kernel(const double* A, int inv, const double* B, double* out) {
+    if (threadIdx.x != 0) return;
+    double a[16], b[16], ai[16], r[16];
+    for (int i = 0; i < 16; ++i) { a[i] = A[i]; b[i] = B[i]; }
+    if (inv) {
+        rigid_inverse(a, ai);
+        rigid_mul(ai, b, r);
+    } else {
+        rigid_mul(a, b, r);
+    }
+    for (int i = 0; i < 16; ++i) out[i] = r[i];
+}
+
+}  // namespace rgbid
+
+using namespace rgbid;
+
+extern "C" int rgbid_fuse_keyframe(float* I_kf, float* W_kf, float* C_kf, int pitch_kf, const float* I_k,
+                                   const float* W_k, int pitch_k, int width, int height, rgbid_intrinsics K,
+                                   const double* T_kf_k, const double* sigma_W, int params_on_device,
+                                   int fuse_intensity, void* stream_) {
+    if (!I_kf || !W_kf || !C_kf || !I_k || !W_k || !T_kf_k || !sigma_W) return RGBID_ERR_INVALID_ARG;
+    if (width < 2 || height < 2 || pitch_kf < width || pitch_k < width) return RGBID_ERR_INVALID_ARG;
+    if (!(K.fx > 0.0) || !(K.fy > 0.0)) return RGBID_ERR_INVALID_ARG;
+    FuseArgs a;
+    memset(&a, 0, sizeof(a));
+    a.I_kf = I_kf; a.W_kf = W_kf; a.C_kf = C_kf; a.I_k = I_k; a.W_k = W_k;
+    a.pitch_kf = pitch_kf; a.pitch_k = pitch_k; a.w = width; a.h = height;
+    a.fx = (float)K.fx; a.fy = (float)K.fy; a.cx = (float)K.cx; a.cy = (float)K.cy;
+    a.ifx = (float)(1.0 / K.fx); a.ify = (float)(1.0 / K.fy);
+    if (params_on_device) {
+        a.T_dev = T_kf_k;
+        a.sigma_dev = sigma_W;
+    } else {
+        for (int i = 0; i < 16; ++i) a.T_val[i] = T_kf_k[i];
+        a.sigma_val = *sigma_W;
+    }
+    a.fuse_intensity = fuse_intensity;
+    dim3 blk(32, 8);
+    dim3 grd((width + 31) / 32, (height + 7) / 8);
+    fuse_kernel<<<grd, blk, 0, (cudaStream_t)stream_>>>(a);
+    return cudaGetLastError() == cudaSuccess ? RGBID_OK : RGBID_ERR_CUDA;
+}
+
+extern "C" int rgbid_init_keyframe(float* I_kf, float* W_kf, float* C_kf, int pitch_kf, const float* I_k,
+                                   const float* W_k, int pitch_k, int width, int height, void* stream_) {
+    if (!I_kf || !W_kf || !C_kf || !I_k || !W_k || width < 1 || height < 1 || pitch_kf < width || pitch_k < width)
+        return RGBID_ERR_INVALID_ARG;
+    dim3 blk(32, 8);
+    dim3 grd((width + 31) / 32, (height + 7) / 8);
+    init_keyframe_kernel<<<grd, blk, 0, (cudaStream_t)stream_>>>(I_kf, W_kf, C_kf, pitch_kf, I_k, W_k, pitch_k, width,
+                                                                height);
+    return cudaGetLastError() == cudaSuccess ? RGBID_OK : RGBID_ERR_CUDA;
+}
+
+extern "C" int rgbid_predict_pose(const double* T_km1, const double* T_km2, double* T_out, void* stream_) {
+    if (!T_km1 || !T_km2 || !T_out) return RGBID_ERR_INVALID_ARG;
+    predict_pose_kernel<<<1, 32, 0, (cudaStream_t)stream_>>>(T_km1, T_km2, T_out);
+    return cudaGetLastError() == cudaSuccess ? RGBID_OK : RGBID_ERR_CUDA;
+}
+
+extern "C" int rgbid_compose_pose(const double* A, int invert_A, const double* B, double* T_out, void* stream_) {
+    if (!A || !B || !T_out || A == T_out) return RGBID_ERR_INVALID_ARG;
+    compose_pose_kernel<<<1, 32, 0, (cudaStream_t)stream_>>>(A, invert_A, B, T_out);
+    return cudaGetLastError() == cudaSuccess ? RGBID_OK : RGBID_ERR_CUDA;
+}
+
+extern "C" const char* rgbid_status_string(int status) {
+    switch (status) {
+        case RGBID_OK: return "RGBID_OK";
+        case RGBID_ERR_INVALID_ARG: return "RGBID_ERR_INVALID_ARG";
+        case RGBID_ERR_CUDA: return "RGBID_ERR_CUDA";
+        case RGBID_ERR_WORKSPACE: return "RGBID_ERR_WORKSPACE";
+        case RGBID_ERR_DEGENERATE: return "RGBID_ERR_DEGENERATE";
+        case RGBID_ERR_TIMEOUT: return "RGBID_ERR_TIMEOUT";
+        case RGBID_ERR_UNSUPPORTED: return "RGBID_ERR_UNSUPPORTED";
+        default: return "RGBID_UNKNOWN_STATUS";
+    }
+}
+
+extern "C" void rgbid_default_params(rgbid_align_params* p) {
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->levels = 3;
+    p->iters[0] = 5;
+    p->iters[1] = 5;
+    p->iters[2] = 10;
+    p->scale_iters = 10;
+    p->bisect_steps = 20;
+    p->sample_cap = RGBID_MAX_SAMPLES;
+    p->estimate_nu = 1;
+    p->min_valid = 60;
+    p->nu0 = 5.0;
+    p->nu_lo = 2.0;
+    p->nu_hi = 10.0;
+}

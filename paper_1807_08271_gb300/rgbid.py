@@ -1,0 +1,316 @@
+"""Thin Python binding of ``librgbid`` (the C ABI declared in ``include/rgbid.h``).
+
+Argument marshalling only: every step of the alignment and fusion runs in the
+library's CUDA kernels.  PyTorch supplies device memory (tensors whose
+``data_ptr()`` is passed through) and streams (``torch.cuda.Stream``); the
+functions below carry the same names as the C entry points.  There is no CPU
+fallback: if the library cannot be built or loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+from ctypes import POINTER, Structure, c_char_p, c_double, c_int, c_size_t, c_uint8, c_void_p
+
+import numpy as np
+
+from . import build as _build
+
+MAX_LEVELS = 6
+MAX_SAMPLES = 19200
+PLANES_F32 = 0
+PLANES_BF16_F16 = 1
+
+OK = 0
+ERR_INVALID_ARG = 1
+ERR_CUDA = 2
+ERR_WORKSPACE = 3
+ERR_DEGENERATE = 4
+ERR_TIMEOUT = 5
+ERR_UNSUPPORTED = 6
+
+
+class Intrinsics(Structure):
+    _fields_ = [("fx", c_double), ("fy", c_double), ("cx", c_double), ("cy", c_double)]
+
+
+class Level(Structure):
+    _fields_ = [("width", c_int), ("height", c_int), ("pitch", c_int), ("pad_", c_int),
+                ("K", Intrinsics), ("IW", c_void_p)]
+
+
+class Pyramid(Structure):
+    _fields_ = [("levels", c_int), ("precision", c_int), ("lv", Level * MAX_LEVELS)]
+
+
+KERNEL_SWEEP = 0
+KERNEL_ROBUST = 1
+
+
+class Timing(Structure):
+    _fields_ = [("ev_start", POINTER(c_void_p)), ("ev_end", POINTER(c_void_p)), ("capacity", c_int),
+                ("kernel", c_int), ("count", c_int), ("pad_", c_int), ("units", ctypes.c_longlong)]
+
+
+class AlignParams(Structure):
+    _fields_ = [("levels", c_int), ("iters", c_int * MAX_LEVELS), ("scale_iters", c_int),
+                ("bisect_steps", c_int), ("sample_cap", c_int), ("estimate_nu", c_int),
+                ("min_valid", c_int), ("pad_", c_int), ("nu0", c_double), ("nu_lo", c_double),
+                ("nu_hi", c_double), ("timing", POINTER(Timing))]
+
+
+class AlignResult(Structure):
+    _fields_ = [("T", c_double * 16), ("H", c_double * 36), ("g", c_double * 6), ("mu", c_double * 2),
+                ("sigma", c_double * 2), ("nu", c_double * 2), ("cost", c_double), ("n_valid", c_int * 2),
+                ("iters_done", c_int), ("iters_skipped", c_int), ("status", c_int), ("pad_", c_int)]
+
+
+RESULT_BYTES = ctypes.sizeof(AlignResult)
+
+_lock = threading.Lock()
+_lib = None
+
+# (name, restype, argtypes) of every entry point declared in include/rgbid.h
+SIGNATURES = [
+    ("rgbid_status_string", c_char_p, [c_int]),
+    ("rgbid_default_params", None, [POINTER(AlignParams)]),
+    ("rgbid_pyramid_bytes", c_size_t, [c_int, c_int, c_int, c_int]),
+    ("rgbid_build_pyramid", c_int, [c_void_p, c_void_p, c_int, c_int, c_int, Intrinsics, c_int, c_int,
+                                    c_void_p, c_size_t, POINTER(Pyramid), c_void_p]),
+    ("rgbid_align_workspace_bytes", c_size_t, [POINTER(Pyramid), POINTER(AlignParams)]),
+    ("rgbid_align", c_int, [POINTER(Pyramid), POINTER(Pyramid), c_void_p, c_int, POINTER(AlignParams),
+                            c_void_p, c_size_t, c_void_p, c_void_p]),
+    ("rgbid_eval_step", c_int, [POINTER(Pyramid), POINTER(Pyramid), c_int, POINTER(c_double), c_void_p,
+                                POINTER(AlignParams), c_void_p, c_size_t, c_void_p, c_void_p, c_void_p,
+                                c_void_p, c_void_p, c_void_p]),
+    ("rgbid_fuse_keyframe", c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_int, c_int,
+                                    c_int, Intrinsics, c_void_p, c_void_p, c_int, c_int, c_void_p]),
+    ("rgbid_init_keyframe", c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_int, c_int,
+                                    c_int, c_void_p]),
+    ("rgbid_predict_pose", c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    ("rgbid_compose_pose", c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
+]
+
+
+class RgbidError(RuntimeError):
+    def __init__(self, fn: str, code: int):
+        super().__init__(f"{fn} failed: {status_name(code)} ({code})")
+        self.code = code
+
+
+def lib():
+    """Load (building first if needed) the in-tree librgbid.so."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = ctypes.CDLL(path)
+            for name, res, args in SIGNATURES:
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def status_name(code: int) -> str:
+    names = {0: "RGBID_OK", 1: "RGBID_ERR_INVALID_ARG", 2: "RGBID_ERR_CUDA", 3: "RGBID_ERR_WORKSPACE",
+             4: "RGBID_ERR_DEGENERATE", 5: "RGBID_ERR_TIMEOUT", 6: "RGBID_ERR_UNSUPPORTED"}
+    return names.get(code, "RGBID_UNKNOWN_STATUS")
+
+
+def _check(fn: str, code: int):
+    if code != OK:
+        raise RgbidError(fn, code)
+
+
+def _stream_ptr(stream) -> c_void_p:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return c_void_p(stream.cuda_stream)
+
+
+def _ptr(t) -> c_void_p:
+    return c_void_p(0 if t is None else t.data_ptr())
+
+
+# ----------------------------------------------------------------------------- entry points
+def rgbid_status_string(code: int) -> str:
+    return lib().rgbid_status_string(code).decode()
+
+
+def rgbid_default_params(levels: int | None = None, iters=None) -> AlignParams:
+    p = AlignParams()
+    lib().rgbid_default_params(ctypes.byref(p))
+    if levels is not None:
+        p.levels = levels
+    if iters is not None:
+        for i in range(MAX_LEVELS):
+            p.iters[i] = int(iters[i]) if i < len(iters) else 0
+    return p
+
+
+def rgbid_pyramid_bytes(width: int, height: int, levels: int, precision: int = PLANES_F32) -> int:
+    return int(lib().rgbid_pyramid_bytes(width, height, levels, precision))
+
+
+def rgbid_build_pyramid(I0, W0, K0, levels: int, precision: int, storage, stream=None) -> Pyramid:
+    """Build a pyramid from float32 CUDA tensors I0, W0 [h, w] into ``storage`` (uint8 CUDA tensor)."""
+    h, w = I0.shape[-2], I0.shape[-1]
+    pitch0 = I0.stride(-2)
+    assert W0.stride(-2) == pitch0 and I0.stride(-1) == 1 and W0.stride(-1) == 1
+    out = Pyramid()
+    K = Intrinsics(*[float(k) for k in K0])
+    code = lib().rgbid_build_pyramid(_ptr(I0), _ptr(W0), pitch0, w, h, K, levels, precision, _ptr(storage),
+                                     storage.numel() * storage.element_size(), ctypes.byref(out),
+                                     _stream_ptr(stream))
+    _check("rgbid_build_pyramid", code)
+    return out
+
+
+def rgbid_align_workspace_bytes(ref: Pyramid, params: AlignParams) -> int:
+    return int(lib().rgbid_align_workspace_bytes(ctypes.byref(ref), ctypes.byref(params)))
+
+
+def rgbid_align(ref: Pyramid, cur: Pyramid, T_init, params: AlignParams, workspace, result, stream=None):
+    """Enqueue an alignment.  ``T_init``: None (identity), a host array of 16
+    doubles, or a CUDA float64 tensor of 16 elements (read on the device)."""
+    if T_init is None:
+        tp, on_dev = c_void_p(0), 0
+    elif hasattr(T_init, "is_cuda") and T_init.is_cuda:
+        tp, on_dev = _ptr(T_init), 1
+    else:
+        arr = np.ascontiguousarray(np.asarray(T_init, dtype=np.float64).reshape(16))
+        tp, on_dev = c_void_p(arr.ctypes.data), 0
+    code = lib().rgbid_align(ctypes.byref(ref), ctypes.byref(cur), tp, on_dev, ctypes.byref(params),
+                             _ptr(workspace), workspace.numel() * workspace.element_size(), _ptr(result),
+                             _stream_ptr(stream))
+    _check("rgbid_align", code)
+
+
+def rgbid_eval_step(ref: Pyramid, cur: Pyramid, level: int, T, robust, params: AlignParams, workspace,
+                    r_I=None, r_W=None, mask_I=None, mask_W=None, result=None, stream=None):
+    Ta = np.ascontiguousarray(np.asarray(T, dtype=np.float64).reshape(16))
+    if robust is not None:
+        ra = np.ascontiguousarray(np.asarray(robust, dtype=np.float64).reshape(6))
+        rp = c_void_p(ra.ctypes.data)
+    else:
+        rp = c_void_p(0)
+    code = lib().rgbid_eval_step(ctypes.byref(ref), ctypes.byref(cur), level,
+                                 Ta.ctypes.data_as(POINTER(c_double)), rp, ctypes.byref(params), _ptr(workspace),
+                                 workspace.numel() * workspace.element_size(), _ptr(r_I), _ptr(r_W),
+                                 _ptr(mask_I), _ptr(mask_W), _ptr(result), _stream_ptr(stream))
+    _check("rgbid_eval_step", code)
+
+
+def rgbid_fuse_keyframe(I_kf, W_kf, C_kf, I_k, W_k, K, T_kf_k, sigma_W, fuse_intensity: bool = True, stream=None):
+    """Fuse frame k into the keyframe in place.  ``T_kf_k``/``sigma_W`` are either
+    host values (16-array, float) or CUDA float64 tensors (read on the device)."""
+    h, w = W_kf.shape[-2], W_kf.shape[-1]
+    on_dev = hasattr(T_kf_k, "is_cuda") and T_kf_k.is_cuda
+    keep = []
+    if on_dev:
+        tp, sp = _ptr(T_kf_k), _ptr(sigma_W)
+    else:
+        Ta = np.ascontiguousarray(np.asarray(T_kf_k, dtype=np.float64).reshape(16))
+        sa = np.array([float(sigma_W)], dtype=np.float64)
+        keep += [Ta, sa]
+        tp, sp = c_void_p(Ta.ctypes.data), c_void_p(sa.ctypes.data)
+    Ki = Intrinsics(*[float(k) for k in K])
+    code = lib().rgbid_fuse_keyframe(_ptr(I_kf), _ptr(W_kf), _ptr(C_kf), W_kf.stride(-2), _ptr(I_k), _ptr(W_k),
+                                     W_k.stride(-2), w, h, Ki, tp, sp, 1 if on_dev else 0,
+                                     1 if fuse_intensity else 0, _stream_ptr(stream))
+    _check("rgbid_fuse_keyframe", code)
+
+
+def rgbid_init_keyframe(I_kf, W_kf, C_kf, I_k, W_k, stream=None):
+    h, w = W_kf.shape[-2], W_kf.shape[-1]
+    code = lib().rgbid_init_keyframe(_ptr(I_kf), _ptr(W_kf), _ptr(C_kf), W_kf.stride(-2), _ptr(I_k), _ptr(W_k),
+                                     W_k.stride(-2), w, h, _stream_ptr(stream))
+    _check("rgbid_init_keyframe", code)
+
+
+def rgbid_predict_pose(T_km1, T_km2, T_out, stream=None):
+    _check("rgbid_predict_pose", lib().rgbid_predict_pose(_ptr(T_km1), _ptr(T_km2), _ptr(T_out), _stream_ptr(stream)))
+
+
+def rgbid_compose_pose(A, invert_A: bool, B, T_out, stream=None):
+    _check("rgbid_compose_pose", lib().rgbid_compose_pose(_ptr(A), 1 if invert_A else 0, _ptr(B), _ptr(T_out),
+                                                          _stream_ptr(stream)))
+
+
+# ----------------------------------------------------------------------------- conveniences
+def parse_result(buf) -> dict:
+    """Decode an rgbid_align_result held in a (device or host) uint8 tensor."""
+    raw = bytes(buf.detach().cpu().numpy().tobytes()[:RESULT_BYTES])
+    r = AlignResult.from_buffer_copy(raw)
+    return dict(T=np.array(r.T).reshape(4, 4), H=np.array(r.H).reshape(6, 6), g=np.array(r.g),
+                mu=list(r.mu), sigma=list(r.sigma), nu=list(r.nu), cost=r.cost, n_valid=list(r.n_valid),
+                iters_done=r.iters_done, iters_skipped=r.iters_skipped, status=r.status)
+
+
+def result_tensor(n: int = 1, device="cuda"):
+    import torch
+    return torch.zeros((n, RESULT_BYTES), dtype=torch.uint8, device=device)
+
+
+class DevicePyramid:
+    """A pyramid plus the device storage that backs it."""
+
+    def __init__(self, width: int, height: int, levels: int, precision: int = PLANES_F32, device="cuda"):
+        import torch
+        self.width, self.height, self.levels, self.precision = width, height, levels, precision
+        nbytes = rgbid_pyramid_bytes(width, height, levels, precision)
+        if nbytes == 0:
+            raise ValueError("invalid pyramid shape")
+        self.storage = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        self.desc = None
+
+    def build(self, I0, W0, K0, stream=None) -> "DevicePyramid":
+        self.desc = rgbid_build_pyramid(I0, W0, K0, self.levels, self.precision, self.storage, stream)
+        return self
+
+    def level_planes(self, l: int):
+        """(I, W) float32 host arrays of level l (for tests and inspection)."""
+        import torch
+        L = self.desc.lv[l]
+        off = L.IW - self.storage.data_ptr()
+        bpp = 8 if self.precision == PLANES_F32 else 4
+        raw = self.storage[off:off + L.pitch * L.height * bpp].cpu().numpy()
+        if self.precision == PLANES_F32:
+            a = raw.view(np.float32).reshape(L.height, L.pitch, 2)[:, :L.width]
+            return a[..., 0].copy(), a[..., 1].copy()
+        u = raw.view(np.uint16).reshape(L.height, L.pitch, 2)[:, :L.width]
+        I = (u[..., 0].astype(np.uint32) << 16).view(np.float32)
+        W = u[..., 1].copy().view(np.float16).astype(np.float32)
+        return I.copy(), W
+
+
+class KernelTimer:
+    """Caller-owned CUDA events that rgbid_align records around one kernel's launches."""
+
+    def __init__(self, kernel: int, capacity: int):
+        import torch
+        self.events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                       for _ in range(capacity)]
+        self._starts = (c_void_p * capacity)(*[e[0].cuda_event for e in self.events])
+        self._ends = (c_void_p * capacity)(*[e[1].cuda_event for e in self.events])
+        self.t = Timing(ctypes.cast(self._starts, POINTER(c_void_p)), ctypes.cast(self._ends, POINTER(c_void_p)),
+                        capacity, kernel, 0, 0, 0)
+
+    def attach(self, params: AlignParams):
+        params.timing = ctypes.pointer(self.t)
+
+    def reset(self):
+        self.t.count = 0
+        self.t.units = 0
+
+    def total_ms(self) -> float:
+        """Sum of the recorded launch durations (call after synchronising)."""
+        return float(sum(s.elapsed_time(e) for s, e in self.events[:self.t.count]))
+
+
+def new_workspace(ref: Pyramid, params: AlignParams, device="cuda"):
+    import torch
+    return torch.empty(rgbid_align_workspace_bytes(ref, params), dtype=torch.uint8, device=device)
