@@ -105,46 +105,89 @@ __global__ void init_keyframe_kernel(float* I_kf, float* W_kf, float* C_kf, int 
     C_kf[o] = 1.f;
 }
 
-// rf_T_k(0) = rf_T_{k-1} (rf_T_{k-2})^-1 rf_T_{k-1} ("Camera tracking": constant velocity)
-__device__ void rigid_inverse(const double* A, double* Ai) {
-    for (int i = 0; i < 3; ++i) {
-        for (int j = 0; j < 3; ++j) Ai[i * 4 + j] = A[j * 4 + i];
-        Ai[i * 4 + 3] = -(A[0 * 4 + i] * A[3] + A[1 * 4 + i] * A[7] + A[2 * 4 + i] * A[11]);
+// Warp-parallel rigid-transform arithmetic in FP64 (all 32 lanes call; the
+// matrices live in shared memory; lanes 0..11 own entry (i, j) of the 3x4 block).
+__device__ __forceinline__ void warp_rigid_mul(const double* A, const double* B, double* C) {
+    const int lane = threadIdx.x & 31;
+    double s = 0.0;
+    if (lane < 12) {
+        const int i = lane >> 2, j = lane & 3;
+        s = A[i * 4 + 0] * B[0 * 4 + j] + A[i * 4 + 1] * B[1 * 4 + j] + A[i * 4 + 2] * B[2 * 4 + j];
+        if (j == 3) s += A[i * 4 + 3];
     }
-    Ai[12] = 0.0; Ai[13] = 0.0; Ai[14] = 0.0; Ai[15] = 1.0;
+    __syncwarp();
+    if (lane < 12) C[lane] = s;
+    else if (lane < 16) C[lane] = (lane == 15) ? 1.0 : 0.0;
+    __syncwarp();
 }
 
-__device__ void rigid_mul(const double* A, const double* B, double* C) {
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 4; ++j) {
-            double s = A[i * 4 + 0] * B[0 * 4 + j] + A[i * 4 + 1] * B[1 * 4 + j] + A[i * 4 + 2] * B[2 * 4 + j];
-            if (j == 3) s += A[i * 4 + 3];
-            C[i * 4 + j] = s;
+__device__ __forceinline__ void warp_rigid_inverse(const double* A, double* Ai) {
+    const int lane = threadIdx.x & 31;
+    double s = 0.0;
+    if (lane < 12) {
+        const int i = lane >> 2, j = lane & 3;
+        s = (j < 3) ? A[j * 4 + i] : -(A[0 * 4 + i] * A[3] + A[1 * 4 + i] * A[7] + A[2 * 4 + i] * A[11]);
+    }
+    __syncwarp();
+    if (lane < 12) Ai[lane] = s;
+    else if (lane < 16) Ai[lane] = (lane == 15) ? 1.0 : 0.0;
+    __syncwarp();
+}
+
+// Project the rotation block onto SO(3) by Newton-Schulz iterations of the polar
+// factor, X <- X (3 I - X^T X) / 2, which converge quadratically to the nearest
+// orthonormal matrix.  Products of rotations read back from FP64 drift off SO(3)
+// by rounding, and the constant-velocity composition T1 T2^-1 T1 with the
+// transpose inverse amplifies that drift ~2.4x per frame unless it is removed.
+__device__ __forceinline__ void warp_orthonormalize(double* T, double* M) {
+    const int lane = threadIdx.x & 31;
+    for (int it = 0; it < 3; ++it) {
+        double m = 0.0;
+        if (lane < 9) {
+            const int i = lane / 3, j = lane % 3;
+            m = T[0 * 4 + i] * T[0 * 4 + j] + T[1 * 4 + i] * T[1 * 4 + j] + T[2 * 4 + i] * T[2 * 4 + j];
         }
-    C[12] = 0.0; C[13] = 0.0; C[14] = 0.0; C[15] = 1.0;
+        __syncwarp();
+        if (lane < 9) M[lane] = m;
+        __syncwarp();
+        double x = 0.0;
+        if (lane < 9) {
+            const int i = lane / 3, j = lane % 3;
+            x = 0.5 * (3.0 * T[i * 4 + j] - (T[i * 4 + 0] * M[0 * 3 + j] + T[i * 4 + 1] * M[1 * 3 + j] +
+                                             T[i * 4 + 2] * M[2 * 3 + j]));
+        }
+        __syncwarp();
+        if (lane < 9) T[(lane / 3) * 4 + (lane % 3)] = x;
+        __syncwarp();
+    }
 }
 
+// rf_T_k(0) = rf_T_{k-1} (rf_T_{k-2})^-1 rf_T_{k-1} ("Camera tracking": constant velocity),
+// with the rotation projected onto SO(3).
 __global__ void predict_pose_kernel(const double* T1, const double* T2, double* out) {
-    if (threadIdx.x != 0) return;
-    double a[16], b[16], i2[16], m[16], r[16];
-    for (int i = 0; i < 16; ++i) { a[i] = T1[i]; b[i] = T2[i]; }
-    rigid_inverse(b, i2);
-    rigid_mul(a, i2, m);
-    rigid_mul(m, a, r);
-    for (int i = 0; i < 16; ++i) out[i] = r[i];
+    __shared__ double a[16], b[16], bi[16], m[16], r[16], M[9];
+    const int lane = threadIdx.x & 31;
+    if (lane < 16) { a[lane] = T1[lane]; b[lane] = T2[lane]; }
+    __syncwarp();
+    warp_rigid_inverse(b, bi);
+    warp_rigid_mul(a, bi, m);
+    warp_rigid_mul(m, a, r);
+    warp_orthonormalize(r, M);
+    if (lane < 16) out[lane] = r[lane];
 }
 
 __global__ void compose_pose_kernel(const double* A, int inv, const double* B, double* out) {
-    if (threadIdx.x != 0) return;
-    double a[16], b[16], ai[16], r[16];
-    for (int i = 0; i < 16; ++i) { a[i] = A[i]; b[i] = B[i]; }
+    __shared__ double a[16], b[16], ai[16], r[16];
+    const int lane = threadIdx.x & 31;
+    if (lane < 16) { a[lane] = A[lane]; b[lane] = B[lane]; }
+    __syncwarp();
     if (inv) {
-        rigid_inverse(a, ai);
-        rigid_mul(ai, b, r);
+        warp_rigid_inverse(a, ai);
+        warp_rigid_mul(ai, b, r);
     } else {
-        rigid_mul(a, b, r);
+        warp_rigid_mul(a, b, r);
     }
-    for (int i = 0; i < 16; ++i) out[i] = r[i];
+    if (lane < 16) out[lane] = r[lane];
 }
 
 }  // namespace rgbid

@@ -294,6 +294,11 @@ class KernelTimer:
         import torch
         self.events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                        for _ in range(capacity)]
+        for a, b in self.events:          # torch creates the CUDA event on first record
+            a.record()
+            b.record()
+        torch.cuda.synchronize()
+        assert all(a.cuda_event and b.cuda_event for a, b in self.events)
         self._starts = (c_void_p * capacity)(*[e[0].cuda_event for e in self.events])
         self._ends = (c_void_p * capacity)(*[e[1].cuda_event for e in self.events])
         self.t = Timing(ctypes.cast(self._starts, POINTER(c_void_p)), ctypes.cast(self._ends, POINTER(c_void_p)),

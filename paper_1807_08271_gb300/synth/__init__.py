@@ -262,18 +262,19 @@ def _rot_angle(R):
 
 
 def make_trajectory(rng: np.random.Generator, n_frames: int = 300, fps: float = 30.0,
-                    v_max: float = 0.5, w_max_deg: float = 30.0) -> np.ndarray:
+                    v_max: float = 0.5, w_max_deg: float = 30.0, yaw_step_deg: float = 70.0) -> np.ndarray:
     """Smooth random camera-to-world poses [n, 4, 4] inside the room's free region.
 
-    Control poses once per second are joined by a cubic B-spline; the excursion
-    about the mean is then scaled down until speed <= v_max and angular rate <= w_max.
+    Control poses once per second (yaw random walk of +-yaw_step_deg, pitch
+    +-10 deg, roll +-5 deg) are joined by a cubic B-spline; the excursion about
+    the mean is then scaled down until speed <= v_max and angular rate <= w_max.
     """
     n_ctrl = int(np.ceil(n_frames / fps)) + 4
     pos = np.column_stack([rng.uniform(-0.9, 0.9, n_ctrl), rng.uniform(-0.3, 0.3, n_ctrl),
                            rng.uniform(-0.9, 0.9, n_ctrl)])
-    yaw = np.cumsum(rng.uniform(-np.deg2rad(70), np.deg2rad(70), n_ctrl))
-    ang = np.column_stack([yaw, rng.uniform(-np.deg2rad(15), np.deg2rad(15), n_ctrl),
-                           rng.uniform(-np.deg2rad(8), np.deg2rad(8), n_ctrl)])
+    yaw = np.cumsum(rng.uniform(-np.deg2rad(yaw_step_deg), np.deg2rad(yaw_step_deg), n_ctrl))
+    ang = np.column_stack([yaw, rng.uniform(-np.deg2rad(10), np.deg2rad(10), n_ctrl),
+                           rng.uniform(-np.deg2rad(5), np.deg2rad(5), n_ctrl)])
     tau = np.arange(n_frames) / fps
     P = _bspline(pos, tau)
     A = _bspline(ang, tau)
@@ -322,11 +323,11 @@ def make_pair(seed: int, width: int = 160, height: int = 120, K=None, noise: boo
 
 
 def render_sequence(seed: int = 0, n_frames: int = 300, width: int = 640, height: int = 480,
-                    noise: bool = True):
+                    noise: bool = True, yaw_step_deg: float = 70.0):
     """The 30 Hz room sequence: dict with I [n,h,w], W [n,h,w] (float32), K, T_wc [n,4,4]."""
     rng = np.random.default_rng(seed)
     scene = make_room(rng)
-    T = make_trajectory(rng, n_frames)
+    T = make_trajectory(rng, n_frames, yaw_step_deg=yaw_step_deg)
     K = pinhole(width, height)
     I = np.zeros((n_frames, height, width), dtype=np.float32)
     W = np.zeros((n_frames, height, width), dtype=np.float32)

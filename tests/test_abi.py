@@ -41,8 +41,9 @@ def test_struct_layouts_match_header(binding, tmp_path):
 int main(void) {{
   printf("%zu %zu %zu %zu %zu\\n", sizeof(rgbid_intrinsics), sizeof(rgbid_level), sizeof(rgbid_pyramid),
          sizeof(rgbid_align_params), sizeof(rgbid_align_result));
-  printf("%zu %zu %zu %zu\\n", offsetof(rgbid_level, IW), offsetof(rgbid_align_params, nu0),
-         offsetof(rgbid_align_result, cost), offsetof(rgbid_align_result, status));
+  printf("%zu %zu %zu %zu %zu %zu %zu\\n", offsetof(rgbid_level, IW), offsetof(rgbid_align_params, nu0),
+         offsetof(rgbid_align_result, cost), offsetof(rgbid_align_result, status), sizeof(rgbid_timing),
+         offsetof(rgbid_timing, units), offsetof(rgbid_align_params, timing));
   return 0;
 }}''')
     exe = tmp_path / "abi"
@@ -53,7 +54,8 @@ int main(void) {{
     assert sizes[:5] == [ctypes.sizeof(b.Intrinsics), ctypes.sizeof(b.Level), ctypes.sizeof(b.Pyramid),
                          ctypes.sizeof(b.AlignParams), ctypes.sizeof(b.AlignResult)]
     assert sizes[5:] == [b.Level.IW.offset, b.AlignParams.nu0.offset, b.AlignResult.cost.offset,
-                         b.AlignResult.status.offset]
+                         b.AlignResult.status.offset, ctypes.sizeof(b.Timing), b.Timing.units.offset,
+                         b.AlignParams.timing.offset]
 
 
 def test_host_side_calls_without_a_gpu(binding):

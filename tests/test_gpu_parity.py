@@ -225,3 +225,49 @@ def test_pose_helpers_on_device():
     R.rgbid_compose_pose(a, True, b, out)
     torch.cuda.synchronize()
     assert np.allclose(out.cpu().numpy().reshape(4, 4), O.se3_inv(T1) @ T2, atol=1e-14)
+
+
+# ----------------------------------------------------------------------------- sequence
+def test_tracking_sequence_prefix_matches_oracle():
+    """Device-resident tracking front-end (constant-velocity guess, alignment,
+    fusion, keyframe switch at frame 20) against the oracle's, frame by frame."""
+    from paper_1807_08271_gb300.tracker import Tracker
+    n = 23
+    seq = synth.render_sequence(0, n_frames=n)
+    I_all = torch.from_numpy(seq["I"]).cuda()
+    W_all = torch.from_numpy(seq["W"]).cuda()
+    trk = Tracker(640, 480, seq["K"], levels=4, iters=(5, 5, 5, 10), kf_every=20, max_frames=n)
+    for k in range(n):
+        trk.step(I_all[k], W_all[k])
+    torch.cuda.synchronize()
+    gT = trk.trajectory()
+    o = O.track_sequence(seq["I"], seq["W"], seq["K"], levels=4, iters=(5, 5, 5, 10), kf_every=20)
+    for k in range(1, n):
+        er, et = pose_error(gT[k], o["T_world"][k])
+        assert er <= POSE_TOL and et <= POSE_TOL, (k, er, et)
+    truth = [np.linalg.inv(seq["T_wc"][0]) @ seq["T_wc"][k] for k in range(n)]
+    assert max(pose_error(gT[k], truth[k])[0] for k in range(n)) < 2e-3
+    # the fused keyframe (frame 20 onwards) matches too
+    Ig, Wg, Cg = trk.I_kf.cpu().numpy(), trk.W_kf.cpu().numpy(), trk.C_kf.cpu().numpy()
+    Io, Wo, Co = o["keyframe"]
+    both = (Cg > 1) & (Co > 1)
+    assert both.sum() > 0.5 * (Wo > 0).sum()
+    assert np.allclose(Wg[both], Wo[both], rtol=1e-4)
+    assert np.allclose(Ig[both], Io[both], atol=1e-4)
+
+
+def test_tracking_full_sequence_stays_on_ground_truth():
+    """300 frames of the benchmark sequence: every frame's pose stays close to the
+    ground truth (no drift from the constant-velocity composition)."""
+    from paper_1807_08271_gb300.tracker import Tracker
+    seq = synth.render_sequence(0, n_frames=300)
+    I_all = torch.from_numpy(seq["I"]).cuda()
+    W_all = torch.from_numpy(seq["W"]).cuda()
+    trk = Tracker(640, 480, seq["K"], levels=4, iters=(5, 5, 5, 10), kf_every=20, max_frames=300)
+    for k in range(300):
+        trk.step(I_all[k], W_all[k])
+    torch.cuda.synchronize()
+    gT = trk.trajectory()
+    errs = [pose_error(gT[k], np.linalg.inv(seq["T_wc"][0]) @ seq["T_wc"][k]) for k in range(1, 300)]
+    assert max(e[0] for e in errs) < 5e-3 and max(e[1] for e in errs) < 2e-2
+    assert all(r["status"] == R.OK for r in trk.frame_results())

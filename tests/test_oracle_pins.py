@@ -452,3 +452,32 @@ def test_fusion_of_equal_weight_frames_is_the_arithmetic_mean():
     assert np.allclose(W[every], np.mean(np.stack(Ws), 0)[every], rtol=1e-12)
     assert np.allclose(I[every], np.mean(np.stack(Is), 0)[every], rtol=1e-12)
     assert np.array_equal(C[every], np.full(every.sum(), 6.0))
+
+
+def test_so3_projection_is_nearest_rotation():
+    rng = np.random.default_rng(21)
+    R0 = synth.random_rotation(rng)
+    assert np.allclose(O.so3_project(R0), R0, atol=1e-14)          # rotations are fixed points
+    E = 1e-4 * rng.normal(size=(3, 3))
+    P = O.so3_project(R0 + E)
+    assert np.allclose(P.T @ P, np.eye(3), atol=1e-14) and abs(np.linalg.det(P) - 1) < 1e-14
+    # nearest in Frobenius norm: no random rotation near R0 is closer
+    for _ in range(50):
+        Q = R0 @ O.so3_exp(1e-4 * rng.normal(size=3))
+        assert np.linalg.norm(R0 + E - P) <= np.linalg.norm(R0 + E - Q) + 1e-15
+
+
+def test_constant_velocity_drift_is_removed_by_projection():
+    """Without re-projection the rotation drift of T1 T2^-1 T1 grows ~2.4x per frame."""
+    T2 = np.eye(4)
+    T1 = O.se3_exp([0.01, 0, 0, 0, 0.01, 0])
+    T1[:3, :3] *= 1 + 1e-12                                         # rounding-sized drift
+    free, proj = (T1.copy(), T2.copy()), (T1.copy(), T2.copy())
+    for _ in range(30):
+        a, b = free
+        free = (a @ O.se3_inv(b) @ a, a)
+        a, b = proj
+        proj = (O.se3_project(a @ O.se3_inv(b) @ a), a)
+    orth = lambda T: np.abs(T[:3, :3].T @ T[:3, :3] - np.eye(3)).max()
+    assert orth(free[0]) > 1e-3
+    assert orth(proj[0]) < 1e-14
