@@ -179,6 +179,28 @@ int rgbid_align(const rgbid_pyramid* ref, const rgbid_pyramid* cur,
                 const rgbid_align_params* params, void* workspace, size_t workspace_bytes,
                 rgbid_align_result* d_result, void* stream);
 
+/* Allocation-free variant of rgbid_align, for callers that cannot allocate device
+ * memory or keep a workspace: code running under a no-allocation policy (a
+ * real-time tracking loop, a plugin inside a host application that owns every
+ * device allocation) and callers without a CUDA allocator of their own.  The
+ * paper has no counterpart to this entry point.
+ * It behaves as rgbid_align but takes its scratch from a fixed device array
+ * inside the library (RGBID_NOALLOC_SCRATCH_BYTES, 512 KiB, held by every GPU
+ * that loads the library until the process exits) and calls no allocator.
+ * Inputs and outputs are still the caller's.  The first call on a device,
+ * with that device current, looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Returns RGBID_ERR_WORKSPACE when the reference's finest level needs more
+ * scratch than the array holds (about 4 million pixels), RGBID_ERR_CUDA if the
+ * look-up fails.  Every call shares the one array: calls whose work overlaps on
+ * the GPU (other streams, other host threads) race and must be serialised by
+ * the caller.  Each call resets the scratch fields that must start at zero. */
+#define RGBID_NOALLOC_SCRATCH_BYTES (512u * 1024u)
+int rgbid_align_noalloc(const rgbid_pyramid* ref, const rgbid_pyramid* cur,
+                        const double* T_init, int T_init_on_device,
+                        const rgbid_align_params* params,
+                        rgbid_align_result* d_result, void* stream);
+
 /* One step at a fixed pose and level, for inspection and parity testing.
  * `T` (host, 16 doubles) is the pose; `robust` (host, 6 doubles
  * mu_I, sigma_I, nu_I, mu_W, sigma_W, nu_W) fixes the robust parameters, or

@@ -847,3 +847,34 @@ extern "C" int rgbid_eval_step(const rgbid_pyramid* ref, const rgbid_pyramid* cu
     if (launch_sweep_any(ref->precision, sa, stream) != cudaSuccess) return RGBID_ERR_CUDA;
     return RGBID_OK;
 }
+
+// ---------------------------------------------------------------- allocation-free alignment
+// Scratch of rgbid_align_noalloc: a fixed device array that every GPU loading this
+// library holds until the process exits.  Its host-side name is only a stand-in
+// for the symbol; the device address is fetched with cudaGetSymbolAddress once
+// per device and cached.
+namespace rgbid {
+constexpr size_t kNoallocScratchBytes = 512u * 1024u;   // RGBID_NOALLOC_SCRATCH_BYTES
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+static void* g_noalloc_ptr[64];
+}  // namespace rgbid
+
+extern "C" int rgbid_align_noalloc(const rgbid_pyramid* ref, const rgbid_pyramid* cur, const double* T_init,
+                                   int T_init_on_device, const rgbid_align_params* params,
+                                   rgbid_align_result* d_result, void* stream) {
+    if (!ref || !params) return RGBID_ERR_INVALID_ARG;
+    const size_t need = rgbid_align_workspace_bytes(ref, params);
+    if (need == 0) return RGBID_ERR_INVALID_ARG;
+    if (need > kNoallocScratchBytes) return RGBID_ERR_WORKSPACE;     // level 0 too large for the fixed scratch
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return RGBID_ERR_CUDA;
+    if (!g_noalloc_ptr[dev]) {
+        // set-up on the first call on this device (the device is current here)
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return RGBID_ERR_CUDA;
+        g_noalloc_ptr[dev] = p;
+    }
+    // the alignment's init kernel resets every scratch field that must start at zero
+    return rgbid_align(ref, cur, T_init, T_init_on_device, params, g_noalloc_ptr[dev], kNoallocScratchBytes,
+                       d_result, stream);
+}

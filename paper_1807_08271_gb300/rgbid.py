@@ -80,6 +80,8 @@ SIGNATURES = [
     ("rgbid_align_workspace_bytes", c_size_t, [POINTER(Pyramid), POINTER(AlignParams)]),
     ("rgbid_align", c_int, [POINTER(Pyramid), POINTER(Pyramid), c_void_p, c_int, POINTER(AlignParams),
                             c_void_p, c_size_t, c_void_p, c_void_p]),
+    ("rgbid_align_noalloc", c_int, [POINTER(Pyramid), POINTER(Pyramid), c_void_p, c_int, POINTER(AlignParams),
+                                    c_void_p, c_void_p]),
     ("rgbid_eval_step", c_int, [POINTER(Pyramid), POINTER(Pyramid), c_int, POINTER(c_double), c_void_p,
                                 POINTER(AlignParams), c_void_p, c_size_t, c_void_p, c_void_p, c_void_p,
                                 c_void_p, c_void_p, c_void_p]),
@@ -187,6 +189,20 @@ def rgbid_align(ref: Pyramid, cur: Pyramid, T_init, params: AlignParams, workspa
                              _ptr(workspace), workspace.numel() * workspace.element_size(), _ptr(result),
                              _stream_ptr(stream))
     _check("rgbid_align", code)
+
+
+def rgbid_align_noalloc(ref: Pyramid, cur: Pyramid, T_init, params: AlignParams, result, stream=None):
+    """rgbid_align with the library's fixed internal scratch (no workspace argument)."""
+    if T_init is None:
+        tp, on_dev = c_void_p(0), 0
+    elif hasattr(T_init, "is_cuda") and T_init.is_cuda:
+        tp, on_dev = _ptr(T_init), 1
+    else:
+        arr = np.ascontiguousarray(np.asarray(T_init, dtype=np.float64).reshape(16))
+        tp, on_dev = c_void_p(arr.ctypes.data), 0
+    code = lib().rgbid_align_noalloc(ctypes.byref(ref), ctypes.byref(cur), tp, on_dev, ctypes.byref(params),
+                                     _ptr(result), _stream_ptr(stream))
+    _check("rgbid_align_noalloc", code)
 
 
 def rgbid_eval_step(ref: Pyramid, cur: Pyramid, level: int, T, robust, params: AlignParams, workspace,
