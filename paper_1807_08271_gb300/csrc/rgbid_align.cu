@@ -107,18 +107,79 @@ __device__ __forceinline__ F2 shfl_f2(const F2& v, int off) {
     return F2{__shfl_xor_sync(0xffffffffu, v.hi, off), __shfl_xor_sync(0xffffffffu, v.lo, off)};
 }
 
+// ---- distributed-shared-memory exchange (push model)
+// Each CTA sends its compensated partials to every CTA of the cluster with
+// st.async, which completes transaction bytes on the receiver's mbarrier; a
+// receiver waits only on its own barrier, so no cluster-wide barrier is needed
+// per round.  Two receive buffers and two barriers alternate between rounds: a
+// CTA cannot send round k+2 before it holds round k+1 from every CTA, which
+// each CTA sends only after it has consumed round k.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint32_t map_to_rank(uint32_t addr, uint32_t rank) {
+    uint32_t out;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(out) : "r"(addr), "r"(rank));
+    return out;
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n"
+        " mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void st_async_f2(uint32_t remote_addr, float a, float b, uint32_t remote_bar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];" ::"r"(
+                     remote_addr),
+                 "f"(a), "f"(b), "r"(remote_bar)
+                 : "memory");
+}
+
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialisation may start while its predecessor is still running; it must wait
+// (griddepcontrol.wait) before reading anything the predecessor writes, and it
+// lets its own successor start early with griddepcontrol.launch_dependents.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+constexpr long long kWaitBudgetCycles = 4000000000LL;   // ~2 s: a wait that exceeds it reports a timeout
+
 template <int CL>
 struct ClusterSum {
-    float (*red_w)[kRobustMaxNV];     // per-warp partials [8][NV]
-    float2 (*red_cta)[kRobustMaxNV];  // per-CTA compensated partials, double-buffered [2][NV]
-    float* out;                       // [NV] cluster totals
-    int buf;
+    float (*red_w)[kRobustMaxNV];             // per-warp partials [8][NV]
+    float2 (*recv)[CL][kRobustMaxNV];         // receive buffers [2][CL][NV]
+    float* out;                               // [NV] cluster totals
+    unsigned long long* mbar;                 // [2]
+    int* timeouts;                            // device counter of expired waits
+    uint32_t rank;
+    int round;
 
-    // v: per-thread partials of NV values (NV <= 8: one per warp-sum; NV = 96: three
-    // reduce-scatter chunks).  On return out[0..NV) holds the cluster totals.
+    // v: per-thread partials of NV values (NV <= 8: one warp sum each; NV = 96: three
+    // reduce-scatter chunks).  On return out[0..NV) holds the cluster totals,
+    // bit-identical in every CTA (same data, same combine order).
     template <int NV>
-    __device__ __forceinline__ void run(cg::cluster_group& cl, float (&v)[NV]) {
+    __device__ __forceinline__ void run(float (&v)[NV]) {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const int par = round & 1;
+        const uint32_t phase = (uint32_t)(round >> 1) & 1u;
+        if (threadIdx.x == 0) mbar_arrive_expect_tx(&mbar[par], (uint32_t)(CL * NV * sizeof(float2)));
         if constexpr (NV <= 8) {
 #pragma unroll
             for (int j = 0; j < NV; ++j) {
@@ -136,28 +197,37 @@ struct ClusterSum {
             }
         }
         __syncthreads();
-        // CTA level: warp w combines values j = w, w + 8, ... over the 8 warps (lanes 0..7)
-        for (int j = warp; j < NV; j += kRobustNT / 32) {
-            F2 t{lane < kRobustNT / 32 ? red_w[lane & 7][j] : 0.f, 0.f};
+        const int t = threadIdx.x;
+        if (t < NV) {
+            F2 s{0.f, 0.f};
 #pragma unroll
-            for (int off = 1; off < kRobustNT / 32; off <<= 1) t.add(shfl_f2(t, off));
-            if (lane == 0) red_cta[buf][j] = make_float2(t.hi, t.lo);
-        }
-        cl.sync();
-        // cluster level: lane r < CL reads CTA r's pair; a shuffle tree combines them
-        for (int j = warp; j < NV; j += kRobustNT / 32) {
-            F2 t{0.f, 0.f};
-            if (lane < CL) {
-                const float2* rem = cl.map_shared_rank(&red_cta[buf][0], lane);
-                const float2 p = rem[j];
-                t = F2{p.x, p.y};
+            for (int w = 0; w < kRobustNT / 32; ++w) s.add(red_w[w][t]);
+            const uint32_t src = smem_addr(&recv[par][rank][t]);
+            const uint32_t bar = smem_addr(&mbar[par]);
+#pragma unroll
+            for (int r = 0; r < CL; ++r) st_async_f2(map_to_rank(src, r), s.hi, s.lo, map_to_rank(bar, r));
+            const long long t0 = clock64();
+            while (!mbar_try_wait(&mbar[par], phase)) {
+                if (clock64() - t0 > kWaitBudgetCycles) {
+                    atomicAdd(timeouts, 1);
+                    break;
+                }
+            }
+            // fixed pairwise tree over the CL source CTAs
+            F2 acc[CL];
+#pragma unroll
+            for (int r = 0; r < CL; ++r) {
+                const float2 p = recv[par][r][t];
+                acc[r] = F2{p.x, p.y};
             }
 #pragma unroll
-            for (int off = 1; off < CL; off <<= 1) t.add(shfl_f2(t, off));
-            if (lane == 0) out[j] = t.value();
+            for (int step = 1; step < CL; step <<= 1)
+#pragma unroll
+                for (int r = 0; r + step < CL; r += 2 * step) acc[r].add(acc[r + step]);
+            out[t] = acc[0].value();
         }
         __syncthreads();
-        buf ^= 1;
+        ++round;
     }
 };
 
@@ -197,31 +267,26 @@ __device__ __forceinline__ float nu_const_f(float nu) {
 constexpr int kChebK = 20;
 constexpr int kChebVals = 2 * kChebK + 2;      // SL, P_1..P_K, G_0..G_K per channel
 
-struct ChebSums {
-    float n, SL, P[kChebK + 1], G[kChebK + 1];   // P[0] unused
-};
-
-// f(nu) from the Chebyshev sums (FP32, Clenshaw).
-__device__ __forceinline__ float nu_equation_cheb(const ChebSums& S, float nu, float m, float h) {
-    const float tau = (nu - m) / h;
+// f(nu) from the Chebyshev coefficients (FP32 Clenshaw): ca[k] = 2 (-1)^(k+1) P_k / k,
+// cb[k] = 2 (-1)^k G_k for k >= 1, so that sum_i ln(alpha_i + tau) = SL + sum_k ca_k T_k(tau)
+// and sum_i 1/(alpha_i + tau) = G_0 + sum_k cb_k T_k(tau).
+__device__ __forceinline__ float nu_equation_cheb(const float* ca, const float* cb, float G0, float n, float SL,
+                                                  float nu, float m, float invh, float lnh) {
+    const float tau = (nu - m) * invh;
     const float t2 = 2.f * tau;
-    // A(tau) = sum_k a_k T_k, a_k = 2 (-1)^(k+1) P_k / k ; B(tau) = G_0 + sum_k b_k T_k, b_k = 2 (-1)^k G_k
     float a1 = 0.f, a2 = 0.f, b1 = 0.f, b2 = 0.f;
 #pragma unroll
     for (int k = kChebK; k >= 1; --k) {
-        const float sgn = (k & 1) ? 1.f : -1.f;
-        const float ak = sgn * 2.f * S.P[k] / (float)k;
-        const float bk = -sgn * 2.f * S.G[k];
-        const float an = fmaf(t2, a1, ak - a2);
-        const float bn = fmaf(t2, b1, bk - b2);
+        const float an = fmaf(t2, a1, ca[k] - a2);
+        const float bn = fmaf(t2, b1, cb[k] - b2);
         a2 = a1; a1 = an;
         b2 = b1; b1 = bn;
     }
     const float A = fmaf(tau, a1, -a2);            // Clenshaw end with c_0 = 0
-    const float B = fmaf(tau, b1, S.G[0] - b2);
+    const float B = fmaf(tau, b1, G0 - b2);
     // f = n [c(nu) + ln(nu + 1) - ln h] - SL - A - (nu + 1) B / h
-    const float base = S.n * (nu_const_f(nu) + logf(nu + 1.f) - logf(h)) - S.SL;
-    return base - A - (nu + 1.f) * B / h;
+    const float base = n * (nu_const_f(nu) + logf(nu + 1.f) - lnh) - SL;
+    return base - A - (nu + 1.f) * B * invh;
 }
 
 template <int PREC, int CL>
@@ -230,32 +295,62 @@ __global__ void __launch_bounds__(kRobustNT) robust_kernel(RobustArgs a) {
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     __shared__ float red_w[kRobustNT / 32][kRobustMaxNV];
-    __shared__ float2 red_cta[2][kRobustMaxNV];
+    __shared__ float2 recv[2][CL][kRobustMaxNV];
     __shared__ float tot[kRobustMaxNV];
+    __shared__ __align__(8) unsigned long long mbar[2];
     __shared__ WarpPose sh_wp;
     __shared__ float nu_out[2];
-    if (threadIdx.x == 0) sh_wp = a.st->wp;
+    __shared__ float cheb[2][2][kChebK + 1];     // per channel: Clenshaw coefficients a_k, b_k
+    __shared__ unsigned bis_mask[2][4];
+    __shared__ int bis_end[2][2];
+    if (threadIdx.x == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    cl.sync();   // every barrier of the cluster is initialised before any remote store
+    pdl_wait();  // the previous iteration's pose update is complete and visible
+    pdl_trigger();
+    if (threadIdx.x < 16) reinterpret_cast<float*>(&sh_wp)[threadIdx.x] = __ldcg(reinterpret_cast<const float*>(&a.st->wp) + threadIdx.x);
     __syncthreads();
     const WarpPose wp = sh_wp;
 
-    // ---- systematic sample residuals r(p, 0) (NaN = masked out)
+    // ---- systematic sample residuals r(p, 0) (NaN = masked out); the samples of a
+    //      thread go through each evaluation stage together so their loads overlap
     float rs[2][MAXS];
-    const int gt = rank * kRobustNT + (int)threadIdx.x;
+    {
+        const int gt = rank * kRobustNT + (int)threadIdx.x;
+        PxA sa[MAXS];
+        PxW sw[MAXS];
+        PxB sb[MAXS];
+        int su[MAXS], sv[MAXS];
 #pragma unroll
-    for (int k = 0; k < MAXS; ++k) {
-        const int i = gt + k * (CL * kRobustNT);
-        rs[0][k] = __int_as_float(0x7fc00000);
-        rs[1][k] = __int_as_float(0x7fc00000);
-        if (i < a.nsamp) {
-            const int sy = i / a.nsx, sx = i - sy * a.nsx;
+        for (int k = 0; k < MAXS; ++k) {
+            const int i = gt + k * (CL * kRobustNT);
+            sa[k].ok = false;
+            su[k] = 0;
+            sv[k] = 0;
+            if (i < a.nsamp) {
+                const int sy = i / a.nsx, sx = i - sy * a.nsx;
+                su[k] = sx * a.s;
+                sv[k] = sy * a.s;
+                stage_a<PREC>(a.A, su[k], sv[k], sa[k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < MAXS; ++k) stage_w(a.A, a.B, wp, su[k], sv[k], sa[k], sw[k]);
+#pragma unroll
+        for (int k = 0; k < MAXS; ++k) stage_b<PREC>(a.B, sw[k], sb[k]);
+#pragma unroll
+        for (int k = 0; k < MAXS; ++k) {
             PixelTerms o;
-            eval_pixel<PREC, false>(a.A, a.B, wp, sx * a.s, sy * a.s, o);
-            if (o.mI) rs[0][k] = o.rI;
-            if (o.mW) rs[1][k] = o.rW;
+            finish<false>(a.A, wp, sa[k], sw[k], sb[k], o);
+            rs[0][k] = o.mI ? o.rI : __int_as_float(0x7fc00000);
+            rs[1][k] = o.mW ? o.rW : __int_as_float(0x7fc00000);
         }
     }
 
-    ClusterSum<CL> R{red_w, red_cta, tot, 0};
+    ClusterSum<CL> R{red_w, recv, tot, mbar, &a.st->timeouts, (uint32_t)rank, 0};
     // ---- counts and mean square -> sigma0 (mu0 = 0)
     {
         float v4[4] = {0.f, 0.f, 0.f, 0.f};
@@ -267,7 +362,7 @@ __global__ void __launch_bounds__(kRobustNT) robust_kernel(RobustArgs a) {
                 if (r == r) { v4[2 * c] += 1.f; v4[2 * c + 1] = fmaf(r, r, v4[2 * c + 1]); }
             }
         }
-        R.run(cl, v4);
+        R.run(v4);
     }
     const float n[2] = {tot[0], tot[2]};
     float mu[2] = {0.f, 0.f};
@@ -275,7 +370,8 @@ __global__ void __launch_bounds__(kRobustNT) robust_kernel(RobustArgs a) {
     bool live[2];
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
-        sig[c] = n[c] > 0.f ? sqrtf(tot[2 * c + 1] / n[c]) : 0.f;
+        const float ms = n[c] > 0.f ? __fdividef(tot[2 * c + 1], n[c]) : 0.f;
+        sig[c] = ms > 0.f ? ms * rsqrtf(ms) : 0.f;
         live[c] = n[c] > 0.f && sig[c] >= 1e-12f;
     }
 
@@ -304,15 +400,15 @@ __global__ void __launch_bounds__(kRobustNT) robust_kernel(RobustArgs a) {
                 }
             }
         }
-        R.run(cl, v6);
+        R.run(v6);
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
             if (!live[c]) continue;
             const float S0 = tot[3 * c], S1 = tot[3 * c + 1], S2 = tot[3 * c + 2];
-            const float delta = S1 / S0;
+            const float delta = __fdividef(S1, S0);
             mu[c] += delta;
-            const float var = fmaf(-S1, delta, S2) / n[c];
-            sig[c] = var > 0.f ? sqrtf(var) : 0.f;
+            const float var = __fdividef(fmaf(-S1, delta, S2), n[c]);
+            sig[c] = var > 0.f ? var * rsqrtf(var) : 0.f;
             if (!(sig[c] >= 1e-12f)) live[c] = false;
         }
     }
@@ -332,7 +428,7 @@ __global__ void __launch_bounds__(kRobustNT) robust_kernel(RobustArgs a) {
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
             if (!ok[c]) continue;
-            const float is = 1.f / sig[c];
+            const float is = __fdividef(1.f, sig[c]);
 #pragma unroll
             for (int k = 0; k < MAXS; ++k) {
                 const float x = (rs[c][k] - mu[c]) * is;
@@ -355,56 +451,71 @@ __global__ void __launch_bounds__(kRobustNT) robust_kernel(RobustArgs a) {
                 }
             }
         }
-        R.run(cl, v);
+        R.run(v);
     }
     cl.sync();   // every remote read of this CTA's shared memory is complete
     if (rank != 0) return;
 
-    if (do_nu && threadIdx.x < 64) {
-        // warp c solves channel c: endpoint tests, then 31-point sections that
-        // replay 5 bisection halvings each (same midpoints, same decisions)
-        const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (do_nu) {
+        // threads [128 c, 128 c + 128) solve channel c.  The first section evaluates
+        // f(hi), f(lo) and 63 interior points (6 halvings), later sections 127
+        // points (7 halvings); each replays exactly the bisection's decisions
+        // at the same dyadic midpoints.
+        const int c = threadIdx.x >> 7, lt = threadIdx.x & 127, lane = threadIdx.x & 31;
+        const int gw = lt >> 5;                      // warp within the channel group
         float nuc = nu0;
         if (ok[c]) {
-            ChebSums S;
-            S.n = n[c];
-            S.SL = tot[c * kChebVals];
-            S.P[0] = 0.f;
-#pragma unroll
-            for (int k = 1; k <= kChebK; ++k) S.P[k] = tot[c * kChebVals + k];
-#pragma unroll
-            for (int k = 0; k <= kChebK; ++k) S.G[k] = tot[c * kChebVals + 1 + kChebK + k];
-            const float fend = nu_equation_cheb(S, lane == 0 ? hi0 : lo0, m, h);
-            const float fhi = __shfl_sync(0xffffffffu, fend, 0);
-            const float flo = __shfl_sync(0xffffffffu, fend, 1);
-            if (fhi >= 0.f) {
-                nuc = hi0;
-            } else if (flo <= 0.f) {
-                nuc = lo0;
-            } else {
-                float lo = lo0, hi = hi0;
-                int left = a.bisect_steps;
-                while (left > 0) {
-                    const int st = left < 5 ? left : 5;
-                    const int np = 1 << st;             // sub-intervals this round
-                    const float step = (hi - lo) / (float)np;
-                    const float xj = fmaf((float)(lane + 1), step, lo);
-                    const float fj = (lane + 1 < np) ? nu_equation_cheb(S, xj, m, h) : 0.f;
-                    const unsigned pos = __ballot_sync(0xffffffffu, (lane + 1 < np) && fj > 0.f);
+            const float* T = tot + c * kChebVals;       // SL, P_1..P_K, G_0..G_K
+            if (lt >= 1 && lt <= kChebK) {
+                const float sgn = (lt & 1) ? 2.f : -2.f;
+                cheb[c][0][lt] = sgn * __fdividef(T[lt], (float)lt);
+                cheb[c][1][lt] = -sgn * T[1 + kChebK + lt];
+            }
+            asm volatile("bar.sync %0, 128;" ::"r"(1 + c) : "memory");
+            const float* ca = cheb[c][0];
+            const float* cb = cheb[c][1];
+            const float G0 = T[1 + kChebK], SL = T[0], nc = n[c];
+            const float invh = 1.f / h, lnh = logf(h);
+            float lo = lo0, hi = hi0;
+            int left = a.bisect_steps;
+            bool first = true, done = false;
+            while (!done) {
+                const int st = left < (first ? 6 : 7) ? left : (first ? 6 : 7);
+                const int np = 1 << st;                  // sub-intervals this round
+                const int off = first ? 2 : 0;           // lanes 0, 1 take the endpoints first
+                const float step = (hi - lo) / (float)np;
+                const int j = lt - off + 1;              // interior point index of this lane
+                float x = 0.f;
+                bool eval = false;
+                if (first && lt == 0) { x = hi; eval = true; }
+                else if (first && lt == 1) { x = lo; eval = true; }
+                else if (j >= 1 && j < np) { x = fmaf((float)j, step, lo); eval = true; }
+                const float f = eval ? nu_equation_cheb(ca, cb, G0, nc, SL, x, m, invh, lnh) : 0.f;
+                const unsigned pos = __ballot_sync(0xffffffffu, eval && f > 0.f);
+                if (lane == 0) bis_mask[c][gw] = pos;
+                if (first && lt == 0) bis_end[c][0] = (f >= 0.f) ? 1 : 0;   // f(hi) >= 0
+                if (first && lt == 1) bis_end[c][1] = (f <= 0.f) ? 1 : 0;   // f(lo) <= 0
+                asm volatile("bar.sync %0, 128;" ::"r"(1 + c) : "memory");
+                if (first && bis_end[c][0]) { nuc = hi0; done = true; }
+                else if (first && bis_end[c][1]) { nuc = lo0; done = true; }
+                else {
                     int jl = 0, jh = np;
-                    for (int s = 0; s < st; ++s) {
+                    for (int q = 0; q < st; ++q) {
                         const int jm = (jl + jh) >> 1;
-                        if ((pos >> (jm - 1)) & 1u) jl = jm; else jh = jm;
+                        const int L = jm - 1 + off;
+                        if ((bis_mask[c][L >> 5] >> (L & 31)) & 1u) jl = jm; else jh = jm;
                     }
                     const float nlo = fmaf((float)jl, step, lo), nhi = fmaf((float)jh, step, lo);
                     lo = nlo;
                     hi = nhi;
                     left -= st;
+                    first = false;
+                    if (left == 0) { nuc = 0.5f * (lo + hi); done = true; }
                 }
-                nuc = 0.5f * (lo + hi);
+                asm volatile("bar.sync %0, 128;" ::"r"(1 + c) : "memory");   // masks are reused next round
             }
         }
-        if (lane == 0) nu_out[c] = nuc;
+        if (lt == 0) nu_out[c] = nuc;
     }
     __syncthreads();
     if (do_nu) {
@@ -441,14 +552,20 @@ __device__ __forceinline__ void accumulate(float (&acc)[kSlots], const float (&J
 }
 
 template <int PREC>
-__global__ void __launch_bounds__(kSweepNT) sweep_kernel(SweepArgs a) {
+__global__ void __launch_bounds__(kSweepNT, 2) sweep_kernel(SweepArgs a) {
     __shared__ float red[kSweepNT / 32][kSlots];
     __shared__ F2 fin[kSweepNT / 32][kSlots];
     __shared__ float tot[kSlots];
     __shared__ bool am_last;
     __shared__ WarpPose sh_wp;
     __shared__ RobustParams sh_rob;
-    if (threadIdx.x == 0) { sh_wp = a.st->wp; sh_rob = a.st->rob; }
+    pdl_wait();   // the robust parameters (and pose) of this iteration are complete and visible
+    if (threadIdx.x < 16) {
+        reinterpret_cast<float*>(&sh_wp)[threadIdx.x] = __ldcg(reinterpret_cast<const float*>(&a.st->wp) + threadIdx.x);
+    } else if (threadIdx.x < 16 + (int)(sizeof(RobustParams) / 4)) {
+        const int q = threadIdx.x - 16;
+        reinterpret_cast<int*>(&sh_rob)[q] = __ldcg(reinterpret_cast<const int*>(&a.st->rob) + q);
+    }
     __syncthreads();
     const WarpPose wp = sh_wp;
     const RobustParams rob = sh_rob;
@@ -460,12 +577,29 @@ __global__ void __launch_bounds__(kSweepNT) sweep_kernel(SweepArgs a) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int u = blockIdx.x * kTileW + lane;
     const bool wantI = rob.ok[0] != 0, wantW = rob.ok[1] != 0;
-#pragma unroll 1
-    for (int r = 0; r < kSweepRowsPerWarp; ++r) {
-        const int v = blockIdx.y * kTileH + warp * kSweepRowsPerWarp + r;
+    // the thread's rows go through each stage together, so the loads of a stage
+    // for all rows are in flight at once
+    constexpr int R = kSweepRowsPerWarp;
+    const int v0 = blockIdx.y * kTileH + warp * R;
+    PxA sa[R];
+    PxW sw[R];
+    PxB sb[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int v = v0 + r;
+        sa[r].ok = false;
+        if (u < a.A.w && v < a.A.h) stage_a<PREC>(a.A, u, v, sa[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) stage_w(a.A, a.B, wp, u, v0 + r, sa[r], sw[r]);
+#pragma unroll
+    for (int r = 0; r < R; ++r) stage_b<PREC>(a.B, sw[r], sb[r]);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int v = v0 + r;
         if (u >= a.A.w || v >= a.A.h) continue;
         PixelTerms o;
-        eval_pixel<PREC, true>(a.A, a.B, wp, u, v, o);
+        finish<true>(a.A, wp, sa[r], sw[r], sb[r], o);
         if (a.r_I) {
             const int oi = v * a.A.w + u;
             a.r_I[oi] = o.mI ? o.rI : 0.f;
@@ -503,9 +637,13 @@ __global__ void __launch_bounds__(kSweepNT) sweep_kernel(SweepArgs a) {
     }
     __syncthreads();
     if (!am_last) return;
+    pdl_trigger();   // the next kernel may launch now; it waits for this grid to finish
     __threadfence();
 
     // ---- last block: fixed-order compensated sum of the block partials
+    __shared__ double T_sh[16];
+    __shared__ WarpPose wp_new;
+    if (threadIdx.x < 16) T_sh[threadIdx.x] = __ldcg(a.st->T + threadIdx.x);   // overlaps the partial loads
     {
         // warp w sums blocks w, w + 8, ...; loads are issued in batches of 24 so
         // that their L2 latencies overlap
@@ -515,12 +653,12 @@ __global__ void __launch_bounds__(kSweepNT) sweep_kernel(SweepArgs a) {
         for (int b0 = warp; b0 < nblocks; b0 += kBatch * kStride) {
             float vals[kBatch];
 #pragma unroll
-            for (int u = 0; u < kBatch; ++u) {
-                const int b = b0 + u * kStride;
-                vals[u] = b < nblocks ? __ldcg(a.partials + (size_t)b * kSlots + lane) : 0.f;
+            for (int q = 0; q < kBatch; ++q) {
+                const int b = b0 + q * kStride;
+                vals[q] = b < nblocks ? __ldcg(a.partials + (size_t)b * kSlots + lane) : 0.f;
             }
 #pragma unroll
-            for (int u = 0; u < kBatch; ++u) acc2.add(vals[u]);
+            for (int q = 0; q < kBatch; ++q) acc2.add(vals[q]);
         }
         fin[warp][lane] = acc2;
     }
@@ -551,37 +689,49 @@ __global__ void __launch_bounds__(kSweepNT) sweep_kernel(SweepArgs a) {
         } else if (lane == kSlotNW) {
             res->n_valid[1] = (int)totf;
         } else if (lane == 30) {
-            res->mu[0] = st->rob.mu[0]; res->mu[1] = st->rob.mu[1];
-            res->sigma[0] = st->rob.sigma[0]; res->sigma[1] = st->rob.sigma[1];
-            res->nu[0] = st->rob.nu[0]; res->nu[1] = st->rob.nu[1];
+            res->mu[0] = rob.mu[0]; res->mu[1] = rob.mu[1];
+            res->sigma[0] = rob.sigma[0]; res->sigma[1] = rob.sigma[1];
+            res->nu[0] = rob.nu[0]; res->nu[1] = rob.nu[1];
         }
     }
     __syncwarp();
     if (lane == 0) st->counter = 0u;
     if (!a.update) return;
     __shared__ float xi_sh[6];
-    __shared__ int ok_sh;
-    if (lane == 0) {
-        float H[36], rhs[6], xi[6];
-        int s = 0;
-        for (int i = 0; i < 6; ++i)
-            for (int j = i; j < 6; ++j) { H[i * 6 + j] = tot[s]; H[j * 6 + i] = tot[s]; ++s; }
-        for (int i = 0; i < 6; ++i) rhs[i] = -tot[kSlotG + i];
-        const int nI = (int)tot[kSlotNI], nW = (int)tot[kSlotNW];
-        bool ok = (nI + nW) >= a.min_valid && cholesky_solve6_f(H, rhs, xi);
-        for (int i = 0; i < 6; ++i) xi_sh[i] = ok ? xi[i] : 0.f;
-        ok_sh = ok ? 1 : 0;
+    __shared__ float Hs[36], gs[6];
+    __shared__ int ok_flag;
+    if (lane < 21) {
+        int i = 0, rem = lane;
+        while (rem >= 6 - i) { rem -= 6 - i; ++i; }
+        const int j = i + rem;
+        Hs[i * 6 + j] = totf;
+        Hs[j * 6 + i] = totf;
+    } else if (lane < 27) {
+        gs[lane - kSlotG] = totf;
     }
     __syncwarp();
+    if (lane == 0) {
+        const int nI = (int)tot[kSlotNI], nW = (int)tot[kSlotNW];
+        float xi[6];
+        const bool okl = (nI + nW) >= a.min_valid && cholesky_solve6_packed(Hs, gs, xi);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) xi_sh[i] = okl ? xi[i] : 0.f;
+        ok_flag = okl ? 1 : 0;
+    }
+    __syncwarp();
+    const int ok_sh = ok_flag;
     const bool ok = ok_sh != 0;
     if (ok) {
         float xi[6];
+#pragma unroll
         for (int i = 0; i < 6; ++i) xi[i] = xi_sh[i];
-        warp_apply_update(xi, st->T);
-        warp_make_pose(st->T, &st->wp);
+        warp_apply_update(xi, T_sh);
+        warp_make_pose(T_sh, &wp_new);
+        __syncwarp();
+        if (lane < 16) reinterpret_cast<float*>(&st->wp)[lane] = reinterpret_cast<const float*>(&wp_new)[lane];
+        if (lane < 16) st->T[lane] = T_sh[lane];
     }
-    __syncwarp();
-    if (lane < 16) res->T[lane] = st->T[lane];
+    if (lane < 16) res->T[lane] = T_sh[lane];
     if (lane == 0) {
         if (!ok) {
             st->iters_skipped += 1;
@@ -590,7 +740,7 @@ __global__ void __launch_bounds__(kSweepNT) sweep_kernel(SweepArgs a) {
         st->iters_done += 1;
         res->iters_done = st->iters_done;
         res->iters_skipped = st->iters_skipped;
-        res->status = st->status;
+        res->status = st->timeouts ? RGBID_ERR_TIMEOUT : st->status;
     }
 }
 
@@ -658,13 +808,15 @@ static cudaError_t launch_robust_cl(const RobustArgs& ra, cudaStream_t stream) {
     cfg.blockDim = dim3(kRobustNT, 1, 1);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = stream;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = CL;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     return cudaLaunchKernelEx(&cfg, robust_kernel<PREC, CL>, ra);
 }
 
@@ -703,9 +855,17 @@ static cudaError_t launch_robust(const RobustArgs& ra, cudaStream_t stream) {
 
 template <int PREC>
 static cudaError_t launch_sweep(const SweepArgs& sa, cudaStream_t stream) {
-    dim3 grid((sa.A.w + kTileW - 1) / kTileW, (sa.A.h + kTileH - 1) / kTileH);
-    sweep_kernel<PREC><<<grid, kSweepNT, 0, stream>>>(sa);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((sa.A.w + kTileW - 1) / kTileW, (sa.A.h + kTileH - 1) / kTileH, 1);
+    cfg.blockDim = dim3(kSweepNT, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, sweep_kernel<PREC>, sa);
 }
 
 static cudaError_t launch_robust_any(int prec, const RobustArgs& ra, cudaStream_t s) {

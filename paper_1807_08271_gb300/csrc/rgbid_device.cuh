@@ -31,6 +31,8 @@ struct WarpPose {
     float tz;       // t_z
 };
 
+static_assert(sizeof(WarpPose) == 16 * sizeof(float), "copied as 16 floats");
+
 // Robust parameters consumed by the weights (per channel: mu, sigma^2 * nu, nu + 1, ok).
 struct RobustParams {
     float mu[2];
@@ -87,22 +89,49 @@ struct PixelTerms {
     bool mI, mW;         // masks
 };
 
-// Evaluate one pixel p = (u, v) of A: warp, residuals and (if WANT_J) Jacobians.
-// Follows eqs. 3d_registration, res_int, res_depth and DeltaX of the paper.
-template <int PREC, bool WANT_J>
-__device__ __forceinline__ void eval_pixel(const LevelDev& A, const LevelDev& B, const WarpPose& wp,
-                                           int u, int v, PixelTerms& o) {
-    o.mI = false;
-    o.mW = false;
-    o.rI = 0.f;
-    o.rW = 0.f;
-    if (u < 1 || v < 1 || u > A.w - 2 || v > A.h - 2) return;      // no central gradient on the border
+// Per-pixel evaluation in four stages so that a thread handling several pixels
+// can issue all loads of one stage before it needs their values:
+//   stage_a   load I_A, W_A at p and its 4-neighbours (central differences)
+//   stage_w   warp p into B (eq. 3d_registration, pixel-offset form)
+//   stage_b   load the four bilinear taps of B at p_B
+//   finish    residuals r(p, 0) (eqs. res_int, res_depth), Jacobians
+//             J = g [I | -[X_A]x] (eq. DeltaX) and the normal weight lambda_n.
+struct PxA {
+    float2 c, nl, nr, nu, nd;
+    float a, b;
+    bool ok;
+};
+
+struct PxW {
+    float du, dv, ax, ay;
+    int bi;
+    bool ok;
+};
+
+struct PxB {
+    float2 t00, t10, t01, t11;
+};
+
+template <int PREC>
+__device__ __forceinline__ void stage_a(const LevelDev& A, int u, int v, PxA& s) {
+    s.ok = !(u < 1 || v < 1 || u > A.w - 2 || v > A.h - 2);     // no central gradient on the border
+    if (!s.ok) return;
     const int idx = v * A.pitch + u;
-    const float2 c = Pix<PREC>::load(A.IW, idx);
-    const float WA = c.y;
-    if (!(WA > 0.f)) return;
-    const float a = ((float)u - A.cx) * A.ifx;
-    const float b = ((float)v - A.cy) * A.ify;
+    s.c = Pix<PREC>::load(A.IW, idx);
+    s.nl = Pix<PREC>::load(A.IW, idx - 1);
+    s.nr = Pix<PREC>::load(A.IW, idx + 1);
+    s.nu = Pix<PREC>::load(A.IW, idx - A.pitch);
+    s.nd = Pix<PREC>::load(A.IW, idx + A.pitch);
+    s.a = ((float)u - A.cx) * A.ifx;
+    s.b = ((float)v - A.cy) * A.ify;
+}
+
+__device__ __forceinline__ void stage_w(const LevelDev& A, const LevelDev& B, const WarpPose& wp, int u, int v,
+                                        const PxA& s, PxW& w) {
+    w.ok = false;
+    const float WA = s.c.y;
+    if (!s.ok || !(WA > 0.f)) return;
+    const float a = s.a, b = s.b;
     // d = (R^T - I) q - W_A R^T t
     const float dx = fmaf(wp.E[0], a, fmaf(wp.E[1], b, wp.E[2])) - WA * wp.s[0];
     const float dy = fmaf(wp.E[3], a, fmaf(wp.E[4], b, wp.E[5])) - WA * wp.s[1];
@@ -110,40 +139,52 @@ __device__ __forceinline__ void eval_pixel(const LevelDev& A, const LevelDev& B,
     const float mz = 1.f + dz;                       // Z_B * W_A
     if (!(mz > 0.f)) return;
     const float imz = 1.f / mz;
-    const float du = A.fx * fmaf(-a, dz, dx) * imz;  // u_B - u
-    const float dv = A.fy * fmaf(-b, dz, dy) * imz;  // v_B - v
-    const float fdu = floorf(du), fdv = floorf(dv);
+    w.du = A.fx * fmaf(-a, dz, dx) * imz;            // u_B - u
+    w.dv = A.fy * fmaf(-b, dz, dy) * imz;            // v_B - v
+    const float fdu = floorf(w.du), fdv = floorf(w.dv);
     if (!(fabsf(fdu) < 1.0e7f && fabsf(fdv) < 1.0e7f)) return;
     const int x0 = u + (int)fdu, y0 = v + (int)fdv;
     if (x0 < 0 || y0 < 0 || x0 > B.w - 2 || y0 > B.h - 2) return;
-    const float ax = du - fdu, ay = dv - fdv;
-    const int bi = y0 * B.pitch + x0;
-    const float2 t00 = Pix<PREC>::load(B.IW, bi);
-    const float2 t10 = Pix<PREC>::load(B.IW, bi + 1);
-    const float2 t01 = Pix<PREC>::load(B.IW, bi + B.pitch);
-    const float2 t11 = Pix<PREC>::load(B.IW, bi + B.pitch + 1);
-    const float itop = fmaf(ax, t10.x - t00.x, t00.x);
-    const float ibot = fmaf(ax, t11.x - t01.x, t01.x);
+    w.ax = w.du - fdu;
+    w.ay = w.dv - fdv;
+    w.bi = y0 * B.pitch + x0;
+    w.ok = true;
+}
+
+template <int PREC>
+__device__ __forceinline__ void stage_b(const LevelDev& B, const PxW& w, PxB& t) {
+    if (!w.ok) return;
+    t.t00 = Pix<PREC>::load(B.IW, w.bi);
+    t.t10 = Pix<PREC>::load(B.IW, w.bi + 1);
+    t.t01 = Pix<PREC>::load(B.IW, w.bi + B.pitch);
+    t.t11 = Pix<PREC>::load(B.IW, w.bi + B.pitch + 1);
+}
+
+template <bool WANT_J>
+__device__ __forceinline__ void finish(const LevelDev& A, const WarpPose& wp, const PxA& s, const PxW& w,
+                                       const PxB& t, PixelTerms& o) {
+    o.mI = false;
+    o.mW = false;
+    o.rI = 0.f;
+    o.rW = 0.f;
+    if (!w.ok) return;
+    const float WA = s.c.y, a = s.a, b = s.b, ax = w.ax, ay = w.ay;
+    const float itop = fmaf(ax, t.t10.x - t.t00.x, t.t00.x);
+    const float ibot = fmaf(ax, t.t11.x - t.t01.x, t.t01.x);
     const float IBw = fmaf(ay, ibot - itop, itop);
     o.mI = true;
-    o.rI = IBw - c.x;
-
-    // neighbours for central differences
-    const float2 nl = Pix<PREC>::load(A.IW, idx - 1);
-    const float2 nr = Pix<PREC>::load(A.IW, idx + 1);
-    const float2 nu = Pix<PREC>::load(A.IW, idx - A.pitch);
-    const float2 nd = Pix<PREC>::load(A.IW, idx + A.pitch);
+    o.rI = IBw - s.c.x;
 
     float WBw = 0.f;
-    bool okW = (t00.y > 0.f) && (t10.y > 0.f) && (t01.y > 0.f) && (t11.y > 0.f) &&
-               (nl.y > 0.f) && (nr.y > 0.f) && (nu.y > 0.f) && (nd.y > 0.f);
+    bool okW = (t.t00.y > 0.f) && (t.t10.y > 0.f) && (t.t01.y > 0.f) && (t.t11.y > 0.f) &&
+               (s.nl.y > 0.f) && (s.nr.y > 0.f) && (s.nu.y > 0.f) && (s.nd.y > 0.f);
     if (okW) {
-        const float wtop = fmaf(ax, t10.y - t00.y, t00.y);
-        const float wbot = fmaf(ax, t11.y - t01.y, t01.y);
+        const float wtop = fmaf(ax, t.t10.y - t.t00.y, t.t00.y);
+        const float wbot = fmaf(ax, t.t11.y - t.t01.y, t.t01.y);
         const float WBp = fmaf(ay, wbot - wtop, wtop);
         // W_B^gamma = 1 / e_z^T (R K^-1 p_B / W_B(p_B) + t) = W_B(p_B) / (R_2 . q_B + t_z W_B(p_B))
-        const float qbx = a + du * A.ifx;
-        const float qby = b + dv * A.ify;
+        const float qbx = a + w.du * A.ifx;
+        const float qby = b + w.dv * A.ify;
         const float den = fmaf(wp.R2[0], qbx, fmaf(wp.R2[1], qby, wp.R2[2])) + wp.tz * WBp;
         okW = den > 0.f;
         if (okW) {
@@ -155,19 +196,19 @@ __device__ __forceinline__ void eval_pixel(const LevelDev& A, const LevelDev& B,
     if (!WANT_J) return;
 
     // g~_I = grad I_A (K - p e_z^T) = (gx fx, gy fy, -(gx fx a + gy fy b))
-    const float gIx = 0.5f * (nr.x - nl.x) * A.fx;
-    const float gIy = 0.5f * (nd.x - nu.x) * A.fy;
+    const float gIx = 0.5f * (s.nr.x - s.nl.x) * A.fx;
+    const float gIy = 0.5f * (s.nd.x - s.nu.x) * A.fy;
     const float gIz = -fmaf(gIx, a, gIy * b);
-    // J_I = (W_A g~_I, q x g~_I)
+    // J_I = (W_A g~_I, q x g~_I), q = (a, b, 1)
     o.JI[0] = WA * gIx;
     o.JI[1] = WA * gIy;
     o.JI[2] = WA * gIz;
-    o.JI[3] = fmaf(b, gIz, -gIy);          // q = (a, b, 1)
+    o.JI[3] = fmaf(b, gIz, -gIy);
     o.JI[4] = fmaf(-a, gIz, gIx);
     o.JI[5] = fmaf(a, gIy, -b * gIx);
     if (okW) {
-        const float gWx = 0.5f * (nr.y - nl.y) * A.fx;
-        const float gWy = 0.5f * (nd.y - nu.y) * A.fy;
+        const float gWx = 0.5f * (s.nr.y - s.nl.y) * A.fx;
+        const float gWy = 0.5f * (s.nd.y - s.nu.y) * A.fy;
         const float gWz0 = -fmaf(gWx, a, gWy * b);
         const float gWz = gWz0 + WBw;      // + W_B^gamma e_z
         o.JW[0] = WA * gWx;
@@ -187,6 +228,19 @@ __device__ __forceinline__ void eval_pixel(const LevelDev& A, const LevelDev& B,
 #pragma unroll
         for (int k = 0; k < 6; ++k) o.JW[k] = 0.f;
     }
+}
+
+// Evaluate one pixel p = (u, v) of A: all four stages in turn.
+template <int PREC, bool WANT_J>
+__device__ __forceinline__ void eval_pixel(const LevelDev& A, const LevelDev& B, const WarpPose& wp,
+                                           int u, int v, PixelTerms& o) {
+    PxA s;
+    PxW w;
+    PxB t;
+    stage_a<PREC>(A, u, v, s);
+    stage_w(A, B, wp, u, v, s, w);
+    stage_b<PREC>(B, w, t);
+    finish<WANT_J>(A, wp, s, w, t, o);
 }
 
 // Student-t weight omega(x, nu) / sigma^2 = (nu + 1) / (nu sigma^2 + (r - mu)^2).
@@ -247,7 +301,7 @@ struct F2 {
 // D = diag(H)^-1/2), then factorised S = L L^T by Cholesky.  Returns false if
 // a diagonal entry or pivot is not positive.
 __device__ __forceinline__ bool cholesky_solve6_f(const float H[36], const float rhs[6], float xi[6]) {
-    float D[6], L[36], y[6];
+    float D[6], L[36], iL[6], y[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
         if (!(H[i * 6 + i] > 0.f)) return false;
@@ -261,6 +315,7 @@ __device__ __forceinline__ bool cholesky_solve6_f(const float H[36], const float
         if (!(d > 1e-7f)) return false;
         const float r = rsqrtf(d);
         L[j * 6 + j] = d * r;
+        iL[j] = r;
 #pragma unroll
         for (int i = j + 1; i < 6; ++i) {
             float t = H[i * 6 + j] * D[i] * D[j];
@@ -274,17 +329,67 @@ __device__ __forceinline__ bool cholesky_solve6_f(const float H[36], const float
         float t = rhs[i] * D[i];
 #pragma unroll
         for (int k = 0; k < i; ++k) t = fmaf(-L[i * 6 + k], y[k], t);
-        y[i] = t / L[i * 6 + i];
+        y[i] = t * iL[i];
     }
 #pragma unroll
     for (int i = 5; i >= 0; --i) {
         float t = y[i];
 #pragma unroll
         for (int k = i + 1; k < 6; ++k) t = fmaf(-L[k * 6 + i], xi[k], t);
-        xi[i] = t / L[i * 6 + i];
+        xi[i] = t * iL[i];
     }
 #pragma unroll
     for (int i = 0; i < 6; ++i) xi[i] *= D[i];
+    return true;
+}
+
+// Same Jacobi-scaled Cholesky solve for one thread with a small register
+// footprint: H and g are read from (shared) memory, L is kept packed (lower
+// triangle, 21 values) and the pivots as reciprocals, so nothing spills to
+// local memory in a kernel with a tight register budget.
+__device__ __forceinline__ bool cholesky_solve6_packed(const float* H, const float* g, float xi[6]) {
+    float D[6], L[21], iL[6], y[6];
+#define LIDX(i, j) ((i) * ((i) + 1) / 2 + (j))
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        const float hii = H[i * 6 + i];
+        if (!(hii > 0.f)) return false;
+        D[i] = rsqrtf(hii);
+    }
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        float d = H[j * 6 + j] * D[j] * D[j];
+#pragma unroll
+        for (int k = 0; k < j; ++k) d = fmaf(-L[LIDX(j, k)], L[LIDX(j, k)], d);
+        if (!(d > 1e-7f)) return false;
+        const float r = rsqrtf(d);
+        L[LIDX(j, j)] = d * r;
+        iL[j] = r;
+#pragma unroll
+        for (int i = j + 1; i < 6; ++i) {
+            float t = H[i * 6 + j] * D[i] * D[j];
+#pragma unroll
+            for (int k = 0; k < j; ++k) t = fmaf(-L[LIDX(i, k)], L[LIDX(j, k)], t);
+            L[LIDX(i, j)] = t * r;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        float t = -g[i] * D[i];
+#pragma unroll
+        for (int k = 0; k < i; ++k) t = fmaf(-L[LIDX(i, k)], y[k], t);
+        y[i] = t * iL[i];
+    }
+#pragma unroll
+    for (int i = 5; i >= 0; --i) {
+        float t = y[i];
+#pragma unroll
+        for (int k = i + 1; k < 6; ++k) t = fmaf(-L[LIDX(k, i)], xi[k], t);
+        xi[i] = t * iL[i];
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) xi[i] *= D[i];
+#undef LIDX
     return true;
 }
 
@@ -317,9 +422,11 @@ __device__ __forceinline__ void warp_apply_update(const float xi[6], double* T) 
     const float tx = xi[3], ty = xi[4], tz = xi[5];
     const float t2 = fmaf(tx, tx, fmaf(ty, ty, tz * tz));
     float A, B;
-    if (t2 < 1e-8f) {
-        A = 1.f - t2 * (1.f / 6.f);
-        B = 0.5f - t2 * (1.f / 24.f);
+    if (t2 < 0.25f) {
+        // sin t / t and (1 - cos t) / t^2 by their Taylor series (|t| < 0.5: the
+        // first omitted terms are below 3e-11)
+        A = 1.f - t2 * (1.f / 6.f - t2 * (1.f / 120.f - t2 * (1.f / 5040.f - t2 * (1.f / 362880.f))));
+        B = 0.5f - t2 * (1.f / 24.f - t2 * (1.f / 720.f - t2 * (1.f / 40320.f - t2 * (1.f / 3628800.f))));
     } else {
         const float t = sqrtf(t2);
         float sn, cs;
