@@ -15,9 +15,13 @@ value      frames (= 640x480 alignments) per second over all ranks, inputs
            timed intervals.
 e2e        the same with every step's frame copied from pinned host memory and
            its result struct read back to pinned host memory inside the step.
-roofline   the sweep kernel (or the kernel named by --roofline-kernel) timed
-           live with CUDA events around its launches inside the timed steps;
-           achieved = 16 B x pixels per launch / launch time.
+roofline   the dominant kernel by share of its timed region: the robust-scale
+           kernel is timed live (CUDA events around each launch, on the
+           tracker's stream) over the device-resident steps, the sweep kernel
+           over the end-to-end steps; achieved = 16 B x units per launch /
+           launch time (units: level pixels for the sweep, systematic-sample
+           pixels for the robust-scale kernel).  The other kernel is reported
+           under roofline_other_kernels.
 
 Multi-GPU: every rank tracks its own independent sequence (seed = rank), no
 collective on the data path ("scaling": "weak").
@@ -44,14 +48,19 @@ KF_EVERY = 20
 N_FRAMES = 300
 BYTES_PER_PX_ITER = 16          # I_A, W_A, I_B, W_B in FP32, each read once
 
+# DRAM bytes (read + write) per unit (level pixel for the sweep, sample pixel for
+# the robust-scale kernel) from the ncu captures summarised in
+# profiles/robust_kernel_seq640_level0.md and profiles/sweep_kernel_seq640_level0.md
+# (level-0 launches, cold caches); set to None whenever those kernels change.
+TRAFFIC_PER_UNIT = {"robust_kernel": 3146752 / 19200, "sweep_kernel": 6176512 / 307200}
+
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=120)
+    ap.add_argument("--steps", type=int, default=240)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--roofline-kernel", choices=["sweep", "robust"], default="sweep")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -71,7 +80,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, ValueError):
             self.proc = None
@@ -207,9 +216,11 @@ def native(args):
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
     stream = torch.cuda.Stream(device=dev)
 
-    kern = R.KERNEL_SWEEP if args.roofline_kernel == "sweep" else R.KERNEL_ROBUST
     per_step_launches = sum(ITERS[:LEVELS])
-    timer = R.KernelTimer(kern, per_step_launches * args.steps + 8)
+    # the robust-scale kernel is timed live over the device-resident steps, the
+    # sweep kernel over the end-to-end steps (one kernel per timed region)
+    timer_robust = R.KernelTimer(R.KERNEL_ROBUST, per_step_launches * args.steps + 8)
+    timer_sweep = R.KernelTimer(R.KERNEL_SWEEP, per_step_launches * args.steps + 8)
     trk = Tracker(W, H, K, levels=LEVELS, iters=ITERS, kf_every=KF_EVERY, max_frames=N_FRAMES + 1, device=dev)
 
     launches = {"n": 0}
@@ -265,7 +276,7 @@ def native(args):
     torch.cuda.synchronize()
 
     # ---- device-resident timed region
-    timer.attach(trk.params)
+    timer_robust.attach(trk.params)
     clocks = ClockSampler(local)
     clocks.start()
     if dist:
@@ -281,9 +292,6 @@ def native(args):
     trk.params.timing = None
     step_ms = [a.elapsed_time(b) for a, b in evs]
     total_ms = float(sum(step_ms))
-    kern_ms = timer.total_ms()
-    kern_units = int(timer.t.units)
-    kern_count = int(timer.t.count)
     gpu_launches = launches["n"]
 
     # ---- end-to-end through host buffers
@@ -292,9 +300,13 @@ def native(args):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
+    timer_sweep.attach(trk.params)
     evs2 = run_steps(args.steps, timed=True, e2e=True, res_host=res_host)
     torch.cuda.synchronize()
+    trk.params.timing = None
     e2e_ms = float(sum(a.elapsed_time(b) for a, b in evs2))
+    kern = {"robust_kernel": (timer_robust.total_ms(), int(timer_robust.t.units), int(timer_robust.t.count), total_ms),
+            "sweep_kernel": (timer_sweep.total_ms(), int(timer_sweep.t.units), int(timer_sweep.t.count), e2e_ms)}
 
     # pose sanity: frames of the last pass vs ground truth
     traj = trk.trajectory()
@@ -302,27 +314,30 @@ def native(args):
     E = [np.linalg.inv(seq["T_wc"][0] @ traj[i]) @ seq["T_wc"][i] for i in range(1, n_ok)]
     rot = max(float(np.arccos(np.clip((np.trace(e[:3, :3]) - 1) / 2, -1, 1))) for e in E) if E else 0.0
 
-    t = torch.tensor([total_ms, e2e_ms, kern_ms], dtype=torch.float64, device=dev)
+    t = torch.tensor([total_ms, e2e_ms], dtype=torch.float64, device=dev)
     if dist:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms, e2e_ms, kern_ms = t.tolist()
+    total_ms, e2e_ms = t.tolist()
     if rank != 0:
         dist.destroy_process_group()
         return
     value = world * args.steps / (total_ms / 1000.0)
     e2e_val = world * args.steps / (e2e_ms / 1000.0)
     peak, peak_kind = measured_peaks()
-    units_per_launch = kern_units / max(kern_count, 1)
-    if args.roofline_kernel == "sweep":
-        alg_bytes = BYTES_PER_PX_ITER * kern_units
-        achieved = alg_bytes / (kern_ms / 1000.0) / 1e9 if kern_ms > 0 else 0.0
-    else:
-        alg_bytes = BYTES_PER_PX_ITER * kern_units
-        achieved = alg_bytes / (kern_ms / 1000.0) / 1e9 if kern_ms > 0 else 0.0
-    roofline = {"bound": "hbm", "kernel": args.roofline_kernel + "_kernel", "achieved": achieved, "peak": peak,
-                "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak if peak else None,
-                "traffic": None, "launches": kern_count, "units_per_launch": units_per_launch,
-                "kernel_ms_per_step": kern_ms / args.steps, "share_of_step": kern_ms / total_ms if total_ms else None}
+    rooflines = {}
+    for name, (k_ms, k_units, k_count, region_ms) in kern.items():
+        alg_bytes = BYTES_PER_PX_ITER * k_units          # 16 B per pixel (or sample) per launch
+        achieved = alg_bytes / (k_ms / 1000.0) / 1e9 if k_ms > 0 else 0.0
+        rooflines[name] = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
+                           "unit": "GB/s", "frac": achieved / peak if peak else None,
+                           "traffic": (TRAFFIC_PER_UNIT[name] * k_units / max(k_count, 1)
+                                       if TRAFFIC_PER_UNIT.get(name) is not None else None),
+                           "launches": k_count, "units_per_launch": k_units / max(k_count, 1),
+                           "avg_launch_us": 1000.0 * k_ms / max(k_count, 1),
+                           "share_of_step": k_ms / region_ms if region_ms else None}
+    dominant = max(rooflines, key=lambda n: rooflines[n]["share_of_step"] or 0.0)
+    roofline = rooflines[dominant]
+    others = {n: r for n, r in rooflines.items() if n != dominant}
     cpu = None
     if not args.no_cpu_baseline:
         r = run_oracle_sample(7)
@@ -335,7 +350,7 @@ def native(args):
         "config": config_dict(),
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 2 * W * H * 4,
                 "d2h_bytes_per_step": R.RESULT_BYTES},
-        "roofline": roofline, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": gpu_launches,
+        "roofline": roofline, "roofline_other_kernels": others, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": gpu_launches,
         "wall_s_timed": t_wall, "max_rot_err_vs_truth_rad": rot,
     }
     print(json.dumps(line))
