@@ -46,7 +46,9 @@ W, H = 640, 480
 LEVELS, ITERS = 4, (5, 5, 5, 10)
 KF_EVERY = 20
 N_FRAMES = 300
-BYTES_PER_PX_ITER = 16          # I_A, W_A, I_B, W_B in FP32, each read once
+# algorithmic bytes per pixel (or sample) per launch: I_A, W_A, I_B, W_B each read
+# once -- 4 B each as float32 planes, 2 B each in the reduced-precision form
+BYTES_PER_UNIT = {"f32": 16, "bf16": 8}
 
 # DRAM bytes (read + write) per unit (level pixel for the sweep, sample pixel for
 # the robust-scale kernel) from the ncu captures summarised in
@@ -62,6 +64,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", choices=["f32", "bf16"], default="f32",
+                    help="plane storage: f32, or the reduced-precision form (bf16 I, fp16 W)")
     return ap.parse_args()
 
 
@@ -140,19 +144,22 @@ sys.path.insert(0, {root!r})
 import numpy as np
 import oracle as O
 from paper_1807_08271_gb300 import synth
-seq = synth.render_sequence(0, n_frames={nf})
+seq = synth.render_sequence(0, n_frames={N})
 t0 = time.perf_counter()
-r = O.track_sequence(seq["I"], seq["W"], seq["K"], levels={levels}, iters={iters}, kf_every={kf})
+r = O.track_sequence(seq["I"], seq["W"], seq["K"], levels={levels}, iters={iters}, kf_every={kf}, n_frames={nf},
+                     reduced={reduced})
 dt = time.perf_counter() - t0
-print(json.dumps({{"frames": {nf} - 1, "seconds": dt}}))
+print(json.dumps({{"frames": {nf} - 1, "seconds": dt, "T_world": r["T_world"].tolist()}}))
 """
 
 
-def run_oracle_sample(n_frames: int) -> dict:
+def run_oracle_sample(n_frames: int, reduced: bool = False) -> dict:
+    """Time the FP64 oracle (one thread) on frames 0..n_frames-1 of the sequence."""
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
         env[k] = "1"
-    code = CPU_SNIPPET.format(root=ROOT, nf=n_frames, levels=LEVELS, iters=tuple(ITERS), kf=KF_EVERY)
+    code = CPU_SNIPPET.format(root=ROOT, N=N_FRAMES, nf=n_frames, levels=LEVELS, iters=tuple(ITERS), kf=KF_EVERY,
+                              reduced=reduced)
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, check=True)
     return json.loads(out.stdout.strip().splitlines()[-1])
 
@@ -163,13 +170,14 @@ def reference(args):
     if rank != 0:
         return
     n_timed = max(1, min(args.steps, 24))
-    r = run_oracle_sample(n_timed + 1)
+    r = run_oracle_sample(n_timed + 1, reduced=(args.precision == "bf16"))
     value = r["frames"] / r["seconds"]
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": r["frames"], "warmup": 0, "ms_per_step": 1000.0 * r["seconds"] / r["frames"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": config_dict("oracle frames 1..%d of the sequence" % r["frames"]),
+        "data": "synthetic", "config": config_dict("oracle frames 1..%d of the sequence" % r["frames"],
+                                                    precision=args.precision),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"frames 1..{r['frames']} of the 300-frame sequence, one thread (numpy float64)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -177,11 +185,14 @@ def reference(args):
     print(json.dumps(line))
 
 
-def config_dict(extra=None):
+def config_dict(extra=None, precision="f32"):
     d = {"workload": "synthetic 640x480 room sequence, 300 frames at 30 Hz; frame-to-keyframe alignment on a "
                      "4-level pyramid [10,5,5,5] iterations, fusion of every frame, keyframe every 20 frames",
          "width": W, "height": H, "levels": LEVELS, "iters_fine_to_coarse": list(ITERS),
-         "frames": N_FRAMES, "keyframe_every": KF_EVERY, "precision": "plain FP32 planes",
+         "frames": N_FRAMES, "keyframe_every": KF_EVERY,
+         "precision": ("plain FP32 planes" if precision == "f32" else
+                       "bf16 intensity / fp16 inverse-depth planes, FP32 residuals, compensated FP32 sums, "
+                       "FP64 6x6 solve and update"),
          "l2": "flushed between steps (512 MiB write), outside the timed intervals"}
     if extra:
         d["note"] = extra
@@ -221,7 +232,10 @@ def native(args):
     # sweep kernel over the end-to-end steps (one kernel per timed region)
     timer_robust = R.KernelTimer(R.KERNEL_ROBUST, per_step_launches * args.steps + 8)
     timer_sweep = R.KernelTimer(R.KERNEL_SWEEP, per_step_launches * args.steps + 8)
-    trk = Tracker(W, H, K, levels=LEVELS, iters=ITERS, kf_every=KF_EVERY, max_frames=N_FRAMES + 1, device=dev)
+    prec = R.PLANES_BF16_F16 if args.precision == "bf16" else R.PLANES_F32
+    bytes_per_unit = BYTES_PER_UNIT[args.precision]
+    trk = Tracker(W, H, K, levels=LEVELS, iters=ITERS, kf_every=KF_EVERY, max_frames=N_FRAMES + 1, device=dev,
+                  precision=prec)
 
     launches = {"n": 0}
 
@@ -326,12 +340,13 @@ def native(args):
     peak, peak_kind = measured_peaks()
     rooflines = {}
     for name, (k_ms, k_units, k_count, region_ms) in kern.items():
-        alg_bytes = BYTES_PER_PX_ITER * k_units          # 16 B per pixel (or sample) per launch
+        alg_bytes = bytes_per_unit * k_units             # 16 B (FP32 planes) or 8 B (bf16/fp16) per unit
         achieved = alg_bytes / (k_ms / 1000.0) / 1e9 if k_ms > 0 else 0.0
         rooflines[name] = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
                            "unit": "GB/s", "frac": achieved / peak if peak else None,
                            "traffic": (TRAFFIC_PER_UNIT[name] * k_units / max(k_count, 1)
-                                       if TRAFFIC_PER_UNIT.get(name) is not None else None),
+                                       if args.precision == "f32" and TRAFFIC_PER_UNIT.get(name) is not None
+                                       else None),
                            "launches": k_count, "units_per_launch": k_units / max(k_count, 1),
                            "avg_launch_us": 1000.0 * k_ms / max(k_count, 1),
                            "share_of_step": k_ms / region_ms if region_ms else None}
@@ -339,19 +354,41 @@ def native(args):
     roofline = rooflines[dominant]
     others = {n: r for n, r in rooflines.items() if n != dominant}
     cpu = None
+    pose_check = None
     if not args.no_cpu_baseline:
-        r = run_oracle_sample(7)
+        n_cmp = 7
+        r = run_oracle_sample(n_cmp, reduced=(args.precision == "bf16"))
         cpu = {"value": r["frames"] / r["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"frames 1..{r['frames']} of the sequence (align + fuse), one thread, numpy float64"}
+               "sample": f"frames 1..{r['frames']} of the sequence (align + fuse), one thread, numpy float64"
+                         + (", bf16/fp16-rounded pyramids" if args.precision == "bf16" else "")}
+        # per-frame pose error of a fresh GPU pass over the same frames against the oracle
+        chk = Tracker(W, H, K, levels=LEVELS, iters=ITERS, kf_every=KF_EVERY, max_frames=n_cmp, device=dev,
+                      precision=prec)
+        for k in range(n_cmp):
+            chk.step(I_all[k], W_all[k])
+        torch.cuda.synchronize()
+        gT = chk.trajectory()
+
+        def errs(oT):
+            out = []
+            for k in range(1, n_cmp):
+                E = np.linalg.inv(np.asarray(oT[k])) @ gT[k]
+                c = float(np.clip((np.trace(E[:3, :3]) - 1) / 2, -1, 1))
+                out.append([float(np.arccos(c)), float(np.linalg.norm(E[:3, 3]))])
+            return out
+        pose_check = {"frames": f"1..{n_cmp - 1}", "vs_oracle_same_planes_rad_m": errs(r["T_world"])}
+        if args.precision == "bf16":
+            rf = run_oracle_sample(n_cmp, reduced=False)
+            pose_check["vs_oracle_fp32_planes_rad_m"] = errs(rf["T_world"])
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": config_dict(),
+        "config": config_dict(precision=args.precision),
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 2 * W * H * 4,
                 "d2h_bytes_per_step": R.RESULT_BYTES},
         "roofline": roofline, "roofline_other_kernels": others, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": gpu_launches,
-        "wall_s_timed": t_wall, "max_rot_err_vs_truth_rad": rot,
+        "wall_s_timed": t_wall, "max_rot_err_vs_truth_rad": rot, "pose_check": pose_check,
     }
     print(json.dumps(line))
     if dist:

@@ -185,7 +185,7 @@ int rgbid_align(const rgbid_pyramid* ref, const rgbid_pyramid* cur,
  * device allocation) and callers without a CUDA allocator of their own.  The
  * paper has no counterpart to this entry point.
  * It behaves as rgbid_align but takes its scratch from a fixed device array
- * inside the library (RGBID_NOALLOC_SCRATCH_BYTES, 512 KiB, held by every GPU
+ * inside the library (RGBID_NOALLOC_SCRATCH_BYTES, 1 MiB, held by every GPU
  * that loads the library until the process exits) and calls no allocator.
  * Inputs and outputs are still the caller's.  The first call on a device,
  * with that device current, looks up the array's device address
@@ -195,7 +195,7 @@ int rgbid_align(const rgbid_pyramid* ref, const rgbid_pyramid* cur,
  * look-up fails.  Every call shares the one array: calls whose work overlaps on
  * the GPU (other streams, other host threads) race and must be serialised by
  * the caller.  Each call resets the scratch fields that must start at zero. */
-#define RGBID_NOALLOC_SCRATCH_BYTES (512u * 1024u)
+#define RGBID_NOALLOC_SCRATCH_BYTES (1024u * 1024u)
 int rgbid_align_noalloc(const rgbid_pyramid* ref, const rgbid_pyramid* cur,
                         const double* T_init, int T_init_on_device,
                         const rgbid_align_params* params,

@@ -185,6 +185,32 @@ def build_pyramid(I0, W0, K0, levels: int) -> list:
     return pyr
 
 
+def round_bf16(x) -> np.ndarray:
+    """Round to bfloat16 (round to nearest, ties to even), via float32, as float64.
+
+    Storage of the reduced-precision form (SURVEY extension X1): each level's
+    intensity is held as bfloat16."""
+    f = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+    u = f.view(np.uint32).astype(np.uint64)
+    lsb = (u >> np.uint64(16)) & np.uint64(1)
+    r = ((u + np.uint64(0x7FFF) + lsb) >> np.uint64(16)) << np.uint64(16)
+    out = r.astype(np.uint32).view(np.float32)
+    out = np.where(np.isnan(f), f, out)
+    return out.astype(np.float64)
+
+
+def round_f16(x) -> np.ndarray:
+    """Round to IEEE binary16 (round to nearest even), via float32, as float64 (the
+    reduced-precision form's inverse-depth storage)."""
+    return np.asarray(x, dtype=np.float32).astype(np.float16).astype(np.float64)
+
+
+def build_pyramid_reduced(I0, W0, K0, levels: int) -> list:
+    """Pyramid of the reduced-precision form: every level computed from level 0
+    as in ``build_pyramid``, then I rounded to bfloat16 and W to binary16."""
+    return [Level(round_bf16(l.I), round_f16(l.W), l.K) for l in build_pyramid(I0, W0, K0, levels)]
+
+
 def gradients(I, W):
     """Central-difference gradients of I and W (reading R3).
 
@@ -516,14 +542,16 @@ def fuse(I_kf, W_kf, C_kf, I_k, W_k, K, T, sigma_W: float, fuse_intensity: bool 
 
 # ----------------------------------------------------------------------------- tracking front-end
 def track_sequence(I_frames, W_frames, K, levels: int = 4, iters=(5, 5, 5, 10), kf_every: int = 20,
-                   fuse_intensity: bool = True, n_frames: int | None = None):
+                   fuse_intensity: bool = True, n_frames: int | None = None, reduced: bool = False):
     """Frame-to-keyframe tracking with fusion ("Camera tracking", "Keyframe fusion").
 
     Frame 0 initialises the keyframe (C_kf = 1).  Frame k is aligned to the
     keyframe from the constant-velocity guess kf_T_k(0) = kf_T_{k-1} (kf_T_{k-2})^-1
     kf_T_{k-1}; every ``kf_every`` frames the aligned frame becomes the new
     keyframe (reading R15), otherwise it is fused into the keyframe with the
-    final sigma_W of its alignment (reading R14).  Returns dict(T_world [n,4,4]
+    final sigma_W of its alignment (reading R14).  With ``reduced`` the pyramids
+    are those of the reduced-precision form (bfloat16 I, binary16 W per level;
+    the keyframe planes themselves stay float).  Returns dict(T_world [n,4,4]
     camera-to-world with frame 0 at the identity, results (per-frame align
     dicts), keyframe=(I, W, C) at the end)."""
     P = AlignParams(levels=levels, iters=tuple(iters))
@@ -531,14 +559,15 @@ def track_sequence(I_frames, W_frames, K, levels: int = 4, iters=(5, 5, 5, 10), 
     I_kf = np.asarray(I_frames[0], dtype=np.float64).copy()
     W_kf = np.asarray(W_frames[0], dtype=np.float64).copy()
     C_kf = np.ones_like(W_kf)
-    kfp = build_pyramid(I_kf, W_kf, K, levels)
+    pyramid = build_pyramid_reduced if reduced else build_pyramid
+    kfp = pyramid(I_kf, W_kf, K, levels)
     T1 = np.eye(4)
     T2 = np.eye(4)
     T_wkf = np.eye(4)
     T_world = [np.eye(4)]
     results = []
     for k in range(1, n):
-        cur = build_pyramid(I_frames[k], W_frames[k], K, levels)
+        cur = pyramid(I_frames[k], W_frames[k], K, levels)
         T_init = se3_project(T1 @ se3_inv(T2) @ T1)
         r = align(kfp, cur, T_init, P)
         results.append(r)
@@ -556,5 +585,5 @@ def track_sequence(I_frames, W_frames, K, levels: int = 4, iters=(5, 5, 5, 10), 
                                        fuse_intensity)
             T2 = T1
             T1 = Tk
-        kfp = build_pyramid(I_kf, W_kf, K, levels)
+        kfp = pyramid(I_kf, W_kf, K, levels)
     return dict(T_world=np.stack(T_world), results=results, keyframe=(I_kf, W_kf, C_kf))

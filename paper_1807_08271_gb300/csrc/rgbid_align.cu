@@ -624,10 +624,10 @@ __global__ void __launch_bounds__(kSweepNT, 2) sweep_kernel(SweepArgs a) {
     const int nblocks = gridDim.x * gridDim.y;
     const int bid = blockIdx.y * gridDim.x + blockIdx.x;
     if (warp == 0) {
-        float s = 0.f;
+        F2 s{0.f, 0.f};
 #pragma unroll
-        for (int w = 0; w < kSweepNT / 32; ++w) s += red[w][lane];
-        a.partials[(size_t)bid * kSlots + lane] = s;
+        for (int w = 0; w < kSweepNT / 32; ++w) s.add(red[w][lane]);
+        reinterpret_cast<float2*>(a.partials)[(size_t)bid * kSlots + lane] = make_float2(s.hi, s.lo);
         __threadfence();
     }
     __syncthreads();
@@ -651,14 +651,15 @@ __global__ void __launch_bounds__(kSweepNT, 2) sweep_kernel(SweepArgs a) {
         constexpr int kStride = kSweepNT / 32;
         F2 acc2{0.f, 0.f};
         for (int b0 = warp; b0 < nblocks; b0 += kBatch * kStride) {
-            float vals[kBatch];
+            float2 vals[kBatch];
 #pragma unroll
             for (int q = 0; q < kBatch; ++q) {
                 const int b = b0 + q * kStride;
-                vals[q] = b < nblocks ? __ldcg(a.partials + (size_t)b * kSlots + lane) : 0.f;
+                vals[q] = b < nblocks ? __ldcg(reinterpret_cast<const float2*>(a.partials) + (size_t)b * kSlots + lane)
+                                      : make_float2(0.f, 0.f);
             }
 #pragma unroll
-            for (int q = 0; q < kBatch; ++q) acc2.add(vals[q]);
+            for (int q = 0; q < kBatch; ++q) acc2.add(F2{vals[q].x, vals[q].y});
         }
         fin[warp][lane] = acc2;
     }
@@ -710,22 +711,39 @@ __global__ void __launch_bounds__(kSweepNT, 2) sweep_kernel(SweepArgs a) {
         gs[lane - kSlotG] = totf;
     }
     __syncwarp();
+    __shared__ double xi_d[6];
     if (lane == 0) {
         const int nI = (int)tot[kSlotNI], nW = (int)tot[kSlotNW];
-        float xi[6];
-        const bool okl = (nI + nW) >= a.min_valid && cholesky_solve6_packed(Hs, gs, xi);
+        bool okl = (nI + nW) >= a.min_valid;
+        if constexpr (PREC == RGBID_PLANES_BF16_F16) {
+            // reduced-precision planes: the 6x6 solve runs in FP64
+            double xi[6];
+            okl = okl && cholesky_solve6_packed_d(Hs, gs, xi);
 #pragma unroll
-        for (int i = 0; i < 6; ++i) xi_sh[i] = okl ? xi[i] : 0.f;
+            for (int i = 0; i < 6; ++i) xi_d[i] = okl ? xi[i] : 0.0;
+        } else {
+            float xi[6];
+            okl = okl && cholesky_solve6_packed(Hs, gs, xi);
+#pragma unroll
+            for (int i = 0; i < 6; ++i) xi_sh[i] = okl ? xi[i] : 0.f;
+        }
         ok_flag = okl ? 1 : 0;
     }
     __syncwarp();
     const int ok_sh = ok_flag;
     const bool ok = ok_sh != 0;
     if (ok) {
-        float xi[6];
+        if constexpr (PREC == RGBID_PLANES_BF16_F16) {
+            double xi[6];
 #pragma unroll
-        for (int i = 0; i < 6; ++i) xi[i] = xi_sh[i];
-        warp_apply_update(xi, T_sh);
+            for (int i = 0; i < 6; ++i) xi[i] = xi_d[i];
+            warp_apply_update_d(xi, T_sh);
+        } else {
+            float xi[6];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) xi[i] = xi_sh[i];
+            warp_apply_update(xi, T_sh);
+        }
         warp_make_pose(T_sh, &wp_new);
         __syncwarp();
         if (lane < 16) reinterpret_cast<float*>(&st->wp)[lane] = reinterpret_cast<const float*>(&wp_new)[lane];
@@ -770,7 +788,7 @@ static int sample_stride(int w, int h, int cap) {
 static int sweep_blocks(int w, int h) { return ((w + kTileW - 1) / kTileW) * ((h + kTileH - 1) / kTileH); }
 
 static size_t workspace_bytes_for(int w0, int h0) {
-    return align_up(sizeof(AlignState), 256) + align_up((size_t)sweep_blocks(w0, h0) * kSlots * sizeof(float), 256);
+    return align_up(sizeof(AlignState), 256) + align_up((size_t)sweep_blocks(w0, h0) * kSlots * sizeof(float2), 256);
 }
 
 static int check_pyramids(const rgbid_pyramid* ref, const rgbid_pyramid* cur, const rgbid_align_params* p) {
@@ -1014,7 +1032,7 @@ extern "C" int rgbid_eval_step(const rgbid_pyramid* ref, const rgbid_pyramid* cu
 // for the symbol; the device address is fetched with cudaGetSymbolAddress once
 // per device and cached.
 namespace rgbid {
-constexpr size_t kNoallocScratchBytes = 512u * 1024u;   // RGBID_NOALLOC_SCRATCH_BYTES
+constexpr size_t kNoallocScratchBytes = 1024u * 1024u;  // RGBID_NOALLOC_SCRATCH_BYTES
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 static void* g_noalloc_ptr[64];
 }  // namespace rgbid

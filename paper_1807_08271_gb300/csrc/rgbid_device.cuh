@@ -393,6 +393,61 @@ __device__ __forceinline__ bool cholesky_solve6_packed(const float* H, const flo
     return true;
 }
 
+// FP64 version for the reduced-precision form: reciprocal square roots from an
+// FP32 seed refined by two Newton steps y <- y (3 - x y^2) / 2 in FP64.
+__device__ __forceinline__ double rsqrt_d(double x) {
+    double y = (double)rsqrtf((float)x);
+    y = y * (1.5 - 0.5 * x * y * y);
+    y = y * (1.5 - 0.5 * x * y * y);
+    return y;
+}
+
+__device__ __forceinline__ bool cholesky_solve6_packed_d(const float* H, const float* g, double xi[6]) {
+    double D[6], L[21], iL[6], y[6];
+#define LIDX(i, j) ((i) * ((i) + 1) / 2 + (j))
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        const double hii = H[i * 6 + i];
+        if (!(hii > 0.0)) return false;
+        D[i] = rsqrt_d(hii);
+    }
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        double d = (double)H[j * 6 + j] * D[j] * D[j];
+#pragma unroll
+        for (int k = 0; k < j; ++k) d = fma(-L[LIDX(j, k)], L[LIDX(j, k)], d);
+        if (!(d > 1e-12)) return false;
+        const double r = rsqrt_d(d);
+        L[LIDX(j, j)] = d * r;
+        iL[j] = r;
+#pragma unroll
+        for (int i = j + 1; i < 6; ++i) {
+            double t = (double)H[i * 6 + j] * D[i] * D[j];
+#pragma unroll
+            for (int k = 0; k < j; ++k) t = fma(-L[LIDX(i, k)], L[LIDX(j, k)], t);
+            L[LIDX(i, j)] = t * r;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        double t = -(double)g[i] * D[i];
+#pragma unroll
+        for (int k = 0; k < i; ++k) t = fma(-L[LIDX(i, k)], y[k], t);
+        y[i] = t * iL[i];
+    }
+#pragma unroll
+    for (int i = 5; i >= 0; --i) {
+        double t = y[i];
+#pragma unroll
+        for (int k = i + 1; k < 6; ++k) t = fma(-L[LIDX(k, i)], xi[k], t);
+        xi[i] = t * iL[i];
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) xi[i] *= D[i];
+#undef LIDX
+    return true;
+}
+
 // ---------------------------------------------------------------- warp-parallel pose arithmetic (double)
 // FP64 on this part runs at ~1/64 of the FP32 rate with ~64-cycle latency, so
 // the 4x4 pose products are spread over the lanes of one warp (one dependent
@@ -456,6 +511,53 @@ __device__ __forceinline__ void warp_apply_update(const float xi[6], double* T) 
         }
         Tn = Rt[0] * T[0 * 4 + j] + Rt[1] * T[1 * 4 + j] + Rt[2] * T[2 * 4 + j];
         if (j == 3) Tn -= Rt[0] * (double)xi[0] + Rt[1] * (double)xi[1] + Rt[2] * (double)xi[2];
+    }
+    __syncwarp();
+    if (lane < 12) T[lane] = Tn;
+    __syncwarp();
+}
+
+// FP64 variant (reduced-precision form): the step and the Rodrigues
+// coefficients are double throughout.
+__device__ __forceinline__ void warp_apply_update_d(const double xi[6], double* T) {
+    const int lane = threadIdx.x & 31;
+    const double tx = xi[3], ty = xi[4], tz = xi[5];
+    const double t2d = tx * tx + ty * ty + tz * tz;
+    double Ad, Bd;
+    if (t2d < 0.25) {
+        // Taylor series of sin t / t and (1 - cos t) / t^2 to t^16 (|t| < 0.5: error < 1e-19)
+        Ad = 1.0 - t2d * (1.0 / 6.0 - t2d * (1.0 / 120.0 - t2d * (1.0 / 5040.0 - t2d * (1.0 / 362880.0 -
+             t2d * (1.0 / 39916800.0 - t2d * (1.0 / 6227020800.0 - t2d * (1.0 / 1307674368000.0 -
+             t2d * (1.0 / 355687428096000.0))))))));
+        Bd = 0.5 - t2d * (1.0 / 24.0 - t2d * (1.0 / 720.0 - t2d * (1.0 / 40320.0 - t2d * (1.0 / 3628800.0 -
+             t2d * (1.0 / 479001600.0 - t2d * (1.0 / 87178291200.0 - t2d * (1.0 / 20922789888000.0 -
+             t2d * (1.0 / 6402373705728000.0))))))));
+    } else {
+        const double t = sqrt(t2d);
+        double sn, cs;
+        sincos(t, &sn, &cs);
+        Ad = sn / t;
+        const double sh = sin(0.5 * t);
+        Bd = 2.0 * sh * sh / t2d;
+    }
+    double Tn = 0.0;
+    if (lane < 12) {
+        const int i = lane / 4, j = lane % 4;
+        const double th[3] = {tx, ty, tz};
+        double Rt[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            double cross = 0.0;
+            if (k == 0 && i == 1) cross = -th[2];
+            if (k == 0 && i == 2) cross = th[1];
+            if (k == 1 && i == 0) cross = th[2];
+            if (k == 1 && i == 2) cross = -th[0];
+            if (k == 2 && i == 0) cross = -th[1];
+            if (k == 2 && i == 1) cross = th[0];
+            Rt[k] = (k == i ? 1.0 : 0.0) + Ad * cross + Bd * (th[k] * th[i] - (k == i ? t2d : 0.0));
+        }
+        Tn = Rt[0] * T[0 * 4 + j] + Rt[1] * T[1 * 4 + j] + Rt[2] * T[2 * 4 + j];
+        if (j == 3) Tn -= Rt[0] * xi[0] + Rt[1] * xi[1] + Rt[2] * xi[2];
     }
     __syncwarp();
     if (lane < 12) T[lane] = Tn;

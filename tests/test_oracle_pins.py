@@ -481,3 +481,27 @@ def test_constant_velocity_drift_is_removed_by_projection():
     orth = lambda T: np.abs(T[:3, :3].T @ T[:3, :3] - np.eye(3)).max()
     assert orth(free[0]) > 1e-3
     assert orth(proj[0]) < 1e-14
+
+
+def test_reduced_precision_rounding_matches_torch_conversions():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(31)
+    x = np.concatenate([rng.random(4000), rng.uniform(0.1, 3.0, 4000), [0.0, 1.0, 0.5, 2.0 ** -10]]).astype(np.float32)
+    # exact ties of the bfloat16 grid round to even
+    ties = np.array([1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8], dtype=np.float32)
+    x = np.concatenate([x, ties])
+    ref_bf = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(O.round_bf16(x), ref_bf)
+    assert list(O.round_bf16(ties)) == [1.0, 1.0 + 4 * 2.0 ** -8]
+    ref_h = torch.from_numpy(x).to(torch.float16).to(torch.float64).numpy()
+    assert np.array_equal(O.round_f16(x), ref_h)
+
+
+def test_reduced_pyramid_rounds_every_level_of_the_fp64_pyramid():
+    p = synth.make_pair(1)
+    full = O.build_pyramid(p["I_A"], p["W_A"], p["K"], 3)
+    red = O.build_pyramid_reduced(p["I_A"], p["W_A"], p["K"], 3)
+    for a, b in zip(full, red):
+        assert np.array_equal(b.I, O.round_bf16(a.I)) and np.array_equal(b.W, O.round_f16(a.W))
+        assert np.array_equal(b.W > 0, a.W > 0)
+        assert np.max(np.abs(b.I - a.I)) <= 2.0 ** -9 and np.max(np.abs(b.W - a.W) / np.where(a.W > 0, a.W, 1)) <= 2.0 ** -11
