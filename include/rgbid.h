@@ -81,7 +81,8 @@ typedef struct {
  * systematic-sample pixels for the robust-scale kernel). */
 typedef enum {
     RGBID_KERNEL_SWEEP = 0,      /* fused warp + residual + Jacobian + weight + reduce (+ solve) */
-    RGBID_KERNEL_ROBUST = 1      /* systematic sample + (mu, sigma, nu) */
+    RGBID_KERNEL_ROBUST = 1,     /* systematic sample + (mu, sigma, nu) */
+    RGBID_KERNEL_BATCH = 2       /* the persistent kernel of rgbid_align_batched (units are not counted) */
 } rgbid_kernel_id;
 
 typedef struct {
@@ -200,6 +201,87 @@ int rgbid_align_noalloc(const rgbid_pyramid* ref, const rgbid_pyramid* cur,
                         const double* T_init, int T_init_on_device,
                         const rgbid_align_params* params,
                         rgbid_align_result* d_result, void* stream);
+
+/* ---------------------------------------------------------------- batched alignment
+ * Many independent alignments in ONE persistent kernel launch: the
+ * verification of loop-closure candidates ("Loop closure": the current frame
+ * is aligned densely against each candidate keyframe from the RANSAC pose),
+ * or the frame-to-keyframe alignments of several concurrent sequences.  Each
+ * alignment runs the same coarse-to-fine IRLS Gauss-Newton iteration as
+ * rgbid_align; pairs may differ in resolution, levels and iteration counts.
+ *
+ * Execution: a thread-block cluster of `cluster` CTAs takes one pair at a time
+ * from a device work queue (array order; put the largest pairs first) and
+ * keeps the whole alignment on chip: sample residuals in shared memory, every
+ * reduction (robust scale, the 27 normal-equation terms) exchanged between the
+ * cluster's CTAs through distributed shared memory, and the 6x6 solve and pose
+ * update repeated identically in every CTA, so no grid-wide synchronisation
+ * and no host round trip occurs.  The call is a single kernel launch and can
+ * be captured in a CUDA graph.  Device-side waits are bounded in time; a
+ * pair whose waits ran out reports RGBID_ERR_TIMEOUT in its result.
+ */
+
+/* One pair of a batch.  The array of items lives in DEVICE memory (the caller
+ * copies these host descriptors there) and must stay valid until the batch
+ * completes; the kernel validates each item and writes RGBID_ERR_INVALID_ARG
+ * into the status of an item that fails the rgbid_align argument rules. */
+typedef struct {
+    rgbid_pyramid ref;           /* A: the keyframe / candidate */
+    rgbid_pyramid cur;           /* B: the current frame */
+    double T_init[16];           /* initial A_T_B, row-major */
+    int levels;                  /* levels used, coarse to fine (<= both pyramids' levels) */
+    int iters[RGBID_MAX_LEVELS]; /* Gauss-Newton iterations per level, index 0 = finest (0..10000) */
+    int pad_;
+    rgbid_align_result* result;  /* device pointer, 8-byte aligned; an item with a NULL or
+                                    misaligned result is skipped */
+} rgbid_batch_item;
+
+/* Launch shape of the persistent kernel (see rgbid_batch_autotune). */
+typedef struct {
+    int cluster;                 /* CTAs (256 threads each) per alignment: 4, 8 or 16; 0 = 8 */
+    int rows_per_warp;           /* sweep tile height per warp: 1, 2 or 4 (tiles are 32 pixels wide); 0 = 2 */
+    int n_clusters;              /* persistent clusters launched; 0 = as many as are resident at once.
+                                    Always capped at the resident maximum and at n_items. */
+    int pad_;
+} rgbid_batch_config;
+
+/* Workspace of rgbid_align_batched: 256 bytes of device memory holding the
+ * queue head.  It must be zero before its first use (e.g. cudaMemset once);
+ * every completed batch leaves it zero again.  Batches sharing a workspace
+ * must not overlap on the device. */
+size_t rgbid_align_batched_workspace_bytes(void);
+
+/* Host-side check of one item (a host copy of the descriptor) against the
+ * rules the kernel applies: returns RGBID_OK or RGBID_ERR_INVALID_ARG. */
+int rgbid_batch_check_item(const rgbid_batch_item* item, int precision);
+
+/* Number of clusters of this shape that are resident on the current device at
+ * once (0 if none fit).  The first query of a shape on a device also sets the
+ * kernel's attributes; make it (or rgbid_batch_autotune) before capturing a
+ * batch into a CUDA graph.  Errors: INVALID_ARG (shape), CUDA. */
+int rgbid_batch_resident_clusters(int precision, const rgbid_batch_config* cfg, int* n_resident);
+
+/* Align every item of `d_items` (device array of n_items; all pyramids of
+ * `precision`).  `params` supplies the robust-estimation constants
+ * (scale_iters, bisect_steps, sample_cap, estimate_nu, min_valid, nu0, nu_lo,
+ * nu_hi) and the optional timing hook; its `levels`/`iters` are ignored (each
+ * item carries its own).  `cfg` may be NULL (defaults).  `workspace` is
+ * device memory of rgbid_align_batched_workspace_bytes(), 256-byte aligned.
+ * Errors: INVALID_ARG (params, cfg, NULL items with n_items > 0), WORKSPACE,
+ * UNSUPPORTED (precision, or no cluster of this shape fits), CUDA. */
+int rgbid_align_batched(const rgbid_batch_item* d_items, int n_items, int precision,
+                        const rgbid_align_params* params, const rgbid_batch_config* cfg,
+                        void* workspace, size_t workspace_bytes, void* stream);
+
+/* The project's autotuner for the batched kernel: runs the batch once per
+ * candidate shape (cluster 4/8/16 x rows_per_warp 1/2/4 x all or half of the
+ * resident clusters) as a warm-up, then `reps` timed runs each (CUDA events on
+ * `stream`, synchronising), and returns the shape with the lowest median time
+ * in *best and that time in *best_ms.  The items' results hold the last
+ * candidate's output afterwards.  Not for use during stream capture. */
+int rgbid_batch_autotune(const rgbid_batch_item* d_items, int n_items, int precision,
+                         const rgbid_align_params* params, void* workspace, size_t workspace_bytes,
+                         int reps, rgbid_batch_config* best, float* best_ms, void* stream);
 
 /* One step at a fixed pose and level, for inspection and parity testing.
  * `T` (host, 16 doubles) is the pose; `robust` (host, 6 doubles

@@ -45,6 +45,7 @@ class Pyramid(Structure):
 
 KERNEL_SWEEP = 0
 KERNEL_ROBUST = 1
+KERNEL_BATCH = 2
 
 
 class Timing(Structure):
@@ -66,6 +67,18 @@ class AlignResult(Structure):
 
 
 RESULT_BYTES = ctypes.sizeof(AlignResult)
+
+
+class BatchItem(Structure):
+    _fields_ = [("ref", Pyramid), ("cur", Pyramid), ("T_init", c_double * 16), ("levels", c_int),
+                ("iters", c_int * MAX_LEVELS), ("pad_", c_int), ("result", c_void_p)]
+
+
+class BatchConfig(Structure):
+    _fields_ = [("cluster", c_int), ("rows_per_warp", c_int), ("n_clusters", c_int), ("pad_", c_int)]
+
+    def as_tuple(self):
+        return (self.cluster, self.rows_per_warp, self.n_clusters)
 
 _lock = threading.Lock()
 _lib = None
@@ -91,6 +104,13 @@ SIGNATURES = [
                                     c_int, c_void_p]),
     ("rgbid_predict_pose", c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     ("rgbid_compose_pose", c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
+    ("rgbid_align_batched_workspace_bytes", c_size_t, []),
+    ("rgbid_batch_check_item", c_int, [POINTER(BatchItem), c_int]),
+    ("rgbid_batch_resident_clusters", c_int, [c_int, POINTER(BatchConfig), POINTER(c_int)]),
+    ("rgbid_align_batched", c_int, [c_void_p, c_int, c_int, POINTER(AlignParams), POINTER(BatchConfig),
+                                    c_void_p, c_size_t, c_void_p]),
+    ("rgbid_batch_autotune", c_int, [c_void_p, c_int, c_int, POINTER(AlignParams), c_void_p, c_size_t, c_int,
+                                     POINTER(BatchConfig), POINTER(ctypes.c_float), c_void_p]),
 ]
 
 
@@ -254,6 +274,46 @@ def rgbid_predict_pose(T_km1, T_km2, T_out, stream=None):
 def rgbid_compose_pose(A, invert_A: bool, B, T_out, stream=None):
     _check("rgbid_compose_pose", lib().rgbid_compose_pose(_ptr(A), 1 if invert_A else 0, _ptr(B), _ptr(T_out),
                                                           _stream_ptr(stream)))
+
+
+def rgbid_align_batched_workspace_bytes() -> int:
+    return int(lib().rgbid_align_batched_workspace_bytes())
+
+
+def rgbid_batch_check_item(item: BatchItem, precision: int) -> int:
+    """Host-side check of one item descriptor; returns the status code (no raise)."""
+    return int(lib().rgbid_batch_check_item(ctypes.byref(item), precision))
+
+
+def rgbid_batch_resident_clusters(precision: int, cfg: BatchConfig | None = None) -> int:
+    n = c_int(0)
+    code = lib().rgbid_batch_resident_clusters(precision, ctypes.byref(cfg) if cfg is not None else None,
+                                               ctypes.byref(n))
+    _check("rgbid_batch_resident_clusters", code)
+    return n.value
+
+
+def rgbid_align_batched(d_items, n_items: int, precision: int, params: AlignParams, cfg: BatchConfig | None,
+                        workspace, stream=None):
+    """Enqueue the persistent batched alignment.  ``d_items``: CUDA uint8 tensor
+    holding ``n_items`` BatchItem descriptors; ``workspace``: zeroed CUDA uint8
+    tensor of rgbid_align_batched_workspace_bytes()."""
+    code = lib().rgbid_align_batched(_ptr(d_items), n_items, precision, ctypes.byref(params),
+                                     ctypes.byref(cfg) if cfg is not None else None, _ptr(workspace),
+                                     workspace.numel() * workspace.element_size(), _stream_ptr(stream))
+    _check("rgbid_align_batched", code)
+
+
+def rgbid_batch_autotune(d_items, n_items: int, precision: int, params: AlignParams, workspace, reps: int = 3,
+                         stream=None):
+    """Time every launch shape on this batch; returns (best BatchConfig, its median ms)."""
+    best = BatchConfig()
+    ms = ctypes.c_float(0.0)
+    code = lib().rgbid_batch_autotune(_ptr(d_items), n_items, precision, ctypes.byref(params), _ptr(workspace),
+                                      workspace.numel() * workspace.element_size(), reps, ctypes.byref(best),
+                                      ctypes.byref(ms), _stream_ptr(stream))
+    _check("rgbid_batch_autotune", code)
+    return best, float(ms.value)
 
 
 # ----------------------------------------------------------------------------- conveniences

@@ -335,3 +335,41 @@ def render_sequence(seed: int = 0, n_frames: int = 300, width: int = 640, height
         ik, zk = scene.render(K, width, height, T[k])
         I[k], W[k] = apply_noise(ik, zk, rng, noise=noise)
     return dict(I=I, W=W, K=tuple(float(k) for k in K), T_wc=T, seed=seed, width=width, height=height)
+
+
+BATCH_SIZES = ((320, 240), (640, 480), (960, 720), (1280, 960))
+
+
+def batch_levels(width: int) -> int:
+    """Pyramid levels of a batch pair: halve down to an 80-pixel-wide coarsest level."""
+    return 1 + int(np.floor(np.log2(width / 80.0)))
+
+
+def batch_iters(levels: int) -> list:
+    """Gauss-Newton iterations per level, finest first: 10 at the coarsest, 5 elsewhere."""
+    return [5] * (levels - 1) + [10]
+
+
+def make_batch(seed: int = 0, n: int = 64, sizes=BATCH_SIZES, max_angle_deg: float = 10.0, max_trans: float = 0.2,
+               init_angle_deg: float = 2.0, init_trans: float = 0.03, noise: bool = True):
+    """Loop-closure-verification-like batch: n independent pairs, an equal share at
+    each resolution of ``sizes`` (shuffled), ground truth A_T_B with angle
+    ~U(0, max_angle_deg) and translation ~U(0, max_trans) m, and an initial guess
+    T_init = T_gt dT with dT ~ U(0, init_angle_deg) / U(0, init_trans) (the
+    perturbed seed pose a RANSAC stage would hand to the dense check).
+    Returns a list of make_pair dicts with T_init, levels and iters added."""
+    rng = np.random.default_rng(seed)
+    res = [sizes[i % len(sizes)] for i in range(n)]
+    order = rng.permutation(n)
+    res = [res[i] for i in order]
+    out = []
+    for (w, h) in res:
+        pair_seed = int(rng.integers(0, 2**31 - 1))
+        p = make_pair(pair_seed, w, h, noise=noise, max_angle_deg=max_angle_deg, max_trans=max_trans)
+        dT = random_relative_pose(rng, init_angle_deg, init_trans)
+        p["T_init"] = p["T_gt"] @ dT
+        L = batch_levels(w)
+        p["levels"] = L
+        p["iters"] = batch_iters(L)
+        out.append(p)
+    return out

@@ -78,3 +78,87 @@ def test_host_side_calls_without_a_gpu(binding):
     assert code == b.ERR_INVALID_ARG
     code = L.rgbid_align(None, None, None, 0, None, None, 0, None, None)
     assert code == b.ERR_INVALID_ARG
+
+
+def test_batch_struct_layouts_match_header(binding, tmp_path):
+    src = tmp_path / "abi_batch.c"
+    src.write_text(f'''#include <stdio.h>
+#include <stddef.h>
+#include "{HEADER}"
+int main(void) {{
+  printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(rgbid_batch_item), offsetof(rgbid_batch_item, cur),
+         offsetof(rgbid_batch_item, T_init), offsetof(rgbid_batch_item, levels),
+         offsetof(rgbid_batch_item, iters), offsetof(rgbid_batch_item, result), sizeof(rgbid_batch_config));
+  return 0;
+}}''')
+    exe = tmp_path / "abi_batch"
+    subprocess.run(["gcc", str(src), "-o", str(exe)], check=True)
+    sizes = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    b = binding
+    assert sizes == [ctypes.sizeof(b.BatchItem), b.BatchItem.cur.offset, b.BatchItem.T_init.offset,
+                     b.BatchItem.levels.offset, b.BatchItem.iters.offset, b.BatchItem.result.offset,
+                     ctypes.sizeof(b.BatchConfig)]
+
+
+def _host_item(b, w=320, h=240, levels=3, precision=0):
+    """A descriptor whose pointers are never dereferenced (host-side checks only)."""
+    it = b.BatchItem()
+    for pyr, base in ((it.ref, 0x10000000), (it.cur, 0x20000000)):
+        pyr.levels, pyr.precision = levels, precision
+        for l in range(levels):
+            L = pyr.lv[l]
+            L.width, L.height, L.pitch = w >> l, h >> l, ((w >> l) + 15) // 16 * 16
+            f = 525.0 * w / 640 / (1 << l)
+            L.K = b.Intrinsics(f, f, (w >> l) / 2.0 - 0.5, (h >> l) / 2.0 - 0.5)
+            L.IW = base + 4096 * l
+    it.levels = levels
+    for l in range(levels):
+        it.iters[l] = 5
+    it.T_init[0] = it.T_init[5] = it.T_init[10] = it.T_init[15] = 1.0
+    it.result = 0x30000000
+    return it
+
+
+def test_batch_item_checks_on_the_host(binding):
+    b = binding
+    assert b.rgbid_align_batched_workspace_bytes() == 256
+    it = _host_item(b)
+    assert b.rgbid_batch_check_item(it, b.PLANES_F32) == b.OK
+    assert b.rgbid_batch_check_item(it, b.PLANES_BF16_F16) == b.ERR_INVALID_ARG   # precision mismatch
+    assert b.rgbid_batch_check_item(it, 7) == b.ERR_UNSUPPORTED
+    bad = _host_item(b)
+    bad.cur.lv[1].width += 1                      # sizes differ between A and B
+    assert b.rgbid_batch_check_item(bad, b.PLANES_F32) == b.ERR_INVALID_ARG
+    bad = _host_item(b)
+    bad.levels = 4                                # more levels than the pyramids hold
+    assert b.rgbid_batch_check_item(bad, b.PLANES_F32) == b.ERR_INVALID_ARG
+    bad = _host_item(b)
+    bad.ref.lv[0].IW += 4                         # float2 planes need 8-byte alignment
+    assert b.rgbid_batch_check_item(bad, b.PLANES_F32) == b.ERR_INVALID_ARG
+    bad = _host_item(b)
+    bad.cur.lv[2].K = b.Intrinsics(1.0, 1.0, 1.0, 1.0)
+    assert b.rgbid_batch_check_item(bad, b.PLANES_F32) == b.ERR_INVALID_ARG
+    bad = _host_item(b)
+    bad.iters[0] = -1
+    assert b.rgbid_batch_check_item(bad, b.PLANES_F32) == b.ERR_INVALID_ARG
+    bad = _host_item(b)
+    bad.result = None
+    assert b.rgbid_batch_check_item(bad, b.PLANES_F32) == b.ERR_INVALID_ARG
+
+
+def test_batched_call_rejects_bad_arguments_before_launching(binding):
+    b = binding
+    L = b.lib()
+    p = b.rgbid_default_params()
+    cfg = b.BatchConfig(5, 2, 0, 0)             # unsupported cluster size
+    ws = ctypes.create_string_buffer(512)
+    assert L.rgbid_align_batched(None, 1, 0, ctypes.byref(p), None, None, 0, None) == b.ERR_INVALID_ARG
+    assert L.rgbid_align_batched(None, 0, 0, ctypes.byref(p), ctypes.byref(cfg), None, 0, None) == b.ERR_INVALID_ARG
+    assert L.rgbid_align_batched(None, 0, 3, ctypes.byref(p), None, None, 0, None) == b.ERR_UNSUPPORTED
+    p.bisect_steps = 99
+    assert L.rgbid_align_batched(None, 0, 0, ctypes.byref(p), None, None, 0, None) == b.ERR_INVALID_ARG
+    p = b.rgbid_default_params()
+    assert L.rgbid_align_batched(None, 0, 0, ctypes.byref(p), None, None, 0, None) == b.ERR_WORKSPACE
+    # an empty batch with a valid (host-memory stand-in) workspace enqueues nothing
+    addr = (ctypes.addressof(ws) + 255) // 256 * 256
+    assert L.rgbid_align_batched(None, 0, 0, ctypes.byref(p), None, ctypes.c_void_p(addr), 256, None) == b.OK
