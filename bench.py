@@ -64,6 +64,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["sequence", "batch"], default="sequence",
+                    help="sequence: the 640x480 tracking sequence (default); batch: 64 uneven loop-closure "
+                         "pairs in one persistent launch")
     ap.add_argument("--precision", choices=["f32", "bf16"], default="f32",
                     help="plane storage: f32, or the reduced-precision form (bf16 I, fp16 W)")
     return ap.parse_args()
@@ -394,10 +397,245 @@ def native(args):
     if dist:
         dist.destroy_process_group()
 
+# ----------------------------------------------------------------------------- batched workload
+BATCH_N = 64
+BATCH_METRIC = "alignments/s of 64 uneven frame-keyframe pairs in one persistent launch (vs the per-pair form)"
+BATCH_CPU_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+import oracle as O
+from paper_1807_08271_gb300 import synth
+pairs = synth.make_batch(seed=0, n=4, sizes=synth.BATCH_SIZES)
+t0 = time.perf_counter()
+for p in pairs:
+    A = O.build_pyramid{red}(p["I_A"], p["W_A"], p["K"], p["levels"])
+    B = O.build_pyramid{red}(p["I_B"], p["W_B"], p["K"], p["levels"])
+    O.align(A, B, p["T_init"], O.AlignParams(levels=p["levels"], iters=tuple(p["iters"])))
+dt = time.perf_counter() - t0
+print(json.dumps({{"alignments": len(pairs), "seconds": dt}}))
+"""
+
+
+def run_oracle_batch_sample(reduced: bool = False) -> dict:
+    """Time the FP64 oracle (one thread) on one pair of each resolution of the batch."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[k] = "1"
+    code = BATCH_CPU_SNIPPET.format(root=ROOT, red="_reduced" if reduced else "")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, check=True)
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def batch_config_dict(precision="f32", shape=None):
+    d = {"workload": "64 independent frame-keyframe pairs (loop-closure verification): 16 each at 320x240, "
+                     "640x480, 960x720 and 1280x960, relative poses up to 10 deg / 20 cm, initial guess = truth "
+                     "perturbed by up to 2 deg / 3 cm; levels 1 + floor(log2(w/80)), 10 iterations at the coarsest "
+                     "level and 5 elsewhere; one persistent launch replayed from a CUDA graph",
+         "pairs": BATCH_N,
+         "precision": ("plain FP32 planes" if precision == "f32" else
+                       "bf16 intensity / fp16 inverse-depth planes, FP32 residuals, compensated FP32 sums, "
+                       "FP64 6x6 solve and update"),
+         "l2": "flushed between steps (512 MiB write), outside the timed intervals"}
+    if shape is not None:
+        d["launch_shape"] = {"cluster": shape[0], "rows_per_warp": shape[1], "n_clusters": shape[2],
+                             "chosen_by": "rgbid_batch_autotune"}
+    return d
+
+
+def reference_batch(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    r = run_oracle_batch_sample(reduced=(args.precision == "bf16"))
+    value = r["alignments"] / r["seconds"]
+    sample = "one pair of each resolution (320x240, 640x480, 960x720, 1280x960), one thread (numpy float64)"
+    print(json.dumps({
+        "impl": "reference", "metric": BATCH_METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": 1, "warmup": 0, "ms_per_step": 1000.0 * r["seconds"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": batch_config_dict(args.precision),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def native_batch(args):
+    import numpy as np
+    import torch
+
+    from paper_1807_08271_gb300 import rgbid as R
+    from paper_1807_08271_gb300 import synth
+    from paper_1807_08271_gb300.batch import BatchAligner
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    prec = R.PLANES_BF16_F16 if args.precision == "bf16" else R.PLANES_F32
+    pairs = synth.make_batch(seed=rank, n=BATCH_N)
+
+    # device-resident inputs (level-0 planes) and their pyramids; pinned host copies for e2e
+    planes, host, pyr, items = [], [], [], []
+    for p in pairs:
+        w, h = p["width"], p["height"]
+        ent = []
+        for key in ("I_A", "W_A", "I_B", "W_B"):
+            ent.append(torch.from_numpy(p[key]).to(dev))
+            host.append(torch.from_numpy(p[key]).pin_memory())
+        planes.append(ent)
+        PA = R.DevicePyramid(w, h, p["levels"], prec, device=dev).build(ent[0], ent[1], p["K"])
+        PB = R.DevicePyramid(w, h, p["levels"], prec, device=dev).build(ent[2], ent[3], p["K"])
+        pyr.append((PA, PB))
+        items.append(dict(ref=PA.desc, cur=PB.desc, T_init=p["T_init"], levels=p["levels"], iters=p["iters"]))
+    B = BatchAligner(items, precision=prec, device=dev)
+    B.tune(reps=3)
+    shape = B.config.as_tuple()
+    B.capture()
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    # pixel evaluations of one batch (the sweep's units): sum over pairs and levels of w_l h_l iters_l
+    units = 0
+    for p in pairs:
+        for l in range(p["levels"]):
+            units += (p["width"] >> l) * (p["height"] >> l) * p["iters"][l]
+    bytes_per_unit = BYTES_PER_UNIT[args.precision]
+
+    for _ in range(max(3, args.warmup)):
+        B.replay()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    evs = []
+    t_wall = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(rank & 0xff)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        B.replay()
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    total_ms = float(sum(a.elapsed_time(b) for a, b in evs))
+
+    # end to end: every step copies all 64 pairs' level-0 planes from pinned host memory,
+    # rebuilds the 128 pyramids (same storage, so the item table stays valid), aligns the
+    # batch and reads the 64 result records back
+    res_host = torch.empty_like(B.results, device="cpu").pin_memory()
+
+    def e2e_step():
+        for i in range(len(pairs)):
+            for j in range(4):
+                planes[i][j].copy_(host[4 * i + j], non_blocking=True)
+            p = pairs[i]
+            pyr[i][0].build(planes[i][0], planes[i][1], p["K"])
+            pyr[i][1].build(planes[i][2], planes[i][3], p["K"])
+        B.replay()
+        res_host.copy_(B.results, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    evs2 = []
+    for _ in range(max(1, args.steps // 4)):
+        flush.fill_(rank & 0xff)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        e2e_step()
+        e1.record(stream)
+        evs2.append((e0, e1))
+    torch.cuda.synchronize()
+    e2e_ms = float(np.mean([a.elapsed_time(b) for a, b in evs2]))
+    h2d = sum(int(t.numel()) * 4 for t in host)
+
+    # the per-pair form on the same batch (one rgbid_align per pair), and pose agreement
+    res_b = B.all_results()
+    ps = [R.rgbid_default_params(levels=p["levels"], iters=p["iters"]) for p in pairs]
+    wss = [R.new_workspace(pyr[i][0].desc, ps[i], device=dev) for i in range(len(pairs))]
+    rs = [R.result_tensor(device=dev) for _ in pairs]
+
+    def plain_pass():
+        for i, p in enumerate(pairs):
+            R.rgbid_align(pyr[i][0].desc, pyr[i][1].desc, p["T_init"], ps[i], wss[i], rs[i])
+
+    plain_pass()
+    torch.cuda.synchronize()
+    plain_ms = []
+    for _ in range(3):
+        flush.fill_(rank & 0xff)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plain_pass()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        plain_ms.append(e0.elapsed_time(e1))
+    res_p = [R.parse_result(r) for r in rs]
+
+    def pose_err(Ta, Tb):
+        E = np.linalg.inv(Ta) @ Tb
+        return (float(np.arccos(np.clip((np.trace(E[:3, :3]) - 1) / 2, -1, 1))), float(np.linalg.norm(E[:3, 3])))
+
+    d_plain = [pose_err(a["T"], b["T"]) for a, b in zip(res_b, res_p)]
+    d_truth = [pose_err(a["T"], p["T_gt"])[0] for a, p in zip(res_b, pairs)]
+
+    t = torch.tensor([total_ms, e2e_ms], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms, e2e_ms = t.tolist()
+    if rank != 0:
+        dist.destroy_process_group()
+        return
+    step_ms = total_ms / args.steps
+    value = world * BATCH_N * args.steps / (total_ms / 1000.0)
+    peak, peak_kind = measured_peaks()
+    achieved = bytes_per_unit * units / (step_ms / 1000.0) / 1e9
+    cpu = None
+    if not args.no_cpu_baseline:
+        r = run_oracle_batch_sample(reduced=(args.precision == "bf16"))
+        cpu = {"value": r["alignments"] / r["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "one pair of each resolution (320x240, 640x480, 960x720, 1280x960), one thread, "
+                         "numpy float64"}
+    line = {
+        "metric": BATCH_METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": batch_config_dict(args.precision, shape),
+        "e2e": {"value": world * BATCH_N / (e2e_ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": int(B.results.numel())},
+        "roofline": {"bound": "hbm", "kernel": "batch_align_kernel", "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "launches": args.steps, "units_per_launch": units,
+                     "avg_launch_us": 1000.0 * step_ms},
+        "per_pair_form": {"value": BATCH_N / (float(np.median(plain_ms)) / 1000.0), "unit": UNIT,
+                          "ms_per_batch": float(np.median(plain_ms))},
+        "pose_check": {"max_vs_per_pair_form_rad": max(d[0] for d in d_plain),
+                       "max_vs_per_pair_form_m": max(d[1] for d in d_plain),
+                       "median_vs_truth_rad": float(np.median(d_truth)), "max_vs_truth_rad": float(np.max(d_truth)),
+                       "status": sorted(set(r["status"] for r in res_b))},
+        "cpu_baseline": cpu, "clocks": clk, "gpu_launches": args.steps, "wall_s_timed": t_wall,
+    }
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.workload == "batch":
+        (reference_batch if args.impl == "reference" else native_batch)(args)
+    elif args.impl == "reference":
         reference(args)
     else:
         native(args)
