@@ -12,3 +12,4 @@ formula per step, with no blocking, fusion or reordering.  See
 labels) and the readings taken where the paper is silent or garbled.
 """
 from .rgbid_oracle import *  # noqa: F401,F403
+from . import cnn_oracle  # noqa: F401  (the learned initialiser's network)

@@ -188,8 +188,8 @@ def build_pyramid(I0, W0, K0, levels: int) -> list:
 def round_bf16(x) -> np.ndarray:
     """Round to bfloat16 (round to nearest, ties to even), via float32, as float64.
 
-    Storage of the reduced-precision form (SURVEY extension X1): each level's
-    intensity is held as bfloat16."""
+    Storage of the reduced-precision form: each level's intensity is held as
+    bfloat16."""
     f = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
     u = f.view(np.uint32).astype(np.uint64)
     lsb = (u >> np.uint64(16)) & np.uint64(1)
