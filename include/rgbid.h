@@ -107,6 +107,9 @@ typedef struct {
     int pad_;
     double nu0, nu_lo, nu_hi;    /* 5, 2, 10; needs (nu_lo + nu_hi) >= 1.4 (nu_hi - nu_lo) */
     rgbid_timing* timing;        /* optional kernel timing (NULL: none) */
+    const int* level_iters;      /* optional DEVICE array of RGBID_MAX_LEVELS ints read by the kernels
+                                    (rgbid_align only): level l runs min(iters[l], level_iters[l])
+                                    iterations; the launches of the others exit at once.  NULL: iters. */
 } rgbid_align_params;
 
 /* Result of an alignment (or of one evaluated step).  Lives in device memory
@@ -282,6 +285,90 @@ int rgbid_align_batched(const rgbid_batch_item* d_items, int n_items, int precis
 int rgbid_batch_autotune(const rgbid_batch_item* d_items, int n_items, int precision,
                          const rgbid_align_params* params, void* workspace, size_t workspace_bytes,
                          int reps, rgbid_batch_config* best, float* best_ms, void* stream);
+
+/* ---------------------------------------------------------------- learned initialiser
+ * A small network that proposes the initial twist of an alignment from the
+ * 80x60 pyramid level of both frames, with a log-variance saying how far to
+ * trust it.  The paper has no learned part; this is the project's extension.
+ * When the proposal is confident, the alignment starts from it and skips the
+ * coarsest levels; otherwise the plain coarse-to-fine alignment runs
+ * unchanged, and in both cases the Gauss-Newton alignment decides the pose.
+ *
+ * Network (activations NHWC bfloat16, batch first):
+ *   x   [B, 60, 80, 4]  I_A - 0.5, W_A, I_B - 0.5, W_B of the 80x60 level
+ *   c1..c4  3x3 convolutions (cross-correlation), stride 2, zero padding 1,
+ *           4 -> 32 -> 32 -> 64 -> 64 channels, ReLU: 30x40, 15x20, 8x10, 4x5
+ *   f1  fully connected 1280 -> 256 (c4 flattened in NHWC order), ReLU
+ *   f2  fully connected 256 -> 7: y[0..5] = twist / RGBID_NET_TWIST_SCALE
+ *       (translation t then rotation vector w of T = [exp([w]x), t; 0, 1]),
+ *       y[6] = s, the log-variance of the scaled twist
+ * Loss (mean over the batch): 0.5 exp(-s) |y[0..5] - target|^2 + 3 s.
+ * Parameters: one float32 array (master copy); layer l's weights start at
+ * rgbid_net_param_offset(l, 0) stored [kh][kw][c_in][c_out] (convolutions)
+ * or [in][out] (fully connected), its biases at rgbid_net_param_offset(l, 1);
+ * every tensor starts on a multiple of 64 floats.  The forward and backward
+ * passes compute on bfloat16 tensor cores (mma.sync m16n8k16, FP32
+ * accumulation): weights, inputs, hidden activations and back-propagated
+ * activation gradients are rounded to bfloat16 where they are stored; the
+ * output, biases and parameter gradients are float32.
+ */
+#define RGBID_NET_IN_H 60
+#define RGBID_NET_IN_W 80
+#define RGBID_NET_IN_C 4
+#define RGBID_NET_OUT 7
+#define RGBID_NET_LAYERS 6
+#define RGBID_NET_TWIST_SCALE 0.1
+
+/* Number of floats of the parameter (and gradient / Adam moment) arrays. */
+size_t rgbid_net_param_count(void);
+
+/* Offset (in floats) of layer `layer`'s weights (what = 0) or biases (what = 1); (size_t)-1 if out of range. */
+size_t rgbid_net_param_offset(int layer, int what);
+
+/* Workspace bytes for batches of up to `batch` inputs (bfloat16 weights,
+ * activations kept for the backward pass, activation gradients). */
+size_t rgbid_net_workspace_bytes(int batch);
+
+/* Fill `params` (device, rgbid_net_param_count floats) with He-uniform weights
+ * U(-sqrt(6/fan_in), sqrt(6/fan_in)) drawn from splitmix64(seed, index), biases 0. */
+int rgbid_net_init(float* params, unsigned long long seed, void* stream);
+
+/* Network inputs of n batch items (device array, as for rgbid_align_batched):
+ * for each item, the level of its ref and cur pyramids that is 80x60 is
+ * packed into x (device, n * 60 * 80 * 4 bfloat16, NHWC).  An item without
+ * an 80x60 level gets zeros.  Errors: INVALID_ARG. */
+int rgbid_net_inputs(const rgbid_batch_item* d_items, int n, int precision, void* x, void* stream);
+
+/* y[batch][7] (float32) of the inputs x (bfloat16 NHWC).  The activations stay
+ * in the workspace for a following rgbid_net_backward on the same inputs. */
+int rgbid_net_forward(const float* params, const void* x, int batch, float* y,
+                      void* workspace, size_t workspace_bytes, void* stream);
+
+/* Parameter gradients (overwritten, float32) for the upstream gradient dy =
+ * dL/dy [batch][7], using the activations of the preceding rgbid_net_forward
+ * with the same params, x, batch and workspace. */
+int rgbid_net_backward(const float* params, const void* x, int batch, const float* dy, float* grad,
+                       void* workspace, size_t workspace_bytes, void* stream);
+
+/* The loss above: writes dy = dL/dy [batch][7] and *loss (device float). */
+int rgbid_net_loss(const float* y, const float* target, int batch, float* dy, float* loss, void* stream);
+
+/* One Adam step (Kingma & Ba 2015, with bias correction; `step` counts from 1)
+ * on params, in place, with moments m and v (device, zero before step 1). */
+int rgbid_net_adam(float* params, const float* grad, float* m, float* v, int step, float lr,
+                   float beta1, float beta2, float eps, void* stream);
+
+/* Turn the network's outputs y [n][7] into the alignments' starting points:
+ * item i of `d_out` = item i of `d_in` (device arrays, may not alias), except
+ * that an item whose log-variance y[i][6] is below max_log_var[k - 1] (host
+ * array of n_tiers thresholds; tier k skips k levels) for some k gets the
+ * proposed pose as T_init and zero iterations on its k coarsest levels, for
+ * the largest such k (at least the finest level is always kept).  Items in no
+ * tier are left as they are (the plain alignment).  skipped (device, n ints,
+ * may be NULL) receives the number of levels skipped per item. */
+#define RGBID_NET_MAX_TIERS 4
+int rgbid_net_plan(const float* y, int n, const float* max_log_var, int n_tiers,
+                   const rgbid_batch_item* d_in, rgbid_batch_item* d_out, int* skipped, void* stream);
 
 /* One step at a fixed pose and level, for inspection and parity testing.
  * `T` (host, 16 doubles) is the pose; `robust` (host, 6 doubles

@@ -36,7 +36,7 @@ class BatchAligner:
     """
 
     def __init__(self, items, precision: int = R.PLANES_F32, params: R.AlignParams | None = None,
-                 device="cuda", tune_cache: str | None = None):
+                 device="cuda", tune_cache: str | None = None, planner_factory=None):
         import torch
         self.precision = precision
         self.params = params if params is not None else R.rgbid_default_params()
@@ -72,6 +72,12 @@ class BatchAligner:
         raw = np.frombuffer(bytes(table), dtype=np.uint8)[: self.n * ctypes.sizeof(R.BatchItem)]
         self.d_items = torch.from_numpy(raw.copy()).to(device)
         self.key = resolution_key(self.items, precision)
+        # with a learned planner the pristine table stays in d_src and every run
+        # writes the planned items (start pose, skipped levels) into d_items
+        self.planner = planner_factory(self.n, precision) if planner_factory is not None else None
+        self.d_src = self.d_items.clone() if self.planner is not None else None
+        if self.planner is not None:
+            self.key += "|learned"
 
     @staticmethod
     def _cost(it) -> float:
@@ -95,6 +101,8 @@ class BatchAligner:
     def tune(self, reps: int = 3, force: bool = False, stream=None) -> R.BatchConfig:
         """Pick the launch shape: the cached one for this resolution mix, else run
         the library's autotuner on this batch and cache its answer."""
+        if self.planner is not None:
+            self.planner.plan(self.d_src, self.d_items, stream)    # tune on the planned work
         hit = self._cache.get(self.key)
         if hit is not None and not force:
             self.config = R.BatchConfig(hit["cluster"], hit["rows_per_warp"], hit["n_clusters"], 0)
@@ -109,7 +117,10 @@ class BatchAligner:
 
     # ------------------------------------------------------------------ execution
     def run(self, stream=None):
-        """Enqueue the batch (one kernel launch)."""
+        """Enqueue the batch: one kernel launch (plus, with a learned planner, the
+        network's input packing, forward pass and plan before it)."""
+        if self.planner is not None:
+            self.planner.plan(self.d_src, self.d_items, stream)
         R.rgbid_align_batched(self.d_items, self.n, self.precision, self.params, self.config, self.workspace,
                               stream)
 

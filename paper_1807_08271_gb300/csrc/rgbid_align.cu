@@ -48,6 +48,8 @@ struct RobustArgs {
     int scale_iters, bisect_steps, estimate_nu;
     float nu0;
     double nu_lo, nu_hi;
+    const int* level_iters;   // device iterations per level (NULL: none skipped)
+    int level, iter;
 };
 
 struct SweepArgs {
@@ -61,7 +63,17 @@ struct SweepArgs {
     float* r_W;
     uint8_t* m_I;
     uint8_t* m_W;
+    const int* level_iters;   // device iterations per level (NULL: none skipped)
+    int level, iter;
 };
+
+// An iteration beyond the device-side count of its level does nothing: every
+// CTA returns before any barrier, atomic or dependent-launch trigger, so the
+// next kernel starts when this grid has finished.  The count is written before
+// the alignment's first kernel runs.
+__device__ __forceinline__ bool iteration_skipped(const int* level_iters, int level, int iter) {
+    return level_iters && iter >= __ldg(level_iters + level);
+}
 
 // ---------------------------------------------------------------- init
 __global__ void init_kernel(InitArgs a) {
@@ -188,6 +200,7 @@ __global__ void __launch_bounds__(kRobustNT) robust_kernel(RobustArgs a) {
     __shared__ float cheb[2][2][kChebK + 1];     // per channel: Clenshaw coefficients a_k, b_k
     __shared__ unsigned bis_mask[2][4];
     __shared__ int bis_end[2][2];
+    if (iteration_skipped(a.level_iters, a.level, a.iter)) return;
     if (threadIdx.x == 0) {
         mbar_init(&mbar[0], 1);
         mbar_init(&mbar[1], 1);
@@ -377,6 +390,7 @@ __global__ void __launch_bounds__(kSweepNT, 2) sweep_kernel(SweepArgs a) {
     __shared__ bool am_last;
     __shared__ WarpPose sh_wp;
     __shared__ RobustParams sh_rob;
+    if (iteration_skipped(a.level_iters, a.level, a.iter)) return;
     pdl_wait();   // the robust parameters (and pose) of this iteration are complete and visible
     if (threadIdx.x < 16) {
         reinterpret_cast<float*>(&sh_wp)[threadIdx.x] = __ldcg(reinterpret_cast<const float*>(&a.st->wp) + threadIdx.x);
@@ -726,6 +740,9 @@ static RobustArgs robust_args(const rgbid_pyramid* ref, const rgbid_pyramid* cur
     ra.nu0 = (float)p->nu0;
     ra.nu_lo = p->nu_lo;
     ra.nu_hi = p->nu_hi;
+    ra.level_iters = nullptr;
+    ra.level = l;
+    ra.iter = 0;
     return ra;
 }
 
@@ -773,8 +790,13 @@ extern "C" int rgbid_align(const rgbid_pyramid* ref, const rgbid_pyramid* cur, c
         sa.res = d_result;
         sa.update = 1;
         sa.min_valid = params->min_valid;
+        ra.level_iters = params->level_iters;
+        sa.level_iters = params->level_iters;
+        sa.level = l;
         rgbid_timing* tm = params->timing;
         for (int it = 0; it < params->iters[l]; ++it) {
+            ra.iter = it;
+            sa.iter = it;
             const bool tr = tm && tm->kernel == RGBID_KERNEL_ROBUST && tm->count < tm->capacity;
             if (tr && cudaEventRecord((cudaEvent_t)tm->ev_start[tm->count], stream) != cudaSuccess) return RGBID_ERR_CUDA;
             if (launch_robust_any(ref->precision, ra, stream) != cudaSuccess) return RGBID_ERR_CUDA;

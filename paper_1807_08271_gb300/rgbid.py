@@ -57,7 +57,7 @@ class AlignParams(Structure):
     _fields_ = [("levels", c_int), ("iters", c_int * MAX_LEVELS), ("scale_iters", c_int),
                 ("bisect_steps", c_int), ("sample_cap", c_int), ("estimate_nu", c_int),
                 ("min_valid", c_int), ("pad_", c_int), ("nu0", c_double), ("nu_lo", c_double),
-                ("nu_hi", c_double), ("timing", POINTER(Timing))]
+                ("nu_hi", c_double), ("timing", POINTER(Timing)), ("level_iters", c_void_p)]
 
 
 class AlignResult(Structure):
@@ -111,6 +111,18 @@ SIGNATURES = [
                                     c_void_p, c_size_t, c_void_p]),
     ("rgbid_batch_autotune", c_int, [c_void_p, c_int, c_int, POINTER(AlignParams), c_void_p, c_size_t, c_int,
                                      POINTER(BatchConfig), POINTER(ctypes.c_float), c_void_p]),
+    ("rgbid_net_param_count", c_size_t, []),
+    ("rgbid_net_param_offset", c_size_t, [c_int, c_int]),
+    ("rgbid_net_workspace_bytes", c_size_t, [c_int]),
+    ("rgbid_net_init", c_int, [c_void_p, ctypes.c_ulonglong, c_void_p]),
+    ("rgbid_net_inputs", c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p]),
+    ("rgbid_net_forward", c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_size_t, c_void_p]),
+    ("rgbid_net_backward", c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    ("rgbid_net_loss", c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
+    ("rgbid_net_adam", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, ctypes.c_float, ctypes.c_float,
+                               ctypes.c_float, ctypes.c_float, c_void_p]),
+    ("rgbid_net_plan", c_int, [c_void_p, c_int, POINTER(ctypes.c_float), c_int, c_void_p, c_void_p, c_void_p,
+                               c_void_p]),
 ]
 
 
@@ -314,6 +326,61 @@ def rgbid_batch_autotune(d_items, n_items: int, precision: int, params: AlignPar
                                       ctypes.byref(ms), _stream_ptr(stream))
     _check("rgbid_batch_autotune", code)
     return best, float(ms.value)
+
+
+NET_IN_H, NET_IN_W, NET_IN_C, NET_OUT, NET_LAYERS = 60, 80, 4, 7, 6
+NET_TWIST_SCALE = 0.1
+
+
+def rgbid_net_param_count() -> int:
+    return int(lib().rgbid_net_param_count())
+
+
+def rgbid_net_param_offset(layer: int, what: int) -> int:
+    return int(lib().rgbid_net_param_offset(layer, what))
+
+
+def rgbid_net_workspace_bytes(batch: int) -> int:
+    return int(lib().rgbid_net_workspace_bytes(batch))
+
+
+def rgbid_net_init(params, seed: int, stream=None):
+    _check("rgbid_net_init", lib().rgbid_net_init(_ptr(params), seed, _stream_ptr(stream)))
+
+
+def rgbid_net_inputs(d_items, n: int, precision: int, x, stream=None):
+    _check("rgbid_net_inputs", lib().rgbid_net_inputs(_ptr(d_items), n, precision, _ptr(x), _stream_ptr(stream)))
+
+
+def rgbid_net_forward(params, x, batch: int, y, workspace, stream=None):
+    _check("rgbid_net_forward", lib().rgbid_net_forward(_ptr(params), _ptr(x), batch, _ptr(y), _ptr(workspace),
+                                                        workspace.numel() * workspace.element_size(),
+                                                        _stream_ptr(stream)))
+
+
+def rgbid_net_backward(params, x, batch: int, dy, grad, workspace, stream=None):
+    _check("rgbid_net_backward", lib().rgbid_net_backward(_ptr(params), _ptr(x), batch, _ptr(dy), _ptr(grad),
+                                                          _ptr(workspace),
+                                                          workspace.numel() * workspace.element_size(),
+                                                          _stream_ptr(stream)))
+
+
+def rgbid_net_loss(y, target, batch: int, dy, loss, stream=None):
+    _check("rgbid_net_loss", lib().rgbid_net_loss(_ptr(y), _ptr(target), batch, _ptr(dy), _ptr(loss),
+                                                  _stream_ptr(stream)))
+
+
+def rgbid_net_adam(params, grad, m, v, step: int, lr: float, beta1: float = 0.9, beta2: float = 0.999,
+                   eps: float = 1e-8, stream=None):
+    _check("rgbid_net_adam", lib().rgbid_net_adam(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), step, lr, beta1,
+                                                  beta2, eps, _stream_ptr(stream)))
+
+
+def rgbid_net_plan(y, n: int, max_log_var, d_in, d_out, skipped=None, stream=None):
+    """``max_log_var``: thresholds of tiers 1.. (tier k skips k coarse levels)."""
+    thr = (ctypes.c_float * max(1, len(max_log_var)))(*[float(t) for t in max_log_var])
+    _check("rgbid_net_plan", lib().rgbid_net_plan(_ptr(y), n, thr, len(max_log_var), _ptr(d_in), _ptr(d_out),
+                                                  _ptr(skipped), _stream_ptr(stream)))
 
 
 # ----------------------------------------------------------------------------- conveniences

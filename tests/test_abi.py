@@ -41,9 +41,10 @@ def test_struct_layouts_match_header(binding, tmp_path):
 int main(void) {{
   printf("%zu %zu %zu %zu %zu\\n", sizeof(rgbid_intrinsics), sizeof(rgbid_level), sizeof(rgbid_pyramid),
          sizeof(rgbid_align_params), sizeof(rgbid_align_result));
-  printf("%zu %zu %zu %zu %zu %zu %zu\\n", offsetof(rgbid_level, IW), offsetof(rgbid_align_params, nu0),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", offsetof(rgbid_level, IW), offsetof(rgbid_align_params, nu0),
          offsetof(rgbid_align_result, cost), offsetof(rgbid_align_result, status), sizeof(rgbid_timing),
-         offsetof(rgbid_timing, units), offsetof(rgbid_align_params, timing));
+         offsetof(rgbid_timing, units), offsetof(rgbid_align_params, timing),
+         offsetof(rgbid_align_params, level_iters));
   return 0;
 }}''')
     exe = tmp_path / "abi"
@@ -55,7 +56,7 @@ int main(void) {{
                          ctypes.sizeof(b.AlignParams), ctypes.sizeof(b.AlignResult)]
     assert sizes[5:] == [b.Level.IW.offset, b.AlignParams.nu0.offset, b.AlignResult.cost.offset,
                          b.AlignResult.status.offset, ctypes.sizeof(b.Timing), b.Timing.units.offset,
-                         b.AlignParams.timing.offset]
+                         b.AlignParams.timing.offset, b.AlignParams.level_iters.offset]
 
 
 def test_host_side_calls_without_a_gpu(binding):
