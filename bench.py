@@ -64,9 +64,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["sequence", "batch"], default="sequence",
+    ap.add_argument("--workload", choices=["sequence", "batch", "learned"], default="sequence",
                     help="sequence: the 640x480 tracking sequence (default); batch: 64 uneven loop-closure "
-                         "pairs in one persistent launch")
+                         "pairs in one persistent launch; learned: held-out 640x480 pairs with the learned "
+                         "start against the plain start")
     ap.add_argument("--precision", choices=["f32", "bf16"], default="f32",
                     help="plane storage: f32, or the reduced-precision form (bf16 I, fp16 W)")
     return ap.parse_args()
@@ -631,10 +632,218 @@ def native_batch(args):
         dist.destroy_process_group()
 
 
+# ----------------------------------------------------------------------------- learned-start workload
+LEARNED_N = 512
+LEARNED_METRIC = ("640x480 alignments/s with the learned start (per pair) at equal or better convergence than "
+                  "the plain start")
+LEARNED_CPU_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+import oracle as O
+from paper_1807_08271_gb300 import synth
+pairs = [synth.make_pair(s, 640, 480, K=(525.0, 525.0, 319.5, 239.5), max_angle_deg=10.0, max_trans=0.15)
+         for s in (11, 12)]
+t0 = time.perf_counter()
+for p in pairs:
+    A = O.build_pyramid(p["I_A"], p["W_A"], p["K"], 4)
+    B = O.build_pyramid(p["I_B"], p["W_B"], p["K"], 4)
+    O.align(A, B, None, O.AlignParams(levels=4, iters=(5, 5, 5, 10)))
+dt = time.perf_counter() - t0
+print(json.dumps({{"alignments": len(pairs), "seconds": dt}}))
+"""
+
+
+def run_oracle_learned_sample() -> dict:
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[k] = "1"
+    out = subprocess.run([sys.executable, "-c", LEARNED_CPU_SNIPPET.format(root=ROOT)], capture_output=True,
+                         text=True, env=env, check=True)
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def learned_config_dict(meta=None):
+    d = {"workload": f"{LEARNED_N} held-out synthetic 640x480 pairs (object scenes, textures unseen in training), "
+                     "relative poses up to 10 deg / 15 cm, no motion prior: the plain start is the identity with "
+                     "the 4-level [10,5,5,5] schedule; the learned start is the network's proposal with the "
+                     "coarsest level(s) skipped by confidence tier (plain otherwise)",
+         "pairs": LEARNED_N, "converged": "final pose within 2 mrad / 5 mm of the plain method's pose started at "
+                                          "the ground truth",
+         "l2": "not flushed: each alignment's pyramids (3.3 MB) are read 15-25 times per alignment by design"}
+    if meta:
+        d["network"] = {k: meta.get(k) for k in ("train_pairs", "epochs", "thresholds")}
+    return d
+
+
+def reference_learned(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    r = run_oracle_learned_sample()
+    value = r["alignments"] / r["seconds"]
+    print(json.dumps({
+        "impl": "reference", "metric": LEARNED_METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": 1, "warmup": 0, "ms_per_step": 1000.0 * r["seconds"] / r["alignments"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": learned_config_dict(),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "two 640x480 pairs aligned from the identity (plain schedule), one thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def native_learned(args):
+    import numpy as np
+    import torch
+
+    from paper_1807_08271_gb300 import rgbid as R
+    from paper_1807_08271_gb300 import learned as Lm
+    from paper_1807_08271_gb300.learned_train import EvalSet, pose_diff, _sized
+    from paper_1807_08271_gb300.synth import gpu as G
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    net = Lm.InitNet.load(Lm.WEIGHTS, max_batch=LEARNED_N)
+    thr = net.meta["thresholds"]
+    bank = G.TextureBank(4242 + rank, n=16)
+    ev = EvalSet(9001 + rank, LEARNED_N, bank, 10.0, 0.15)
+    n_steps = max(1, min(args.steps, LEARNED_N))
+
+    # per-pair forms: one alignment per step, timed with CUDA events on the stream
+    params = R.rgbid_default_params(levels=4, iters=[5, 5, 5, 10])
+    ws = R.new_workspace(ev.pyr[0][0].desc, params)
+    res = R.result_tensor(LEARNED_N)
+    la = Lm.LearnedAligner(_sized(net, 1), thr, levels=4, iters=[5, 5, 5, 10])
+    la.set_pairs([(a.desc, b.desc) for a, b in ev.pyr])
+    timer = R.KernelTimer(R.KERNEL_ROBUST, 25 * n_steps + 8)
+    stream = torch.cuda.current_stream()
+
+    def run(kind, k, timed=False):
+        if kind == "plain":
+            R.rgbid_align(ev.pyr[k][0].desc, ev.pyr[k][1].desc, None, params, ws, res[k])
+        else:
+            la.align(k, ws, res[k])
+
+    out = {}
+    clk = None
+    for kind in ("plain", "learned"):
+        for k in range(max(3, args.warmup)):
+            run(kind, k)
+        torch.cuda.synchronize()
+        if kind == "learned":
+            clocks = ClockSampler(local)
+            clocks.start()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(n_steps):
+            run(kind, k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if kind == "learned":
+            clk = clocks.stop()
+        rr = [R.parse_result(res[k]) for k in range(n_steps)]
+        ok = ev.converged(rr)
+        out[kind] = dict(ms=e0.elapsed_time(e1), converged=float(np.mean(ok)),
+                         iters=float(np.mean([r["iters_done"] for r in rr])),
+                         median_err=float(np.median([pose_diff(r["T"], ev.T_gt[k])[0] for k, r in enumerate(rr)])))
+    # the robust-scale kernel timed live over a separate pass (events around each launch
+    # add their own cost, so the timed value above runs without them)
+    timer.attach(la.params)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(n_steps):
+        run("learned", k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    la.params.timing = None
+    timer_region_ms = e0.elapsed_time(e1)
+
+    # end to end (learned): each step copies the pair's four planes from pinned host memory,
+    # rebuilds both pyramids in place and reads the result record back
+    res_host = torch.empty(R.RESULT_BYTES, dtype=torch.uint8).pin_memory()
+    d = G.make_pairs_gpu(9001 + rank, n_steps, bank, 640, 480, 10.0, 0.15)
+    I_h, W_h = d["I"].cpu().pin_memory(), d["W"].cpu().pin_memory()
+    I_d, W_d = torch.empty_like(d["I"][0]), torch.empty_like(d["W"][0])
+    PA = R.DevicePyramid(640, 480, 4).build(I_d[0], W_d[0], d["K"])
+    PB = R.DevicePyramid(640, 480, 4).build(I_d[1], W_d[1], d["K"])
+    la_e = Lm.LearnedAligner(_sized(net, 1), thr, levels=4, iters=[5, 5, 5, 10])
+    la_e.set_pairs([(PA.desc, PB.desc)])
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(n_steps):
+        I_d.copy_(I_h[k], non_blocking=True)
+        W_d.copy_(W_h[k], non_blocking=True)
+        PA.build(I_d[0], W_d[0], d["K"])
+        PB.build(I_d[1], W_d[1], d["K"])
+        la_e.align(0, ws, res[0])
+        res_host.copy_(res[0], non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+
+    # the batched forms on the whole held-out set (one persistent launch each)
+    res_p, ms_p, _ = ev.run(None, reps=5)
+    from paper_1807_08271_gb300.learned import LearnedPlanner
+    res_l, ms_l, _ = ev.run(lambda m, prec: LearnedPlanner(_sized(net, m), m, prec, thr), reps=5)
+
+    t = torch.tensor([out["learned"]["ms"], e2e_ms], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    learned_ms, e2e_ms = t.tolist()
+    if rank != 0:
+        dist.destroy_process_group()
+        return
+    peak, peak_kind = measured_peaks()
+    k_ms, k_units, k_count = timer.total_ms(), int(timer.t.units), int(timer.t.count)
+    achieved = BYTES_PER_UNIT["f32"] * k_units / (k_ms / 1000.0) / 1e9 if k_ms > 0 else 0.0
+    cpu = None
+    if not args.no_cpu_baseline:
+        r = run_oracle_learned_sample()
+        cpu = {"value": r["alignments"] / r["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "two 640x480 pairs aligned from the identity with the plain schedule, one thread, "
+                         "numpy float64"}
+    line = {
+        "metric": LEARNED_METRIC, "value": world * n_steps / (learned_ms / 1000.0), "unit": UNIT, "n_gpus": world,
+        "steps": n_steps, "warmup": max(3, args.warmup), "ms_per_step": learned_ms / n_steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 alignment, bf16 network",
+        "data": "synthetic", "config": learned_config_dict(net.meta),
+        "e2e": {"value": world * n_steps / (e2e_ms / 1000.0), "unit": UNIT,
+                "h2d_bytes_per_step": 4 * 640 * 480 * 4, "d2h_bytes_per_step": R.RESULT_BYTES},
+        "roofline": {"bound": "hbm", "kernel": "robust_kernel", "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak if peak else None,
+                     "traffic": None, "launches": k_count, "avg_launch_us": 1000.0 * k_ms / max(k_count, 1),
+                     "share_of_step": k_ms / timer_region_ms},
+        "per_pair": {kind: {"alignments_per_s": n_steps / (v["ms"] / 1000.0), "converged_fraction": v["converged"],
+                            "mean_iterations": v["iters"], "median_rot_err_vs_truth_rad": v["median_err"]}
+                     for kind, v in out.items()},
+        "batched": {"plain_alignments_per_s": LEARNED_N / (ms_p / 1000.0),
+                    "learned_alignments_per_s": LEARNED_N / (ms_l / 1000.0),
+                    "plain_converged": float(np.mean(ev.converged(res_p))),
+                    "learned_converged": float(np.mean(ev.converged(res_l)))},
+        # per learned alignment: input packing, bf16 weights, 6 GEMMs and their 6 split-K reductions,
+        # the plan, the alignment's init kernel and 2 launches per scheduled iteration (skipped ones included)
+        "cpu_baseline": cpu, "clocks": clk, "gpu_launches": n_steps * (15 + 1 + 2 * 25),
+    }
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.workload == "batch":
         (reference_batch if args.impl == "reference" else native_batch)(args)
+    elif args.workload == "learned":
+        (reference_learned if args.impl == "reference" else native_learned)(args)
     elif args.impl == "reference":
         reference(args)
     else:

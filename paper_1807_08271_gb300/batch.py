@@ -144,3 +144,48 @@ class BatchAligner:
     def all_results(self) -> list[dict]:
         host = self.results.cpu()
         return [R.parse_result(host[i]) for i in range(self.n)]
+
+
+def main(argv=None):
+    """Align a seeded batch of same-size synthetic pairs with a given launch shape
+    and print the per-launch time (a command-line check of the batched kernel)."""
+    import argparse
+
+    import torch
+
+    from . import synth
+    ap = argparse.ArgumentParser(prog="python -m paper_1807_08271_gb300.batch")
+    ap.add_argument("--size", default="1280x960", help="pair resolution WxH")
+    ap.add_argument("--pairs", type=int, default=16)
+    ap.add_argument("--cluster", type=int, default=8)
+    ap.add_argument("--rows", type=int, default=1)
+    ap.add_argument("--runs", type=int, default=3)
+    ap.add_argument("--seed", type=int, default=3)
+    ap.add_argument("--precision", choices=["f32", "bf16"], default="f32")
+    a = ap.parse_args(argv)
+    w, h = (int(v) for v in a.size.split("x"))
+    prec = R.PLANES_BF16_F16 if a.precision == "bf16" else R.PLANES_F32
+    pairs = synth.make_batch(seed=a.seed, n=a.pairs, sizes=((w, h),))
+    keep, items = [], []
+    for p in pairs:
+        PA = R.DevicePyramid(w, h, p["levels"], prec).build(torch.from_numpy(p["I_A"]).cuda(),
+                                                            torch.from_numpy(p["W_A"]).cuda(), p["K"])
+        PB = R.DevicePyramid(w, h, p["levels"], prec).build(torch.from_numpy(p["I_B"]).cuda(),
+                                                            torch.from_numpy(p["W_B"]).cuda(), p["K"])
+        keep += [PA, PB]
+        items.append(dict(ref=PA.desc, cur=PB.desc, T_init=p["T_init"], levels=p["levels"], iters=p["iters"]))
+    B = BatchAligner(items, precision=prec)
+    B.config = R.BatchConfig(a.cluster, a.rows, 0, 0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for k in range(a.runs):
+        e0.record()
+        B.run()
+        e1.record()
+        torch.cuda.synchronize()
+        print(f"run {k}: {e0.elapsed_time(e1):.3f} ms")
+    res = B.all_results()
+    print("status", sorted(set(r["status"] for r in res)), "iterations", res[0]["iters_done"])
+
+
+if __name__ == "__main__":
+    main()

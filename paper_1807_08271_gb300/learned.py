@@ -184,3 +184,45 @@ class _DevicePtr:
 
     def data_ptr(self) -> int:
         return self._p
+
+
+def main(argv=None):
+    """Time training steps (random inputs) and batch-1 inference of the network
+    (a command-line check of the network kernels)."""
+    import argparse
+
+    import torch
+    ap = argparse.ArgumentParser(prog="python -m paper_1807_08271_gb300.learned")
+    ap.add_argument("--batch", type=int, default=256)
+    ap.add_argument("--steps", type=int, default=20)
+    a = ap.parse_args(argv)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(0)
+    net = InitNet(max_batch=a.batch, seed=1)
+    x = (torch.randn(a.batch, R.NET_IN_H, R.NET_IN_W, R.NET_IN_C, device="cuda", generator=gen) * 0.5)
+    x = x.to(torch.bfloat16).contiguous()
+    t = torch.randn(a.batch, 6, device="cuda", generator=gen)
+    for _ in range(5):
+        net.train_step(x, t, a.batch, 1e-3)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.steps):
+        net.train_step(x, t, a.batch, 1e-3)
+    e1.record()
+    torch.cuda.synchronize()
+    print(f"training step (batch {a.batch}): {e0.elapsed_time(e1) / a.steps:.3f} ms, loss {float(net.loss):.4f}")
+    x1 = x[:1].contiguous()
+    for _ in range(5):
+        net.forward(x1, 1)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(a.steps):
+        net.forward(x1, 1)
+    e1.record()
+    torch.cuda.synchronize()
+    print(f"forward (batch 1): {e0.elapsed_time(e1) / a.steps:.3f} ms")
+
+
+if __name__ == "__main__":
+    main()
