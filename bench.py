@@ -50,6 +50,21 @@ N_FRAMES = 300
 # once -- 4 B each as float32 planes, 2 B each in the reduced-precision form
 BYTES_PER_UNIT = {"f32": 16, "bf16": 8}
 
+# FP32 operations (FMA, multiply or add, each counted once) per pixel-iteration of the
+# sweep: warp 20, bilinear taps and transfer 18, gradients/Jacobians/lambda_n 45,
+# weights 10, accumulation of both residuals 2 x 35, counts 2
+OPS_PER_PIXEL = 165
+# FP32 lanes x SMs x maximum SM clock of GB300 (the recipe's unit counts and clock)
+ALU_PEAK_GOPS = 128 * 152 * 2.07
+
+
+def alu_roofline(kernel: str, units_per_launch: float, ms_per_launch: float) -> dict:
+    achieved = OPS_PER_PIXEL * units_per_launch / (ms_per_launch / 1000.0) / 1e9 if ms_per_launch > 0 else 0.0
+    return {"bound": "alu", "kernel": kernel, "ops_per_unit": OPS_PER_PIXEL, "achieved": achieved,
+            "peak": ALU_PEAK_GOPS, "peak_kind": "nominal (128 FP32 lanes x 152 SMs x 2.07 GHz)",
+            "unit": "Gop/s", "frac": achieved / ALU_PEAK_GOPS}
+
+
 # DRAM bytes (read + write) per unit (level pixel for the sweep, sample pixel for
 # the robust-scale kernel) from the ncu captures summarised in
 # profiles/robust_kernel_seq640_level0.md and profiles/sweep_kernel_seq640_level0.md
@@ -391,7 +406,10 @@ def native(args):
         "config": config_dict(precision=args.precision),
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 2 * W * H * 4,
                 "d2h_bytes_per_step": R.RESULT_BYTES},
-        "roofline": roofline, "roofline_other_kernels": others, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": gpu_launches,
+        "roofline": roofline, "roofline_other_kernels": others,
+        "alu_roofline": alu_roofline("sweep_kernel", rooflines["sweep_kernel"]["units_per_launch"],
+                                     rooflines["sweep_kernel"]["avg_launch_us"] / 1000.0),
+        "cpu_baseline": cpu, "clocks": clk, "gpu_launches": gpu_launches,
         "wall_s_timed": t_wall, "max_rot_err_vs_truth_rad": rot, "pose_check": pose_check,
     }
     print(json.dumps(line))
@@ -619,6 +637,7 @@ def native_batch(args):
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
                      "launches": args.steps, "units_per_launch": units,
                      "avg_launch_us": 1000.0 * step_ms},
+        "alu_roofline": alu_roofline("batch_align_kernel", units, step_ms),
         "per_pair_form": {"value": BATCH_N / (float(np.median(plain_ms)) / 1000.0), "unit": UNIT,
                           "ms_per_batch": float(np.median(plain_ms))},
         "pose_check": {"max_vs_per_pair_form_rad": max(d[0] for d in d_plain),
