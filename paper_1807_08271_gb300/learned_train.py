@@ -78,7 +78,44 @@ def build_dataset(seed: int, n: int, bank, precision: int, max_angle: float, max
     return torch.cat(xs), torch.cat(ys), np.concatenate(ts)
 
 
-def train(net: InitNet, X, Y, epochs: int, batch: int, lr: float, seed: int, log):
+def augment(xb, yb, gen):
+    """Label-consistent augmentation of a batch (torch ops on the device):
+    swap A and B (the twist of the inverse pose), mirror both frames left-right
+    (t -> (-tx, ty, tz), w -> (wx, -wy, -wz)) and up-down (t -> (tx, -ty, tz),
+    w -> (-wx, wy, -wz)); the 80x60 level's principal point is the image centre,
+    so mirroring keeps the intrinsics.  Each sample gets each transform with
+    probability 1/2."""
+    import torch
+    n = xb.shape[0]
+    r = torch.rand((n, 3), generator=gen, device=xb.device) < 0.5
+    x, y = xb.clone(), yb.clone()
+    s = r[:, 0]
+    if bool(s.any()):
+        # inverse of the decoupled pose: R' = R^T, t' = -R^T t, w' = -w
+        tw = y[s].double() * R.NET_TWIST_SCALE
+        w = tw[:, 3:]
+        th = torch.linalg.norm(w, dim=1, keepdim=True).clamp_min(1e-12)
+        k = w / th
+        K = torch.zeros((w.shape[0], 3, 3), dtype=torch.float64, device=x.device)
+        K[:, 0, 1], K[:, 0, 2], K[:, 1, 2] = -k[:, 2], k[:, 1], -k[:, 0]
+        K = K - K.transpose(1, 2)
+        st, ct = torch.sin(th)[:, :, None], torch.cos(th)[:, :, None]
+        Rm = torch.eye(3, dtype=torch.float64, device=x.device) + st * K + (1 - ct) * (K @ K)
+        t_new = -(Rm.transpose(1, 2) @ tw[:, :3, None])[:, :, 0]
+        y[s] = (torch.cat([t_new, -w], dim=1) / R.NET_TWIST_SCALE).float()
+        x[s] = x[s][..., [2, 3, 0, 1]]
+    h = r[:, 1]
+    if bool(h.any()):
+        x[h] = torch.flip(x[h], dims=[2])
+        y[h] = y[h] * torch.tensor([-1.0, 1.0, 1.0, 1.0, -1.0, -1.0], device=y.device)
+    v = r[:, 2]
+    if bool(v.any()):
+        x[v] = torch.flip(x[v], dims=[1])
+        y[v] = y[v] * torch.tensor([1.0, -1.0, 1.0, -1.0, 1.0, -1.0], device=y.device)
+    return x.contiguous(), y.contiguous()
+
+
+def train(net: InitNet, X, Y, epochs: int, batch: int, lr: float, seed: int, log, augmented: bool = True):
     import torch
     n = X.shape[0]
     gen = torch.Generator(device=X.device)
@@ -96,6 +133,8 @@ def train(net: InitNet, X, Y, epochs: int, batch: int, lr: float, seed: int, log
             idx = perm[b * batch:(b + 1) * batch]
             xb = X.index_select(0, idx).contiguous()
             yb = Y.index_select(0, idx).contiguous()
+            if augmented:
+                xb, yb = augment(xb, yb, gen)
             rate = lr * min(1.0, (s + 1) / warm) * 0.5 * (1.0 + math.cos(math.pi * s / steps))
             acc += net.train_step(xb, yb, batch, rate)[0]
             s += 1
@@ -342,6 +381,7 @@ def main(argv=None):
     ap.add_argument("--max-angle", type=float, default=10.0)
     ap.add_argument("--max-trans", type=float, default=0.15)
     ap.add_argument("--cal-pairs", type=int, default=2048)
+    ap.add_argument("--no-augment", action="store_true")
     ap.add_argument("--eval-pairs", type=int, default=256)
     ap.add_argument("--from-weights", default=None,
                     help="skip the training set and training: calibrate and evaluate these weights")
@@ -369,7 +409,7 @@ def main(argv=None):
         Xv, Yv, _ = build_dataset(a.seed + 7919, a.val, bank, R.PLANES_F32, a.max_angle, a.max_trans, a.chunk, log)
         log(f"dataset: {X.shape[0]} training, {Xv.shape[0]} held-out pairs")
         net = InitNet(max_batch=a.batch, seed=a.seed)
-        hist = train(net, X, Y, a.epochs, a.batch, a.lr, a.seed, log)
+        hist = train(net, X, Y, a.epochs, a.batch, a.lr, a.seed, log, augmented=not a.no_augment)
         yv = predict(net, Xv)
         lv = Yv.cpu().numpy().astype(np.float64)
         er, et = proposal_errors(yv, lv)
