@@ -15,13 +15,14 @@ value      frames (= 640x480 alignments) per second over all ranks, inputs
            timed intervals.
 e2e        the same with every step's frame copied from pinned host memory and
            its result struct read back to pinned host memory inside the step.
-roofline   the dominant kernel by share of its timed region: the robust-scale
-           kernel is timed live (CUDA events around each launch, on the
-           tracker's stream) over the device-resident steps, the sweep kernel
-           over the end-to-end steps; achieved = 16 B x units per launch /
-           launch time (units: level pixels for the sweep, systematic-sample
-           pixels for the robust-scale kernel).  The other kernel is reported
-           under roofline_other_kernels.
+roofline   the dominant kernel by share of its timed region: each alignment
+           kernel is timed live (CUDA events around each of its launches, on the
+           tracker's stream) over its own pass of 60 device-resident steps, since
+           events between launches break the programmatic dependent launches and
+           would slow the value pass; achieved = 16 B x units per launch / launch
+           time (units: level pixels for the sweep, systematic-sample pixels for
+           the robust-scale kernel).  The other kernel is reported under
+           roofline_other_kernels.
 
 Multi-GPU: every rank tracks its own independent sequence (seed = rank), no
 collective on the data path ("scaling": "weak").
@@ -69,7 +70,7 @@ def alu_roofline(kernel: str, units_per_launch: float, ms_per_launch: float) -> 
 # the robust-scale kernel) from the ncu captures summarised in
 # profiles/robust_kernel_seq640_level0.md and profiles/sweep_kernel_seq640_level0.md
 # (level-0 launches, cold caches); set to None whenever those kernels change.
-TRAFFIC_PER_UNIT = {"robust_kernel": 3146752 / 19200, "sweep_kernel": 6176512 / 307200}
+TRAFFIC_PER_UNIT = {"robust_kernel": 3191296 / 19200, "sweep_kernel": 6765056 / 307200}
 
 
 def parse():
@@ -249,8 +250,8 @@ def native(args):
     per_step_launches = sum(ITERS[:LEVELS])
     # the robust-scale kernel is timed live over the device-resident steps, the
     # sweep kernel over the end-to-end steps (one kernel per timed region)
-    timer_robust = R.KernelTimer(R.KERNEL_ROBUST, per_step_launches * args.steps + 8)
-    timer_sweep = R.KernelTimer(R.KERNEL_SWEEP, per_step_launches * args.steps + 8)
+    timer_robust = R.KernelTimer(R.KERNEL_ROBUST, (per_step_launches + 1) * max(1, min(args.steps, 60)) + 8)
+    timer_sweep = R.KernelTimer(R.KERNEL_SWEEP, per_step_launches * max(1, min(args.steps, 60)) + 8)
     prec = R.PLANES_BF16_F16 if args.precision == "bf16" else R.PLANES_F32
     bytes_per_unit = BYTES_PER_UNIT[args.precision]
     trk = Tracker(W, H, K, levels=LEVELS, iters=ITERS, kf_every=KF_EVERY, max_frames=N_FRAMES + 1, device=dev,
@@ -259,8 +260,9 @@ def native(args):
     launches = {"n": 0}
 
     def kernels_in_step(k):
-        # pyramid (levels) + predict + init + 2 per iteration + fuse, or switch (compose + init_kf) + kf pyramid
-        n = LEVELS + 1 + 1 + 2 * per_step_launches + LEVELS
+        # pyramid (levels) + predict + init + 2 per iteration + the closing reduction
+        # + fuse, or switch (compose + init_kf) + kf pyramid
+        n = LEVELS + 1 + 1 + 2 * per_step_launches + 1 + LEVELS
         n += 2 if k % KF_EVERY == 0 else 1
         return n
 
@@ -308,8 +310,8 @@ def native(args):
     run_steps(args.warmup, timed=False)
     torch.cuda.synchronize()
 
-    # ---- device-resident timed region
-    timer_robust.attach(trk.params)
+    # ---- device-resident timed region (no per-launch events: they would break the
+    #      programmatic dependent launches between the kernels)
     clocks = ClockSampler(local)
     clocks.start()
     if dist:
@@ -322,24 +324,33 @@ def native(args):
         dist.barrier()
     t_wall = time.perf_counter() - t_wall
     clk = clocks.stop()
-    trk.params.timing = None
     step_ms = [a.elapsed_time(b) for a, b in evs]
     total_ms = float(sum(step_ms))
     gpu_launches = launches["n"]
 
-    # ---- end-to-end through host buffers
+    # ---- end-to-end through host buffers (no per-launch events either)
     res_host = torch.empty(R.RESULT_BYTES, dtype=torch.uint8).pin_memory()
     run_steps(2, timed=False, e2e=True, res_host=res_host)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    timer_sweep.attach(trk.params)
     evs2 = run_steps(args.steps, timed=True, e2e=True, res_host=res_host)
     torch.cuda.synchronize()
-    trk.params.timing = None
     e2e_ms = float(sum(a.elapsed_time(b) for a, b in evs2))
-    kern = {"robust_kernel": (timer_robust.total_ms(), int(timer_robust.t.units), int(timer_robust.t.count), total_ms),
-            "sweep_kernel": (timer_sweep.total_ms(), int(timer_sweep.t.units), int(timer_sweep.t.count), e2e_ms)}
+
+    # ---- the two alignment kernels timed live, each over its own pass of device-resident
+    #      steps (CUDA events around every launch of that kernel on the tracker's stream)
+    kern = {}
+    n_kern = max(1, min(args.steps, 60))
+    for name, timer in (("robust_kernel", timer_robust), ("sweep_kernel", timer_sweep)):
+        timer.reset()
+        timer.attach(trk.params)
+        evk = run_steps(n_kern, timed=True)
+        torch.cuda.synchronize()
+        trk.params.timing = None
+        kern[name] = (timer.total_ms(), int(timer.t.units), int(timer.t.count),
+                      float(sum(a.elapsed_time(b) for a, b in evk)))
+    launches["n"] = gpu_launches
 
     # pose sanity: frames of the last pass vs ground truth
     traj = trk.trajectory()
@@ -849,8 +860,9 @@ def native_learned(args):
                     "plain_converged": float(np.mean(ev.converged(res_p))),
                     "learned_converged": float(np.mean(ev.converged(res_l)))},
         # per learned alignment: input packing, bf16 weights, 6 GEMMs and their 6 split-K reductions,
-        # the plan, the alignment's init kernel and 2 launches per scheduled iteration (skipped ones included)
-        "cpu_baseline": cpu, "clocks": clk, "gpu_launches": n_steps * (15 + 1 + 2 * 25),
+        # the plan, the alignment's init kernel, 2 launches per scheduled iteration (skipped ones
+        # included) and the closing reduction
+        "cpu_baseline": cpu, "clocks": clk, "gpu_launches": n_steps * (15 + 1 + 2 * 25 + 1),
     }
     print(json.dumps(line))
     if dist:

@@ -50,15 +50,18 @@ struct RobustArgs {
     double nu_lo, nu_hi;
     const int* level_iters;   // device iterations per level (NULL: none skipped)
     int level, iter;
+    // reduction of the previous sweep's block partials, solve and update
+    const float2* partials;
+    rgbid_align_result* res;
+    int update;               // 0: results only (one evaluated step), 1: also update the pose
+    int min_valid;
+    int finalize_only;        // 1: finish the previous sweep and stop (no robust estimation)
 };
 
 struct SweepArgs {
     LevelDev A, B;
     AlignState* st;
     float* partials;
-    rgbid_align_result* res;
-    int update;
-    int min_valid;
     float* r_I;
     float* r_W;
     uint8_t* m_I;
@@ -67,10 +70,11 @@ struct SweepArgs {
     int level, iter;
 };
 
-// An iteration beyond the device-side count of its level does nothing: every
-// CTA returns before any barrier, atomic or dependent-launch trigger, so the
-// next kernel starts when this grid has finished.  The count is written before
-// the alignment's first kernel runs.
+// An iteration beyond the device-side count of its level does nothing.  Its
+// CTAs still wait for the preceding grid (griddepcontrol.wait) before they
+// return, and they never trigger the next launch, so the chain of dependent
+// launches stays ordered end to end whichever levels are skipped.  The counts
+// are written before the alignment's first kernel runs.
 __device__ __forceinline__ bool iteration_skipped(const int* level_iters, int level, int iter) {
     return level_iters && iter >= __ldg(level_iters + level);
 }
@@ -87,7 +91,7 @@ __global__ void init_kernel(InitArgs a) {
     __syncwarp();
     warp_make_pose(T, &st->wp);
     if (threadIdx.x != 0) return;
-    st->counter = 0u;
+    st->pending = 0u;
     st->status = RGBID_OK;
     st->iters_done = 0;
     st->iters_skipped = 0;
@@ -129,12 +133,43 @@ struct ClusterSum {
     // v: per-thread partials of NV values (NV <= 8: one warp sum each; NV = 96: three
     // reduce-scatter chunks).  On return out[0..NV) holds the cluster totals,
     // bit-identical in every CTA (same data, same combine order).
+    // Threads t < NV of every CTA call this with the CTA's compensated partial of
+    // value t; each returns the cluster total (same pairwise tree over the ranks
+    // in every CTA).  The caller separates rounds with __syncthreads and next().
+    template <int NV>
+    __device__ __forceinline__ F2 exchange(int t, F2 s) {
+        const int par = round & 1;
+        const uint32_t phase = (uint32_t)(round >> 1) & 1u;
+        if (t == 0) mbar_arrive_expect_tx(&mbar[par], (uint32_t)(CL * NV * sizeof(float2)));
+        const uint32_t src = smem_addr(&recv[par][rank][t]);
+        const uint32_t bar = smem_addr(&mbar[par]);
+#pragma unroll
+        for (int r = 0; r < CL; ++r) st_async_f2(map_to_rank(src, r), s.hi, s.lo, map_to_rank(bar, r));
+        const long long t0 = clock64();
+        while (!mbar_try_wait(&mbar[par], phase)) {
+            if (clock64() - t0 > kWaitBudgetCycles) {
+                atomicAdd(timeouts, 1);
+                break;
+            }
+        }
+        // fixed pairwise tree over the CL source CTAs
+        F2 acc[CL];
+#pragma unroll
+        for (int r = 0; r < CL; ++r) {
+            const float2 p = recv[par][r][t];
+            acc[r] = F2{p.x, p.y};
+        }
+#pragma unroll
+        for (int step = 1; step < CL; step <<= 1)
+#pragma unroll
+            for (int r = 0; r + step < CL; r += 2 * step) acc[r].add(acc[r + step]);
+        return acc[0];
+    }
+    __device__ __forceinline__ void next() { ++round; }
+
     template <int NV>
     __device__ __forceinline__ void run(float (&v)[NV]) {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        const int par = round & 1;
-        const uint32_t phase = (uint32_t)(round >> 1) & 1u;
-        if (threadIdx.x == 0) mbar_arrive_expect_tx(&mbar[par], (uint32_t)(CL * NV * sizeof(float2)));
         if constexpr (NV <= 8) {
 #pragma unroll
             for (int j = 0; j < NV; ++j) {
@@ -157,32 +192,10 @@ struct ClusterSum {
             F2 s{0.f, 0.f};
 #pragma unroll
             for (int w = 0; w < kRobustNT / 32; ++w) s.add(red_w[w][t]);
-            const uint32_t src = smem_addr(&recv[par][rank][t]);
-            const uint32_t bar = smem_addr(&mbar[par]);
-#pragma unroll
-            for (int r = 0; r < CL; ++r) st_async_f2(map_to_rank(src, r), s.hi, s.lo, map_to_rank(bar, r));
-            const long long t0 = clock64();
-            while (!mbar_try_wait(&mbar[par], phase)) {
-                if (clock64() - t0 > kWaitBudgetCycles) {
-                    atomicAdd(timeouts, 1);
-                    break;
-                }
-            }
-            // fixed pairwise tree over the CL source CTAs
-            F2 acc[CL];
-#pragma unroll
-            for (int r = 0; r < CL; ++r) {
-                const float2 p = recv[par][r][t];
-                acc[r] = F2{p.x, p.y};
-            }
-#pragma unroll
-            for (int step = 1; step < CL; step <<= 1)
-#pragma unroll
-                for (int r = 0; r + step < CL; r += 2 * step) acc[r].add(acc[r + step]);
-            out[t] = acc[0].value();
+            out[t] = exchange<NV>(t, s).value();
         }
         __syncthreads();
-        ++round;
+        next();
     }
 };
 
@@ -200,17 +213,153 @@ __global__ void __launch_bounds__(kRobustNT) robust_kernel(RobustArgs a) {
     __shared__ float cheb[2][2][kChebK + 1];     // per channel: Clenshaw coefficients a_k, b_k
     __shared__ unsigned bis_mask[2][4];
     __shared__ int bis_end[2][2];
-    if (iteration_skipped(a.level_iters, a.level, a.iter)) return;
+    __shared__ F2 fin2[kRobustNT / 32][kSlots];
+    __shared__ double T_sh[16];
+    __shared__ double totd[kSlots];
+    __shared__ float Hs[36], gs[6];
+    __shared__ float xi_f[6];
+    __shared__ double xi_d[6];
+    __shared__ int ok_flag;
+    if (!a.finalize_only && iteration_skipped(a.level_iters, a.level, a.iter)) {
+        pdl_wait();
+        return;
+    }
     if (threadIdx.x == 0) {
         mbar_init(&mbar[0], 1);
         mbar_init(&mbar[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     cl.sync();   // every barrier of the cluster is initialised before any remote store
-    pdl_wait();  // the previous iteration's pose update is complete and visible
+    pdl_wait();  // the previous sweep's partials (and the state) are complete and visible
     pdl_trigger();
-    if (threadIdx.x < 16) reinterpret_cast<float*>(&sh_wp)[threadIdx.x] = __ldcg(reinterpret_cast<const float*>(&a.st->wp) + threadIdx.x);
-    __syncthreads();
+    ClusterSum<CL> R{red_w, recv, tot, mbar, &a.st->timeouts, (uint32_t)rank, 0};
+    const unsigned int nb = __ldcg(&a.st->pending);   // the same value in every CTA
+
+    // ---- finish the previous sweep: the CTAs sum disjoint subsets of its block
+    //      partials (compensated pairs), one exchange gives every CTA the totals,
+    //      and every CTA solves H xi = -g and updates its copy of the pose
+    if (nb) {
+        const int t = (int)threadIdx.x, lane = t & 31, grp = t >> 5;
+        if (t < 16) T_sh[t] = __ldcg(a.st->T + t);
+        F2 acc{0.f, 0.f};
+        for (unsigned int b = (unsigned)rank + (unsigned)CL * (unsigned)grp; b < nb; b += (unsigned)CL * (kRobustNT / 32)) {
+            const float2 v = __ldcg(a.partials + (size_t)b * kSlots + lane);
+            acc.add(F2{v.x, v.y});
+        }
+        fin2[grp][lane] = acc;
+        __syncthreads();
+        if (t < kSlots) {
+            F2 c{0.f, 0.f};
+#pragma unroll
+            for (int w = 0; w < kRobustNT / 32; ++w) c.add(fin2[w][t]);
+            const F2 T2 = R.template exchange<kSlots>(t, c);
+            tot[t] = T2.value();
+            totd[t] = (double)T2.hi + (double)T2.lo;
+        }
+        __syncthreads();
+        R.next();
+        if (t < 32) {
+            if (lane < 21) {
+                int i = 0, rem = lane;
+                while (rem >= 6 - i) { rem -= 6 - i; ++i; }
+                const int j = i + rem;
+                Hs[i * 6 + j] = tot[lane];
+                Hs[j * 6 + i] = tot[lane];
+            } else if (lane < 27) {
+                gs[lane - kSlotG] = tot[lane];
+            }
+            __syncwarp();
+            if (lane == 0) {
+                const int nI = (int)tot[kSlotNI], nW = (int)tot[kSlotNW];
+                bool okl = a.update && (nI + nW) >= a.min_valid;
+                if constexpr (PREC == RGBID_PLANES_BF16_F16) {
+                    // reduced-precision planes: the 6x6 solve runs in FP64
+                    double xi[6];
+                    okl = okl && cholesky_solve6_packed_d(Hs, gs, xi);
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) xi_d[i] = okl ? xi[i] : 0.0;
+                } else {
+                    float xi[6];
+                    okl = okl && cholesky_solve6_packed(Hs, gs, xi);
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) xi_f[i] = okl ? xi[i] : 0.f;
+                }
+                ok_flag = okl ? 1 : 0;
+            }
+            __syncwarp();
+            if (ok_flag) {
+                if constexpr (PREC == RGBID_PLANES_BF16_F16) {
+                    double xi[6];
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) xi[i] = xi_d[i];
+                    warp_apply_update_d(xi, T_sh);
+                } else {
+                    float xi[6];
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) xi[i] = xi_f[i];
+                    warp_apply_update(xi, T_sh);
+                }
+                warp_make_pose(T_sh, &sh_wp);
+            } else if (lane < 16) {
+                reinterpret_cast<float*>(&sh_wp)[lane] = __ldcg(reinterpret_cast<const float*>(&a.st->wp) + lane);
+            }
+            __syncwarp();
+            if (rank == 0) {
+                // the step's results and the new state (written once, by CTA 0)
+                AlignState* st = a.st;
+                rgbid_align_result* res = a.res;
+                const double td = totd[lane];
+                const float tf = tot[lane];
+                if (lane < 21) {
+                    int i = 0, rem = lane;
+                    while (rem >= 6 - i) { rem -= 6 - i; ++i; }
+                    const int j = i + rem;
+                    res->H[i * 6 + j] = td;
+                    res->H[j * 6 + i] = td;
+                } else if (lane < 27) {
+                    res->g[lane - kSlotG] = td;
+                } else if (lane == kSlotCost) {
+                    res->cost = td;
+                } else if (lane == kSlotNI) {
+                    res->n_valid[0] = (int)tf;
+                } else if (lane == kSlotNW) {
+                    res->n_valid[1] = (int)tf;
+                } else if (lane == 30) {
+                    const RobustParams rob = st->rob;     // the parameters the sweep used
+                    res->mu[0] = rob.mu[0]; res->mu[1] = rob.mu[1];
+                    res->sigma[0] = rob.sigma[0]; res->sigma[1] = rob.sigma[1];
+                    res->nu[0] = rob.nu[0]; res->nu[1] = rob.nu[1];
+                }
+                if (a.update) {
+                    if (ok_flag && lane < 16) {
+                        reinterpret_cast<float*>(&st->wp)[lane] = reinterpret_cast<const float*>(&sh_wp)[lane];
+                        st->T[lane] = T_sh[lane];
+                    }
+                    if (lane < 16) res->T[lane] = T_sh[lane];
+                    if (lane == 0) {
+                        if (!ok_flag) {
+                            st->iters_skipped += 1;
+                            st->status = RGBID_ERR_DEGENERATE;
+                        }
+                        st->iters_done += 1;
+                        res->iters_done = st->iters_done;
+                        res->iters_skipped = st->iters_skipped;
+                        res->status = st->timeouts ? RGBID_ERR_TIMEOUT : st->status;
+                    }
+                }
+                if (lane == 0) st->pending = 0u;
+            }
+        }
+        __syncthreads();
+    } else {
+        if (threadIdx.x < 16)
+            reinterpret_cast<float*>(&sh_wp)[threadIdx.x] = __ldcg(reinterpret_cast<const float*>(&a.st->wp) + threadIdx.x);
+        __syncthreads();
+    }
+    if (a.finalize_only) {
+        cl.sync();   // every remote write into this CTA has landed before it exits
+        return;
+    }
     const WarpPose wp = sh_wp;
 
     // ---- systematic sample residuals r(p, 0) (NaN = masked out); the samples of a
@@ -248,7 +397,6 @@ __global__ void __launch_bounds__(kRobustNT) robust_kernel(RobustArgs a) {
         }
     }
 
-    ClusterSum<CL> R{red_w, recv, tot, mbar, &a.st->timeouts, (uint32_t)rank, 0};
     // ---- counts and mean square -> sigma0 (mu0 = 0)
     {
         float v4[4] = {0.f, 0.f, 0.f, 0.f};
@@ -385,12 +533,12 @@ __global__ void __launch_bounds__(kRobustNT) robust_kernel(RobustArgs a) {
 template <int PREC>
 __global__ void __launch_bounds__(kSweepNT, 2) sweep_kernel(SweepArgs a) {
     __shared__ float red[kSweepNT / 32][kSlots];
-    __shared__ F2 fin[kSweepNT / 32][kSlots];
-    __shared__ float tot[kSlots];
-    __shared__ bool am_last;
     __shared__ WarpPose sh_wp;
     __shared__ RobustParams sh_rob;
-    if (iteration_skipped(a.level_iters, a.level, a.iter)) return;
+    if (iteration_skipped(a.level_iters, a.level, a.iter)) {
+        pdl_wait();
+        return;
+    }
     pdl_wait();   // the robust parameters (and pose) of this iteration are complete and visible
     if (threadIdx.x < 16) {
         reinterpret_cast<float*>(&sh_wp)[threadIdx.x] = __ldcg(reinterpret_cast<const float*>(&a.st->wp) + threadIdx.x);
@@ -449,148 +597,22 @@ __global__ void __launch_bounds__(kSweepNT, 2) sweep_kernel(SweepArgs a) {
         }
     }
 
-    // block reduction: warp reduce-scatter, then warp 0 sums the 8 warps
+    // the next kernel may be scheduled once every block has finished its pixels;
+    // it waits for this grid to complete before it reads anything written here
+    pdl_trigger();
+
+    // block reduction: warp reduce-scatter, then warp 0 sums the 8 warps into
+    // compensated pairs; the next robust-scale kernel reduces the blocks
     const float mine = warp_reduce_scatter32(acc);
     red[warp][lane] = mine;
     __syncthreads();
-    const int nblocks = gridDim.x * gridDim.y;
-    const int bid = blockIdx.y * gridDim.x + blockIdx.x;
     if (warp == 0) {
         F2 s{0.f, 0.f};
 #pragma unroll
         for (int w = 0; w < kSweepNT / 32; ++w) s.add(red[w][lane]);
+        const int bid = blockIdx.y * gridDim.x + blockIdx.x;
         reinterpret_cast<float2*>(a.partials)[(size_t)bid * kSlots + lane] = make_float2(s.hi, s.lo);
-        __threadfence();
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned ticket = atomicAdd(&a.st->counter, 1u);
-        am_last = (ticket == (unsigned)(nblocks - 1));
-    }
-    __syncthreads();
-    if (!am_last) return;
-    pdl_trigger();   // the next kernel may launch now; it waits for this grid to finish
-    __threadfence();
-
-    // ---- last block: fixed-order compensated sum of the block partials
-    __shared__ double T_sh[16];
-    __shared__ WarpPose wp_new;
-    if (threadIdx.x < 16) T_sh[threadIdx.x] = __ldcg(a.st->T + threadIdx.x);   // overlaps the partial loads
-    {
-        // warp w sums blocks w, w + 8, ...; loads are issued in batches of 24 so
-        // that their L2 latencies overlap
-        constexpr int kBatch = 24;
-        constexpr int kStride = kSweepNT / 32;
-        F2 acc2{0.f, 0.f};
-        for (int b0 = warp; b0 < nblocks; b0 += kBatch * kStride) {
-            float2 vals[kBatch];
-#pragma unroll
-            for (int q = 0; q < kBatch; ++q) {
-                const int b = b0 + q * kStride;
-                vals[q] = b < nblocks ? __ldcg(reinterpret_cast<const float2*>(a.partials) + (size_t)b * kSlots + lane)
-                                      : make_float2(0.f, 0.f);
-            }
-#pragma unroll
-            for (int q = 0; q < kBatch; ++q) acc2.add(F2{vals[q].x, vals[q].y});
-        }
-        fin[warp][lane] = acc2;
-    }
-    __syncthreads();
-    if (warp != 0) return;
-    F2 t2{0.f, 0.f};
-#pragma unroll
-    for (int w = 0; w < kSweepNT / 32; ++w) t2.add(fin[w][lane]);
-    const float totf = t2.value();
-    tot[lane] = totf;
-    AlignState* st = a.st;
-    rgbid_align_result* res = a.res;
-    // results (double) written by the lanes in parallel
-    {
-        const double td = (double)t2.hi + (double)t2.lo;
-        if (lane < 21) {
-            int i = 0, rem = lane;
-            while (rem >= 6 - i) { rem -= 6 - i; ++i; }
-            const int j = i + rem;
-            res->H[i * 6 + j] = td;
-            res->H[j * 6 + i] = td;
-        } else if (lane < 27) {
-            res->g[lane - kSlotG] = td;
-        } else if (lane == kSlotCost) {
-            res->cost = td;
-        } else if (lane == kSlotNI) {
-            res->n_valid[0] = (int)totf;
-        } else if (lane == kSlotNW) {
-            res->n_valid[1] = (int)totf;
-        } else if (lane == 30) {
-            res->mu[0] = rob.mu[0]; res->mu[1] = rob.mu[1];
-            res->sigma[0] = rob.sigma[0]; res->sigma[1] = rob.sigma[1];
-            res->nu[0] = rob.nu[0]; res->nu[1] = rob.nu[1];
-        }
-    }
-    __syncwarp();
-    if (lane == 0) st->counter = 0u;
-    if (!a.update) return;
-    __shared__ float xi_sh[6];
-    __shared__ float Hs[36], gs[6];
-    __shared__ int ok_flag;
-    if (lane < 21) {
-        int i = 0, rem = lane;
-        while (rem >= 6 - i) { rem -= 6 - i; ++i; }
-        const int j = i + rem;
-        Hs[i * 6 + j] = totf;
-        Hs[j * 6 + i] = totf;
-    } else if (lane < 27) {
-        gs[lane - kSlotG] = totf;
-    }
-    __syncwarp();
-    __shared__ double xi_d[6];
-    if (lane == 0) {
-        const int nI = (int)tot[kSlotNI], nW = (int)tot[kSlotNW];
-        bool okl = (nI + nW) >= a.min_valid;
-        if constexpr (PREC == RGBID_PLANES_BF16_F16) {
-            // reduced-precision planes: the 6x6 solve runs in FP64
-            double xi[6];
-            okl = okl && cholesky_solve6_packed_d(Hs, gs, xi);
-#pragma unroll
-            for (int i = 0; i < 6; ++i) xi_d[i] = okl ? xi[i] : 0.0;
-        } else {
-            float xi[6];
-            okl = okl && cholesky_solve6_packed(Hs, gs, xi);
-#pragma unroll
-            for (int i = 0; i < 6; ++i) xi_sh[i] = okl ? xi[i] : 0.f;
-        }
-        ok_flag = okl ? 1 : 0;
-    }
-    __syncwarp();
-    const int ok_sh = ok_flag;
-    const bool ok = ok_sh != 0;
-    if (ok) {
-        if constexpr (PREC == RGBID_PLANES_BF16_F16) {
-            double xi[6];
-#pragma unroll
-            for (int i = 0; i < 6; ++i) xi[i] = xi_d[i];
-            warp_apply_update_d(xi, T_sh);
-        } else {
-            float xi[6];
-#pragma unroll
-            for (int i = 0; i < 6; ++i) xi[i] = xi_sh[i];
-            warp_apply_update(xi, T_sh);
-        }
-        warp_make_pose(T_sh, &wp_new);
-        __syncwarp();
-        if (lane < 16) reinterpret_cast<float*>(&st->wp)[lane] = reinterpret_cast<const float*>(&wp_new)[lane];
-        if (lane < 16) st->T[lane] = T_sh[lane];
-    }
-    if (lane < 16) res->T[lane] = T_sh[lane];
-    if (lane == 0) {
-        if (!ok) {
-            st->iters_skipped += 1;
-            st->status = RGBID_ERR_DEGENERATE;
-        }
-        st->iters_done += 1;
-        res->iters_done = st->iters_done;
-        res->iters_skipped = st->iters_skipped;
-        res->status = st->timeouts ? RGBID_ERR_TIMEOUT : st->status;
+        if (bid == 0 && lane == 0) a.st->pending = gridDim.x * gridDim.y;
     }
 }
 
@@ -743,6 +765,11 @@ static RobustArgs robust_args(const rgbid_pyramid* ref, const rgbid_pyramid* cur
     ra.level_iters = nullptr;
     ra.level = l;
     ra.iter = 0;
+    ra.partials = nullptr;
+    ra.res = nullptr;
+    ra.update = 1;
+    ra.min_valid = p->min_valid;
+    ra.finalize_only = 0;
     return ra;
 }
 
@@ -779,21 +806,21 @@ extern "C" int rgbid_align(const rgbid_pyramid* ref, const rgbid_pyramid* cur, c
     init_kernel<<<1, 32, 0, stream>>>(ia);
     if (cudaGetLastError() != cudaSuccess) return RGBID_ERR_CUDA;
 
+    rgbid_timing* tm = params->timing;
+    RobustArgs ra{};
     for (int l = params->levels - 1; l >= 0; --l) {
-        RobustArgs ra = robust_args(ref, cur, l, params, st);
+        ra = robust_args(ref, cur, l, params, st);
+        ra.partials = reinterpret_cast<const float2*>(partials);
+        ra.res = d_result;
+        ra.level_iters = params->level_iters;
         SweepArgs sa;
         memset(&sa, 0, sizeof(sa));
         sa.A = ra.A;
         sa.B = ra.B;
         sa.st = st;
         sa.partials = partials;
-        sa.res = d_result;
-        sa.update = 1;
-        sa.min_valid = params->min_valid;
-        ra.level_iters = params->level_iters;
         sa.level_iters = params->level_iters;
         sa.level = l;
-        rgbid_timing* tm = params->timing;
         for (int it = 0; it < params->iters[l]; ++it) {
             ra.iter = it;
             sa.iter = it;
@@ -814,6 +841,15 @@ extern "C" int rgbid_align(const rgbid_pyramid* ref, const rgbid_pyramid* cur, c
                 tm->units += (long long)sa.A.w * sa.A.h;
             }
         }
+    }
+    // the last sweep's reduction, solve and update (no robust estimation)
+    ra.finalize_only = 1;
+    const bool tr = tm && tm->kernel == RGBID_KERNEL_ROBUST && tm->count < tm->capacity;
+    if (tr && cudaEventRecord((cudaEvent_t)tm->ev_start[tm->count], stream) != cudaSuccess) return RGBID_ERR_CUDA;
+    if (launch_robust_any(ref->precision, ra, stream) != cudaSuccess) return RGBID_ERR_CUDA;
+    if (tr) {
+        if (cudaEventRecord((cudaEvent_t)tm->ev_end[tm->count], stream) != cudaSuccess) return RGBID_ERR_CUDA;
+        tm->count += 1;
     }
     return RGBID_OK;
 }
@@ -848,6 +884,9 @@ extern "C" int rgbid_eval_step(const rgbid_pyramid* ref, const rgbid_pyramid* cu
     init_kernel<<<1, 32, 0, stream>>>(ia);
     if (cudaGetLastError() != cudaSuccess) return RGBID_ERR_CUDA;
     RobustArgs ra = robust_args(ref, cur, level, &p, st);
+    ra.partials = reinterpret_cast<const float2*>(partials);
+    ra.res = d_result;
+    ra.update = 0;
     if (!robust && launch_robust_any(ref->precision, ra, stream) != cudaSuccess) return RGBID_ERR_CUDA;
     SweepArgs sa;
     memset(&sa, 0, sizeof(sa));
@@ -855,14 +894,14 @@ extern "C" int rgbid_eval_step(const rgbid_pyramid* ref, const rgbid_pyramid* cu
     sa.B = ra.B;
     sa.st = st;
     sa.partials = partials;
-    sa.res = d_result;
-    sa.update = 0;
-    sa.min_valid = p.min_valid;
     sa.r_I = r_I;
     sa.r_W = r_W;
     sa.m_I = mask_I;
     sa.m_W = mask_W;
     if (launch_sweep_any(ref->precision, sa, stream) != cudaSuccess) return RGBID_ERR_CUDA;
+    // the step's normal equations and results (no update)
+    ra.finalize_only = 1;
+    if (launch_robust_any(ref->precision, ra, stream) != cudaSuccess) return RGBID_ERR_CUDA;
     return RGBID_OK;
 }
 

@@ -52,7 +52,7 @@ struct AlignState {
     double T[16];           // current estimate A_T_B
     WarpPose wp;            // FP32 warp parameters of T
     RobustParams rob;       // robust parameters of the current iteration
-    unsigned int counter;   // last-block ticket of the sweep
+    unsigned int pending;   // blocks of the last sweep whose partials await reduction (0: none)
     int status;
     int iters_done;
     int iters_skipped;
