@@ -1,18 +1,23 @@
 // Dense IRLS alignment kernels and the rgbid_align / rgbid_eval_step entry points.
 //
 // Per Gauss-Newton iteration two kernels run on the caller's stream:
-//   robust_kernel  one thread-block cluster: warps the <= 19200 systematic
-//                  sample pixels with the current pose, then estimates the
-//                  Student-t (mu, sigma) at nu0 by the lagged-weight fixed
-//                  point and nu by bisection on the robustness equation, with
-//                  every reduction done across the cluster through distributed
-//                  shared memory ("Error distribution and robust optimisation").
-//   sweep_kernel   the whole level: warp, residuals, Jacobians, weights and the
-//                  per-block reduction of the 27 normal-equation terms (plus
-//                  cost and counts); the last block to finish sums the block
-//                  partials in a fixed order (compensated FP32), solves
+//   robust_kernel  one thread-block cluster.  It first finishes the previous
+//                  iteration's sweep: the CTAs sum disjoint subsets of its block
+//                  partials (compensated FP32), one exchange through distributed
+//                  shared memory gives every CTA the totals, and every CTA solves
 //                  H xi = -g by a Jacobi-scaled Cholesky and applies
-//                  T <- exp(xi)^-1 T to the FP64 pose ("Iterative optimisation").
+//                  T <- exp(xi)^-1 T to its copy of the FP64 pose ("Iterative
+//                  optimisation"); CTA 0 writes the new state and the step's
+//                  results.  It then warps the <= 19200 systematic sample pixels
+//                  with the new pose and estimates the Student-t (mu, sigma) at
+//                  nu0 by the lagged-weight fixed point and nu by bisection on the
+//                  robustness equation, every reduction exchanged across the
+//                  cluster ("Error distribution and robust optimisation").
+//   sweep_kernel   the whole level: warp, residuals, Jacobians, weights and the
+//                  per-block compensated partials of the 27 normal-equation terms
+//                  (plus cost and counts).
+// A closing robust_kernel launch (finalize_only) finishes the last sweep of an
+// alignment.
 #include <cooperative_groups.h>
 #include <cstdio>
 #include <cstring>

@@ -9,10 +9,6 @@
 
 namespace rgbid {
 
-__device__ __forceinline__ F2 shfl_f2(const F2& v, int off) {
-    return F2{__shfl_xor_sync(0xffffffffu, v.hi, off), __shfl_xor_sync(0xffffffffu, v.lo, off)};
-}
-
 // ---- distributed-shared-memory exchange (push model)
 // Each CTA sends its compensated partials to every CTA of the cluster with
 // st.async, which completes transaction bytes on the receiver's mbarrier; a

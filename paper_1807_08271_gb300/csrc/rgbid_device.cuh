@@ -230,19 +230,6 @@ __device__ __forceinline__ void finish(const LevelDev& A, const WarpPose& wp, co
     }
 }
 
-// Evaluate one pixel p = (u, v) of A: all four stages in turn.
-template <int PREC, bool WANT_J>
-__device__ __forceinline__ void eval_pixel(const LevelDev& A, const LevelDev& B, const WarpPose& wp,
-                                           int u, int v, PixelTerms& o) {
-    PxA s;
-    PxW w;
-    PxB t;
-    stage_a<PREC>(A, u, v, s);
-    stage_w(A, B, wp, u, v, s, w);
-    stage_b<PREC>(B, w, t);
-    finish<WANT_J>(A, wp, s, w, t, o);
-}
-
 // Student-t weight omega(x, nu) / sigma^2 = (nu + 1) / (nu sigma^2 + (r - mu)^2).
 __device__ __forceinline__ float robust_weight(float r, float mu, float sig, float nu) {
     const float d = r - mu;
@@ -272,12 +259,6 @@ __device__ __forceinline__ float warp_sum(float x) {
     return x;
 }
 
-__device__ __forceinline__ double warp_sum_d(double x) {
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    return x;
-}
-
 // ---------------------------------------------------------------- compensated sums
 // Knuth TwoSum accumulation of floats: the pair (hi, lo) carries the rounding error.
 struct F2 {
@@ -295,53 +276,6 @@ struct F2 {
     }
     __device__ __forceinline__ float value() const { return hi + lo; }
 };
-
-// ---------------------------------------------------------------- 6x6 solve (FP32, Jacobi-scaled)
-// Solve H xi = rhs for SPD H.  H is first scaled to unit diagonal (S = D H D,
-// D = diag(H)^-1/2), then factorised S = L L^T by Cholesky.  Returns false if
-// a diagonal entry or pivot is not positive.
-__device__ __forceinline__ bool cholesky_solve6_f(const float H[36], const float rhs[6], float xi[6]) {
-    float D[6], L[36], iL[6], y[6];
-#pragma unroll
-    for (int i = 0; i < 6; ++i) {
-        if (!(H[i * 6 + i] > 0.f)) return false;
-        D[i] = rsqrtf(H[i * 6 + i]);
-    }
-#pragma unroll
-    for (int j = 0; j < 6; ++j) {
-        float d = H[j * 6 + j] * D[j] * D[j];
-#pragma unroll
-        for (int k = 0; k < j; ++k) d = fmaf(-L[j * 6 + k], L[j * 6 + k], d);
-        if (!(d > 1e-7f)) return false;
-        const float r = rsqrtf(d);
-        L[j * 6 + j] = d * r;
-        iL[j] = r;
-#pragma unroll
-        for (int i = j + 1; i < 6; ++i) {
-            float t = H[i * 6 + j] * D[i] * D[j];
-#pragma unroll
-            for (int k = 0; k < j; ++k) t = fmaf(-L[i * 6 + k], L[j * 6 + k], t);
-            L[i * 6 + j] = t * r;
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < 6; ++i) {
-        float t = rhs[i] * D[i];
-#pragma unroll
-        for (int k = 0; k < i; ++k) t = fmaf(-L[i * 6 + k], y[k], t);
-        y[i] = t * iL[i];
-    }
-#pragma unroll
-    for (int i = 5; i >= 0; --i) {
-        float t = y[i];
-#pragma unroll
-        for (int k = i + 1; k < 6; ++k) t = fmaf(-L[k * 6 + i], xi[k], t);
-        xi[i] = t * iL[i];
-    }
-#pragma unroll
-    for (int i = 0; i < 6; ++i) xi[i] *= D[i];
-    return true;
-}
 
 // Same Jacobi-scaled Cholesky solve for one thread with a small register
 // footprint: H and g are read from (shared) memory, L is kept packed (lower
@@ -562,21 +496,6 @@ __device__ __forceinline__ void warp_apply_update_d(const double xi[6], double* 
     __syncwarp();
     if (lane < 12) T[lane] = Tn;
     __syncwarp();
-}
-
-// digamma by the recurrence psi(x) = psi(x + 1) - 1/x up to x >= 6 followed by the
-// asymptotic series psi(x) ~ ln x - 1/(2x) - sum_k B_2k / (2k x^2k)
-// (Abramowitz & Stegun 6.3.5 and 6.3.18).
-__device__ __forceinline__ double digamma_d(double x) {
-    double acc = 0.0;
-    while (x < 6.0) {
-        acc -= 1.0 / x;
-        x += 1.0;
-    }
-    const double ix = 1.0 / x, ix2 = ix * ix;
-    // B2/2 = 1/12, B4/4 = -1/120, B6/6 = 1/252, B8/8 = -1/240, B10/10 = 1/132, B12/12 = -691/32760
-    const double series = ix2 * (1.0 / 12.0 - ix2 * (1.0 / 120.0 - ix2 * (1.0 / 252.0 - ix2 * (1.0 / 240.0 - ix2 * (1.0 / 132.0 - ix2 * (691.0 / 32760.0))))));
-    return acc + log(x) - 0.5 * ix - series;
 }
 
 }  // namespace rgbid
