@@ -9,7 +9,10 @@
  *    (the current frame); a pose T = A_T_B is a row-major 4x4 double matrix
  *    that maps B's coordinates into A's (X_A = R X_B + t).
  *  - Images are row-major.  I is intensity in [0, 1]; W is inverse depth in
- *    1/m with W == 0 (or any W <= 0, or NaN) meaning "no measurement" (a hole).
+ *    1/m with W == 0 (or any W <= 0) meaning "no measurement" (a hole).  A
+ *    pixel whose I or W is not a finite number (NaN, +-inf) is a hole too: the
+ *    pyramid and the keyframe initialisation store it with W = 0 (and I = 0
+ *    where I is not finite), and fusion never reads it as a measurement.
  *    `pitch` arguments count ELEMENTS per row (>= width).
  *  - Ownership: the caller allocates and owns every buffer (planes, pyramid
  *    storage, workspace, results).  The library keeps no global state and
@@ -21,7 +24,15 @@
  *    (nothing is enqueued).  A failed kernel launch returns RGBID_ERR_CUDA.
  *    Numerical outcomes (degenerate steps) are written to the result struct's
  *    `status` field on the device.  No C++ exception crosses this ABI.
- *  - All device pointers must be 16-byte aligned.
+ *  - Alignment: every device pointer must be a multiple of its element size
+ *    (float planes 4 bytes; an interleaved pyramid level its pixel size, 8 or
+ *    4 bytes; doubles, result records and batch items 8 bytes); workspaces and
+ *    pyramid storage 256 bytes.  A misaligned argument is rejected before
+ *    anything is enqueued (RGBID_ERR_INVALID_ARG, or RGBID_ERR_WORKSPACE for a
+ *    workspace).  Pointers inside device-resident batch items are checked on
+ *    the device: the item reports RGBID_ERR_INVALID_ARG (a misaligned result
+ *    record is skipped like NULL).
+ *  - Intrinsics must be finite with fx, fy > 0 (else RGBID_ERR_INVALID_ARG).
  */
 #ifndef RGBID_H
 #define RGBID_H
@@ -383,6 +394,16 @@ int rgbid_eval_step(const rgbid_pyramid* ref, const rgbid_pyramid* cur, int leve
                     void* workspace, size_t workspace_bytes,
                     float* r_I, float* r_W, uint8_t* mask_I, uint8_t* mask_W,
                     rgbid_align_result* d_result, void* stream);
+
+/* Diagnostic of the device-side failure detection (the paper has no
+ * counterpart).  Launches one 4-CTA cluster that runs one round of the
+ * alignment's cluster reduction with every CTA withholding its partials, so
+ * each CTA's wait runs out of `budget_cycles` (clock64 cycles, <= 2e10), adds 1 to
+ * *d_timeouts (device int, not reset) and ends; nothing faults or hangs and the
+ * context stays usable.  The alignment kernels use the same wait with a budget
+ * of about 2 s and report RGBID_ERR_TIMEOUT in their results.
+ * Errors: INVALID_ARG, CUDA. */
+int rgbid_probe_wait_timeout(long long budget_cycles, int* d_timeouts, void* stream);
 
 /* ---------------------------------------------------------------- fusion
  * Keyframe fusion ("Keyframe fusion", section "RGB-ID SLAM system"): every

@@ -53,6 +53,11 @@ Readings taken where the paper is silent, ambiguous or garbled (R1..R17):
   R18 the constant-velocity guess T1 T2^-1 T1 is projected onto SE(3) (nearest
       rotation); otherwise rounding drift of the rotation block compounds by
       ~2.4x per frame and tracking is lost after a few dozen frames.
+  R19 a pixel whose I or W is not a finite number carries no measurement (the
+      paper's sensor gives finite intensities and marks missing depth only):
+      it enters the pyramid and the keyframe as a hole, W = 0, with I = 0
+      where I is not finite; in fusion such a keyframe pixel or frame-k tap is
+      not a measurement.
 """
 from __future__ import annotations
 
@@ -147,6 +152,16 @@ class Level:
     K: tuple        # (fx, fy, cx, cy) at this level
 
 
+def measurement_planes(I, W):
+    """Level-0 planes with every non-finite pixel made a hole (reading R19):
+    W = 0 where I or W is not finite, I = 0 where I is not finite; every other
+    pixel unchanged."""
+    I = np.asarray(I, dtype=np.float64)
+    W = np.asarray(W, dtype=np.float64)
+    fin_I = np.isfinite(I)
+    return np.where(fin_I, I, 0.0), np.where(fin_I & np.isfinite(W), W, 0.0)
+
+
 def downsample(I, W):
     """One pyramid step ("Iterative optimisation": downsample {I_A, W_A}), reading R1."""
     I = np.asarray(I, dtype=np.float64)
@@ -175,9 +190,8 @@ def level_intrinsics(K0, level: int) -> tuple:
 
 
 def build_pyramid(I0, W0, K0, levels: int) -> list:
-    """Image pyramid {I, W} per level, finest first."""
-    I = np.asarray(I0, dtype=np.float64)
-    W = np.asarray(W0, dtype=np.float64)
+    """Image pyramid {I, W} per level, finest first (level 0: reading R19)."""
+    I, W = measurement_planes(I0, W0)
     pyr = [Level(I, W, tuple(float(k) for k in K0))]
     for l in range(1, levels):
         I, W = downsample(I, W)
@@ -517,8 +531,10 @@ def fuse(I_kf, W_kf, C_kf, I_k, W_k, K, T, sigma_W: float, fuse_intensity: bool 
     C_kf = np.asarray(C_kf, dtype=np.float64)
     T = np.asarray(T, dtype=np.float64)
     R, t = T[:3, :3], T[:3, 3]
-    A = Level(I_kf, W_kf, tuple(float(k) for k in K))
-    B = Level(np.asarray(I_k, dtype=np.float64), np.asarray(W_k, dtype=np.float64), A.K)
+    # non-finite keyframe pixels and frame-k taps are not measurements (reading R19);
+    # where the gate passes the keyframe values are the given ones
+    A = Level(*measurement_planes(I_kf, W_kf), tuple(float(k) for k in K))
+    B = Level(*measurement_planes(I_k, W_k), A.K)
     wp = inverse_geometric_warp(A, B, T)
     fx, fy, cx, cy = A.K
     w_B = 1.0 / np.where(wp["front"], wp["Z_B"], 1.0)
@@ -556,8 +572,7 @@ def track_sequence(I_frames, W_frames, K, levels: int = 4, iters=(5, 5, 5, 10), 
     dicts), keyframe=(I, W, C) at the end)."""
     P = AlignParams(levels=levels, iters=tuple(iters))
     n = len(I_frames) if n_frames is None else n_frames
-    I_kf = np.asarray(I_frames[0], dtype=np.float64).copy()
-    W_kf = np.asarray(W_frames[0], dtype=np.float64).copy()
+    I_kf, W_kf = measurement_planes(I_frames[0], W_frames[0])       # reading R19
     C_kf = np.ones_like(W_kf)
     pyramid = build_pyramid_reduced if reduced else build_pyramid
     kfp = pyramid(I_kf, W_kf, K, levels)
@@ -577,8 +592,7 @@ def track_sequence(I_frames, W_frames, K, levels: int = 4, iters=(5, 5, 5, 10), 
             T2 = se3_inv(Tk) @ T1
             T1 = np.eye(4)
             T_wkf = T_wkf @ Tk
-            I_kf = np.asarray(I_frames[k], dtype=np.float64).copy()
-            W_kf = np.asarray(W_frames[k], dtype=np.float64).copy()
+            I_kf, W_kf = measurement_planes(I_frames[k], W_frames[k])
             C_kf = np.ones_like(W_kf)
         else:
             I_kf, W_kf, C_kf, _ = fuse(I_kf, W_kf, C_kf, I_frames[k], W_frames[k], K, Tk, r["robust"]["sigma"][1],

@@ -134,6 +134,7 @@ struct ClusterSum {
     int* timeouts;                            // device counter of expired waits
     uint32_t rank;
     int round;
+    long long budget = kWaitBudgetCycles;     // clock64 cycles a wait may take before it gives up
 
     // v: per-thread partials of NV values (NV <= 8: one warp sum each; NV = 96: three
     // reduce-scatter chunks).  On return out[0..NV) holds the cluster totals,
@@ -141,18 +142,21 @@ struct ClusterSum {
     // Threads t < NV of every CTA call this with the CTA's compensated partial of
     // value t; each returns the cluster total (same pairwise tree over the ranks
     // in every CTA).  The caller separates rounds with __syncthreads and next().
+    // (`send` = false withholds this CTA's partials: used only by the wait-timeout probe.)
     template <int NV>
-    __device__ __forceinline__ F2 exchange(int t, F2 s) {
+    __device__ __forceinline__ F2 exchange(int t, F2 s, bool send = true) {
         const int par = round & 1;
         const uint32_t phase = (uint32_t)(round >> 1) & 1u;
         if (t == 0) mbar_arrive_expect_tx(&mbar[par], (uint32_t)(CL * NV * sizeof(float2)));
         const uint32_t src = smem_addr(&recv[par][rank][t]);
         const uint32_t bar = smem_addr(&mbar[par]);
+        if (send) {
 #pragma unroll
-        for (int r = 0; r < CL; ++r) st_async_f2(map_to_rank(src, r), s.hi, s.lo, map_to_rank(bar, r));
+            for (int r = 0; r < CL; ++r) st_async_f2(map_to_rank(src, r), s.hi, s.lo, map_to_rank(bar, r));
+        }
         const long long t0 = clock64();
         while (!mbar_try_wait(&mbar[par], phase)) {
-            if (clock64() - t0 > kWaitBudgetCycles) {
+            if (clock64() - t0 > budget) {
                 atomicAdd(timeouts, 1);
                 break;
             }
@@ -621,6 +625,33 @@ __global__ void __launch_bounds__(kSweepNT, 2) sweep_kernel(SweepArgs a) {
     }
 }
 
+// ---------------------------------------------------------------- wait-timeout probe
+// One exchange round of the cluster reduction in which every CTA withholds its
+// partials: no CTA's barrier can complete, so every wait runs out of `budget`,
+// counts a timeout and returns.  Shows on the device that a wait with nothing to
+// wait for ends with a status instead of hanging.  No CTA writes to another's
+// shared memory, so none can exit with a store to it still in flight.
+template <int CL>
+__global__ void __launch_bounds__(32) wait_timeout_probe_kernel(long long budget, int* timeouts) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    __shared__ float red_w[kRobustNT / 32][kRobustMaxNV];
+    __shared__ float2 recv[2][CL][kRobustMaxNV];
+    __shared__ float tot[kRobustMaxNV];
+    __shared__ __align__(8) unsigned long long mbar[2];
+    if (threadIdx.x == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    cl.sync();
+    ClusterSum<CL> R{red_w, recv, tot, mbar, timeouts, (uint32_t)rank, 0};
+    R.budget = budget;
+    if (threadIdx.x == 0) tot[0] = R.template exchange<1>(0, F2{1.f, 0.f}, false).value();
+    __syncwarp();
+    cl.sync();
+}
+
 // ---------------------------------------------------------------- host side
 static LevelDev level_dev(const rgbid_level& L) {
     LevelDev d;
@@ -656,6 +687,8 @@ static int check_pyramids(const rgbid_pyramid* ref, const rgbid_pyramid* cur, co
     if (p->levels < 1 || p->levels > ref->levels) return RGBID_ERR_INVALID_ARG;
     if (ref->precision != cur->precision) return RGBID_ERR_INVALID_ARG;
     if (ref->precision != RGBID_PLANES_F32 && ref->precision != RGBID_PLANES_BF16_F16) return RGBID_ERR_UNSUPPORTED;
+    const uintptr_t px_bytes = ref->precision == RGBID_PLANES_F32 ? 8u : 4u;   // one interleaved (I, W) pixel
+    if (p->level_iters && misaligned(p->level_iters, 4)) return RGBID_ERR_INVALID_ARG;
     if (p->sample_cap < 1 || p->sample_cap > RGBID_MAX_SAMPLES) return RGBID_ERR_INVALID_ARG;
     if (p->scale_iters < 0 || p->bisect_steps < 0 || p->bisect_steps > 60) return RGBID_ERR_INVALID_ARG;
     if (!(p->nu_lo > 0.0) || !(p->nu_hi > p->nu_lo) || !(p->nu0 > 0.0)) return RGBID_ERR_INVALID_ARG;
@@ -666,10 +699,11 @@ static int check_pyramids(const rgbid_pyramid* ref, const rgbid_pyramid* cur, co
         const rgbid_level& b = cur->lv[l];
         if (p->iters[l] < 0) return RGBID_ERR_INVALID_ARG;
         if (!a.IW || !b.IW) return RGBID_ERR_INVALID_ARG;
+        if (misaligned(a.IW, px_bytes) || misaligned(b.IW, px_bytes)) return RGBID_ERR_INVALID_ARG;
         if (a.width != b.width || a.height != b.height || a.width < 4 || a.height < 4) return RGBID_ERR_INVALID_ARG;
         if (a.pitch < a.width || b.pitch < b.width) return RGBID_ERR_INVALID_ARG;
         if (a.K.fx != b.K.fx || a.K.fy != b.K.fy || a.K.cx != b.K.cx || a.K.cy != b.K.cy) return RGBID_ERR_INVALID_ARG;
-        if (!(a.K.fx > 0.0) || !(a.K.fy > 0.0)) return RGBID_ERR_INVALID_ARG;
+        if (!intrinsics_ok(a.K.fx, a.K.fy, a.K.cx, a.K.cy)) return RGBID_ERR_INVALID_ARG;
     }
     return RGBID_OK;
 }
@@ -793,7 +827,8 @@ extern "C" int rgbid_align(const rgbid_pyramid* ref, const rgbid_pyramid* cur, c
                            rgbid_align_result* d_result, void* stream_) {
     int st_chk = check_pyramids(ref, cur, params);
     if (st_chk != RGBID_OK) return st_chk;
-    if (!d_result) return RGBID_ERR_INVALID_ARG;
+    if (!d_result || misaligned(d_result, 8)) return RGBID_ERR_INVALID_ARG;
+    if (T_init && T_init_on_device && misaligned(T_init, 8)) return RGBID_ERR_INVALID_ARG;
     if (!workspace || ((uintptr_t)workspace & 255u) || workspace_bytes < rgbid_align_workspace_bytes(ref, params))
         return RGBID_ERR_WORKSPACE;
     cudaStream_t stream = (cudaStream_t)stream_;
@@ -871,6 +906,7 @@ extern "C" int rgbid_eval_step(const rgbid_pyramid* ref, const rgbid_pyramid* cu
     if (st_chk != RGBID_OK) return st_chk;
     const bool any_out = r_I || r_W || mask_I || mask_W;
     if (any_out && !(r_I && r_W && mask_I && mask_W)) return RGBID_ERR_INVALID_ARG;
+    if (misaligned(d_result, 8) || misaligned(r_I, 4) || misaligned(r_W, 4)) return RGBID_ERR_INVALID_ARG;
     if (!workspace || ((uintptr_t)workspace & 255u) || workspace_bytes < rgbid_align_workspace_bytes(ref, &p))
         return RGBID_ERR_WORKSPACE;
     cudaStream_t stream = (cudaStream_t)stream_;
@@ -939,4 +975,24 @@ extern "C" int rgbid_align_noalloc(const rgbid_pyramid* ref, const rgbid_pyramid
     // the alignment's init kernel resets every scratch field that must start at zero
     return rgbid_align(ref, cur, T_init, T_init_on_device, params, g_noalloc_ptr[dev], kNoallocScratchBytes,
                        d_result, stream);
+}
+
+extern "C" int rgbid_probe_wait_timeout(long long budget_cycles, int* d_timeouts, void* stream) {
+    if (!d_timeouts || budget_cycles < 0 || budget_cycles > 20000000000LL) return RGBID_ERR_INVALID_ARG;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(4, 1, 1);
+    cfg.blockDim = dim3(32, 1, 1);
+    cfg.stream = (cudaStream_t)stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 4;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, wait_timeout_probe_kernel<4>, budget_cycles, d_timeouts) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return RGBID_ERR_CUDA;
+    }
+    return RGBID_OK;
 }

@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "rgbid_batch.cuh"
+#include "rgbid_util.h"
 
 namespace rgbid {
 
@@ -113,7 +114,7 @@ extern "C" int rgbid_align_batched(const rgbid_batch_item* d_items, int n_items,
     int cl, rows, ncl_req;
     rc = resolve_shape(cfg, &cl, &rows, &ncl_req);
     if (rc != RGBID_OK) return rc;
-    if (n_items < 0 || (n_items > 0 && !d_items)) return RGBID_ERR_INVALID_ARG;
+    if (n_items < 0 || (n_items > 0 && !d_items) || misaligned(d_items, 8)) return RGBID_ERR_INVALID_ARG;
     if (!workspace || ((uintptr_t)workspace & 255u) || workspace_bytes < sizeof(BatchWorkspace))
         return RGBID_ERR_WORKSPACE;
     if (n_items == 0) return RGBID_OK;

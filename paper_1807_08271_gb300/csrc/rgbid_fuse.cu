@@ -9,6 +9,12 @@
 //   W_kf <- (W_kf C_kf + C_k W_k*) / (C_kf + C_k),  C_kf <- C_kf + C_k,
 // with W_k* = W_k(p_k) / (R_2 . K^-1 p_k + t_z W_k(p_k)) the transferred
 // inverse depth and C_k = (dW_k*/dW_k)^-2 = (R_2 . K^-1 p_k + t_z W_k)^4 / (R_2 . K^-1 p_k)^2.
+//
+// Non-finite input carries no measurement: a keyframe pixel takes part only if
+// its I_kf and W_kf are finite (and W_kf > 0), a tap of frame k is valid only
+// if its I_k and W_k are finite (and W_k > 0), and the keyframe initialisation
+// stores a pixel with a non-finite I or W as a hole (W = 0; I = 0 where I is
+// not finite), as the pyramid does.
 #include <cstdint>
 #include <cstring>
 
@@ -50,7 +56,8 @@ __global__ void __launch_bounds__(256) fuse_kernel(FuseArgs a) {
     const WarpPose& wp = sh_wp;
     const size_t o = (size_t)v * a.pitch_kf + u;
     const float Wkf = a.W_kf[o];
-    if (!(Wkf > 0.f)) return;
+    const float Ikf = a.I_kf[o];
+    if (!(Wkf > 0.f && isfinite(Wkf) && isfinite(Ikf))) return;
     const float qa = ((float)u - a.cx) * a.ifx;
     const float qb = ((float)v - a.cy) * a.ify;
     const float dx = fmaf(wp.E[0], qa, fmaf(wp.E[1], qb, wp.E[2])) - Wkf * wp.s[0];
@@ -70,6 +77,12 @@ __global__ void __launch_bounds__(256) fuse_kernel(FuseArgs a) {
     const float w00 = __ldg(a.W_k + bi), w10 = __ldg(a.W_k + bi + 1);
     const float w01 = __ldg(a.W_k + bi + a.pitch_k), w11 = __ldg(a.W_k + bi + a.pitch_k + 1);
     if (!(w00 > 0.f && w10 > 0.f && w01 > 0.f && w11 > 0.f)) return;
+    const float i00 = __ldg(a.I_k + bi), i10 = __ldg(a.I_k + bi + 1);
+    const float i01 = __ldg(a.I_k + bi + a.pitch_k), i11 = __ldg(a.I_k + bi + a.pitch_k + 1);
+    // a tap is a measurement only if both of its values are finite (w > 0 is checked above)
+    if (!(isfinite(w00) && isfinite(w10) && isfinite(w01) && isfinite(w11) && isfinite(i00) && isfinite(i10) &&
+          isfinite(i01) && isfinite(i11)))
+        return;
     const float wtop = fmaf(ax, w10 - w00, w00), wbot = fmaf(ax, w11 - w01, w01);
     const float Wkp = fmaf(ay, wbot - wtop, wtop);
     const float wB = Wkf * imz;                     // 1 / Z_k of the keyframe point
@@ -85,11 +98,9 @@ __global__ void __launch_bounds__(256) fuse_kernel(FuseArgs a) {
     const float inv = 1.f / (C + Ck);
     a.W_kf[o] = (Wkf * C + Ck * Wstar) * inv;
     if (a.fuse_intensity) {
-        const float i00 = __ldg(a.I_k + bi), i10 = __ldg(a.I_k + bi + 1);
-        const float i01 = __ldg(a.I_k + bi + a.pitch_k), i11 = __ldg(a.I_k + bi + a.pitch_k + 1);
         const float itop = fmaf(ax, i10 - i00, i00), ibot = fmaf(ax, i11 - i01, i01);
         const float Ik = fmaf(ay, ibot - itop, itop);
-        a.I_kf[o] = (a.I_kf[o] * C + Ck * Ik) * inv;
+        a.I_kf[o] = (Ikf * C + Ck * Ik) * inv;
     }
     a.C_kf[o] = C + Ck;
 }
@@ -100,8 +111,10 @@ __global__ void init_keyframe_kernel(float* I_kf, float* W_kf, float* C_kf, int 
     const int v = blockIdx.y * blockDim.y + threadIdx.y;
     if (u >= w || v >= h) return;
     const size_t o = (size_t)v * pitch_kf + u, s = (size_t)v * pitch_k + u;
-    I_kf[o] = I_k[s];
-    W_kf[o] = W_k[s];
+    const float ik = I_k[s], wk = W_k[s];
+    const bool fi = isfinite(ik);
+    I_kf[o] = fi ? ik : 0.f;
+    W_kf[o] = (fi && isfinite(wk)) ? wk : 0.f;
     C_kf[o] = 1.f;
 }
 
@@ -199,8 +212,11 @@ extern "C" int rgbid_fuse_keyframe(float* I_kf, float* W_kf, float* C_kf, int pi
                                    const double* T_kf_k, const double* sigma_W, int params_on_device,
                                    int fuse_intensity, void* stream_) {
     if (!I_kf || !W_kf || !C_kf || !I_k || !W_k || !T_kf_k || !sigma_W) return RGBID_ERR_INVALID_ARG;
+    if (misaligned(I_kf, 4) || misaligned(W_kf, 4) || misaligned(C_kf, 4) || misaligned(I_k, 4) || misaligned(W_k, 4))
+        return RGBID_ERR_INVALID_ARG;
+    if (params_on_device && (misaligned(T_kf_k, 8) || misaligned(sigma_W, 8))) return RGBID_ERR_INVALID_ARG;
     if (width < 2 || height < 2 || pitch_kf < width || pitch_k < width) return RGBID_ERR_INVALID_ARG;
-    if (!(K.fx > 0.0) || !(K.fy > 0.0)) return RGBID_ERR_INVALID_ARG;
+    if (!intrinsics_ok(K.fx, K.fy, K.cx, K.cy)) return RGBID_ERR_INVALID_ARG;
     FuseArgs a;
     memset(&a, 0, sizeof(a));
     a.I_kf = I_kf; a.W_kf = W_kf; a.C_kf = C_kf; a.I_k = I_k; a.W_k = W_k;
@@ -225,6 +241,8 @@ extern "C" int rgbid_init_keyframe(float* I_kf, float* W_kf, float* C_kf, int pi
                                    const float* W_k, int pitch_k, int width, int height, void* stream_) {
     if (!I_kf || !W_kf || !C_kf || !I_k || !W_k || width < 1 || height < 1 || pitch_kf < width || pitch_k < width)
         return RGBID_ERR_INVALID_ARG;
+    if (misaligned(I_kf, 4) || misaligned(W_kf, 4) || misaligned(C_kf, 4) || misaligned(I_k, 4) || misaligned(W_k, 4))
+        return RGBID_ERR_INVALID_ARG;
     dim3 blk(32, 8);
     dim3 grd((width + 31) / 32, (height + 7) / 8);
     init_keyframe_kernel<<<grd, blk, 0, (cudaStream_t)stream_>>>(I_kf, W_kf, C_kf, pitch_kf, I_k, W_k, pitch_k, width,
@@ -234,12 +252,14 @@ extern "C" int rgbid_init_keyframe(float* I_kf, float* W_kf, float* C_kf, int pi
 
 extern "C" int rgbid_predict_pose(const double* T_km1, const double* T_km2, double* T_out, void* stream_) {
     if (!T_km1 || !T_km2 || !T_out) return RGBID_ERR_INVALID_ARG;
+    if (misaligned(T_km1, 8) || misaligned(T_km2, 8) || misaligned(T_out, 8)) return RGBID_ERR_INVALID_ARG;
     predict_pose_kernel<<<1, 32, 0, (cudaStream_t)stream_>>>(T_km1, T_km2, T_out);
     return cudaGetLastError() == cudaSuccess ? RGBID_OK : RGBID_ERR_CUDA;
 }
 
 extern "C" int rgbid_compose_pose(const double* A, int invert_A, const double* B, double* T_out, void* stream_) {
     if (!A || !B || !T_out || A == T_out) return RGBID_ERR_INVALID_ARG;
+    if (misaligned(A, 8) || misaligned(B, 8) || misaligned(T_out, 8)) return RGBID_ERR_INVALID_ARG;
     compose_pose_kernel<<<1, 32, 0, (cudaStream_t)stream_>>>(A, invert_A, B, T_out);
     return cudaGetLastError() == cudaSuccess ? RGBID_OK : RGBID_ERR_CUDA;
 }

@@ -419,7 +419,10 @@ __global__ void inputs_kernel(const rgbid_batch_item* items, int precision, bf16
         for (int l = 0; l < L && l < it->cur.levels; ++l)
             if (it->ref.lv[l].width == RGBID_NET_IN_W && it->ref.lv[l].height == RGBID_NET_IN_H &&
                 it->cur.lv[l].width == RGBID_NET_IN_W && it->cur.lv[l].height == RGBID_NET_IN_H &&
-                it->ref.lv[l].IW && it->cur.lv[l].IW && it->ref.lv[l].pitch >= RGBID_NET_IN_W &&
+                it->ref.lv[l].IW && it->cur.lv[l].IW &&
+                !((uintptr_t)it->ref.lv[l].IW & (precision == RGBID_PLANES_F32 ? 7u : 3u)) &&
+                !((uintptr_t)it->cur.lv[l].IW & (precision == RGBID_PLANES_F32 ? 7u : 3u)) &&
+                it->ref.lv[l].pitch >= RGBID_NET_IN_W &&
                 it->cur.lv[l].pitch >= RGBID_NET_IN_W && it->ref.precision == precision &&
                 it->cur.precision == precision)
                 found = l;
@@ -575,7 +578,7 @@ extern "C" size_t rgbid_net_workspace_bytes(int batch) {
 }
 
 extern "C" int rgbid_net_init(float* params, unsigned long long seed, void* stream) {
-    if (!params) return RGBID_ERR_INVALID_ARG;
+    if (!params || misaligned(params, 4)) return RGBID_ERR_INVALID_ARG;
     InitSpans sp;
     for (int l = 0; l < RGBID_NET_LAYERS; ++l) {
         sp.w0[l] = w_offset(l);
@@ -588,6 +591,7 @@ extern "C" int rgbid_net_init(float* params, unsigned long long seed, void* stre
 
 extern "C" int rgbid_net_inputs(const rgbid_batch_item* d_items, int n, int precision, void* x, void* stream) {
     if (n < 0 || (n > 0 && (!d_items || !x))) return RGBID_ERR_INVALID_ARG;
+    if (misaligned(d_items, 8) || misaligned(x, 4)) return RGBID_ERR_INVALID_ARG;
     if (precision != RGBID_PLANES_F32 && precision != RGBID_PLANES_BF16_F16) return RGBID_ERR_UNSUPPORTED;
     if (n == 0) return RGBID_OK;
     inputs_kernel<<<(unsigned)n, 256, 0, (cudaStream_t)stream>>>(d_items, precision, (bf16*)x);
@@ -597,6 +601,7 @@ extern "C" int rgbid_net_inputs(const rgbid_batch_item* d_items, int n, int prec
 extern "C" int rgbid_net_forward(const float* params, const void* x, int batch, float* y, void* workspace,
                                  size_t workspace_bytes, void* stream_) {
     if (!params || !x || !y) return RGBID_ERR_INVALID_ARG;
+    if (misaligned(params, 4) || misaligned(x, 4) || misaligned(y, 4)) return RGBID_ERR_INVALID_ARG;
     Ws w;
     const int rc = check_ws(batch, workspace, workspace_bytes, &w);
     if (rc != RGBID_OK) return rc;
@@ -627,6 +632,7 @@ extern "C" int rgbid_net_forward(const float* params, const void* x, int batch, 
 extern "C" int rgbid_net_backward(const float* params, const void* x, int batch, const float* dy, float* grad,
                                   void* workspace, size_t workspace_bytes, void* stream_) {
     if (!params || !x || !dy || !grad) return RGBID_ERR_INVALID_ARG;
+    if (misaligned(params, 4) || misaligned(x, 4) || misaligned(dy, 4) || misaligned(grad, 4)) return RGBID_ERR_INVALID_ARG;
     Ws w;
     const int rc = check_ws(batch, workspace, workspace_bytes, &w);
     if (rc != RGBID_OK) return rc;
@@ -670,6 +676,7 @@ extern "C" int rgbid_net_backward(const float* params, const void* x, int batch,
 
 extern "C" int rgbid_net_loss(const float* y, const float* target, int batch, float* dy, float* loss, void* stream) {
     if (!y || !target || !dy || !loss || batch < 1) return RGBID_ERR_INVALID_ARG;
+    if (misaligned(y, 4) || misaligned(target, 4) || misaligned(dy, 4) || misaligned(loss, 4)) return RGBID_ERR_INVALID_ARG;
     loss_kernel<<<1, 256, 0, (cudaStream_t)stream>>>(y, target, batch, dy, loss);
     return cudaGetLastError() == cudaSuccess ? RGBID_OK : RGBID_ERR_CUDA;
 }
@@ -677,6 +684,7 @@ extern "C" int rgbid_net_loss(const float* y, const float* target, int batch, fl
 extern "C" int rgbid_net_adam(float* params, const float* grad, float* m, float* v, int step, float lr, float beta1,
                               float beta2, float eps, void* stream) {
     if (!params || !grad || !m || !v || step < 1) return RGBID_ERR_INVALID_ARG;
+    if (misaligned(params, 4) || misaligned(grad, 4) || misaligned(m, 4) || misaligned(v, 4)) return RGBID_ERR_INVALID_ARG;
     if (!(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f)) return RGBID_ERR_INVALID_ARG;
     const float c1 = (float)(1.0 / (1.0 - pow((double)beta1, step)));
     const float c2 = (float)(1.0 / (1.0 - pow((double)beta2, step)));
@@ -690,6 +698,8 @@ extern "C" int rgbid_net_plan(const float* y, int n, const float* max_log_var, i
         return RGBID_ERR_INVALID_ARG;
     if (n_tiers > 0 && !max_log_var) return RGBID_ERR_INVALID_ARG;
     if (d_in == d_out) return RGBID_ERR_INVALID_ARG;
+    if (misaligned(y, 4) || misaligned(d_in, 8) || misaligned(d_out, 8) || misaligned(skipped, 4))
+        return RGBID_ERR_INVALID_ARG;
     if (n == 0) return RGBID_OK;
     Tiers tiers;
     tiers.n = n_tiers;

@@ -3,6 +3,8 @@
 // Level l+1 is the 2x2 box mean of level l: I = ((a + b) + (c + d)) / 4 and
 // W = mean of the valid (> 0) children, 0 when none; odd sizes drop the last
 // row/column; the intrinsics follow f <- f/2, c <- (c + 0.5)/2 - 0.5.
+// A level-0 pixel whose I or W is not a finite number carries no measurement:
+// it enters as a hole (W = 0), with I = 0 where I itself is not finite.
 // Every level is computed in FP32 from the level-0 planes by the same
 // quadtree of 2x2 means (so the reduced-precision storage form rounds each
 // level once, never a rounded parent), and stored as interleaved (I, W) pairs.
@@ -52,9 +54,11 @@ template <>
 struct Down<0> {
     static __device__ __forceinline__ IWf at(const PyrSrc& s, int x, int y) {
         const size_t o = (size_t)y * s.pitch + x;
+        const float i = __ldg(s.I + o), w = __ldg(s.W + o);
+        const bool fi = isfinite(i);
         IWf r;
-        r.i = __ldg(s.I + o);
-        r.w = __ldg(s.W + o);
+        r.i = fi ? i : 0.f;
+        r.w = (fi && isfinite(w)) ? w : 0.f;
         r.n = 1.f;
         return r;
     }
@@ -127,7 +131,7 @@ extern "C" int rgbid_build_pyramid(const float* I0, const float* W0, int pitch0,
     if (precision != RGBID_PLANES_F32 && precision != RGBID_PLANES_BF16_F16) return RGBID_ERR_UNSUPPORTED;
     if (((uintptr_t)I0 & 3u) || ((uintptr_t)W0 & 3u)) return RGBID_ERR_INVALID_ARG;
     if ((width >> (levels - 1)) < 4 || (height >> (levels - 1)) < 4) return RGBID_ERR_INVALID_ARG;
-    if (!(K0.fx > 0.0) || !(K0.fy > 0.0)) return RGBID_ERR_INVALID_ARG;
+    if (!intrinsics_ok(K0.fx, K0.fy, K0.cx, K0.cy)) return RGBID_ERR_INVALID_ARG;
     const size_t need = rgbid_pyramid_bytes(width, height, levels, precision);
     if (!storage || ((uintptr_t)storage & 255u) || storage_bytes < need) return RGBID_ERR_WORKSPACE;
     cudaStream_t stream = (cudaStream_t)stream_;

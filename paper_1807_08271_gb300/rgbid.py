@@ -111,6 +111,7 @@ SIGNATURES = [
                                     c_void_p, c_size_t, c_void_p]),
     ("rgbid_batch_autotune", c_int, [c_void_p, c_int, c_int, POINTER(AlignParams), c_void_p, c_size_t, c_int,
                                      POINTER(BatchConfig), POINTER(ctypes.c_float), c_void_p]),
+    ("rgbid_probe_wait_timeout", c_int, [ctypes.c_longlong, c_void_p, c_void_p]),
     ("rgbid_net_param_count", c_size_t, []),
     ("rgbid_net_param_offset", c_size_t, [c_int, c_int]),
     ("rgbid_net_workspace_bytes", c_size_t, [c_int]),
@@ -326,6 +327,12 @@ def rgbid_batch_autotune(d_items, n_items: int, precision: int, params: AlignPar
                                       ctypes.byref(ms), _stream_ptr(stream))
     _check("rgbid_batch_autotune", code)
     return best, float(ms.value)
+
+
+def rgbid_probe_wait_timeout(budget_cycles: int, d_timeouts, stream=None):
+    """One cluster-reduction round with the partials withheld: every wait runs out (see rgbid.h)."""
+    _check("rgbid_probe_wait_timeout", lib().rgbid_probe_wait_timeout(budget_cycles, _ptr(d_timeouts),
+                                                                      _stream_ptr(stream)))
 
 
 NET_IN_H, NET_IN_W, NET_IN_C, NET_OUT, NET_LAYERS = 60, 80, 4, 7, 6

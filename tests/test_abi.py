@@ -6,6 +6,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -163,3 +164,78 @@ def test_batched_call_rejects_bad_arguments_before_launching(binding):
     # an empty batch with a valid (host-memory stand-in) workspace enqueues nothing
     addr = (ctypes.addressof(ws) + 255) // 256 * 256
     assert L.rgbid_align_batched(None, 0, 0, ctypes.byref(p), None, ctypes.c_void_p(addr), 256, None) == b.OK
+
+
+def _no_device():
+    """The pointer-check tests below pass made-up device addresses: they run only
+    where no GPU exists, so a check that failed to reject could never reach a kernel."""
+    try:
+        import torch
+        return not torch.cuda.is_available()
+    except ImportError:  # pragma: no cover
+        return True
+
+
+@pytest.mark.skipif(not _no_device(), reason="made-up device addresses stay off machines with a GPU")
+def test_misaligned_and_nonfinite_arguments_are_rejected_on_the_host(binding):
+    b = binding
+    L = b.lib()
+    V = ctypes.c_void_p
+    base = 0x7F0000000000                                  # 256-byte aligned stand-in addresses
+    K = b.Intrinsics(131.25, 131.25, 79.5, 59.5)
+
+    def pyr(iw, prec=b.PLANES_F32, K=K):
+        P = b.Pyramid()
+        P.levels, P.precision = 1, prec
+        lv = P.lv[0]
+        lv.width, lv.height, lv.pitch, lv.IW, lv.K = 160, 120, 160, iw, K
+        return P
+
+    p = b.rgbid_default_params(levels=1, iters=[3])
+    ws, wsb = V(base + 0x100000), 1 << 24
+    res = V(base + 0x200000)
+
+    def align(A, B, T=None, on_dev=0, result=res, params=p):
+        return L.rgbid_align(ctypes.byref(A), ctypes.byref(B), T, on_dev, ctypes.byref(params), ws, wsb, result, None)
+
+    good = pyr(base)
+    assert align(pyr(base + 4), good) == b.ERR_INVALID_ARG                   # f32 pixel is 8 bytes
+    assert align(good, pyr(base + 4)) == b.ERR_INVALID_ARG
+    assert align(pyr(base + 2, b.PLANES_BF16_F16), pyr(base, b.PLANES_BF16_F16)) == b.ERR_INVALID_ARG
+    assert align(good, good, result=V(base + 0x200004)) == b.ERR_INVALID_ARG  # result record: 8 bytes
+    assert align(good, good, T=V(base + 0x300004), on_dev=1) == b.ERR_INVALID_ARG
+    q = b.rgbid_default_params(levels=1, iters=[3])
+    q.level_iters = base + 0x400002
+    assert align(good, good, params=q) == b.ERR_INVALID_ARG
+    for bad in ((np.nan, 131.25, 79.5, 59.5), (131.25, np.inf, 79.5, 59.5), (131.25, 131.25, np.nan, 59.5),
+                (131.25, 131.25, 79.5, -np.inf), (-1.0, 131.25, 79.5, 59.5)):
+        Kb = b.Intrinsics(*bad)
+        assert align(pyr(base, K=Kb), pyr(base, K=Kb)) == b.ERR_INVALID_ARG, bad
+        out = b.Pyramid()
+        assert L.rgbid_build_pyramid(V(base), V(base + 0x10000), 160, 160, 120, Kb, 1, 0, ws, wsb,
+                                     ctypes.byref(out), None) == b.ERR_INVALID_ARG, bad
+    # fusion, keyframe initialisation, pose helpers
+    f = [V(base + i * 0x100000) for i in range(5)]
+    T, s = V(base + 0x600000), V(base + 0x700000)
+    assert L.rgbid_fuse_keyframe(V(base + 2), *f[1:3], 160, *f[3:5], 160, 160, 120, K, T, s, 1, 1, None) == \
+        b.ERR_INVALID_ARG
+    assert L.rgbid_fuse_keyframe(*f[:3], 160, *f[3:5], 160, 160, 120, K, V(base + 0x600004), s, 1, 1, None) == \
+        b.ERR_INVALID_ARG
+    assert L.rgbid_fuse_keyframe(*f[:3], 160, *f[3:5], 160, 160, 120, b.Intrinsics(131.25, 131.25, np.nan, 59.5),
+                                 T, s, 1, 1, None) == b.ERR_INVALID_ARG
+    assert L.rgbid_init_keyframe(*f[:3], 160, f[3], V(base + 0x400001), 160, 160, 120, None) == b.ERR_INVALID_ARG
+    assert L.rgbid_predict_pose(T, V(base + 0x600004), s, None) == b.ERR_INVALID_ARG
+    assert L.rgbid_compose_pose(T, 0, s, V(base + 0x800004), None) == b.ERR_INVALID_ARG
+    # batched alignment and the network
+    assert L.rgbid_align_batched(V(base + 4), 1, 0, ctypes.byref(p), None, ws, wsb, None) == b.ERR_INVALID_ARG
+    nws = b.rgbid_net_workspace_bytes(4)
+    assert L.rgbid_net_forward(V(base + 2), f[1], 4, f[2], ws, nws, None) == b.ERR_INVALID_ARG
+    assert L.rgbid_net_backward(*f[:2], 4, V(base + 0x300002), f[3], ws, nws, None) == b.ERR_INVALID_ARG
+    assert L.rgbid_net_loss(f[0], f[1], 4, f[2], V(base + 0x400002), None) == b.ERR_INVALID_ARG
+    assert L.rgbid_net_adam(*f[:3], V(base + 0x400001), 1, 1e-3, 0.9, 0.999, 1e-8, None) == b.ERR_INVALID_ARG
+    assert L.rgbid_net_inputs(V(base + 4), 1, 0, f[1], None) == b.ERR_INVALID_ARG
+    assert L.rgbid_net_init(V(base + 2), 1, None) == b.ERR_INVALID_ARG
+    assert L.rgbid_net_plan(f[0], 1, None, 0, V(base + 0x100004), f[2], None, None) == b.ERR_INVALID_ARG
+    # the wait-timeout probe's own arguments
+    assert L.rgbid_probe_wait_timeout(-1, f[0], None) == b.ERR_INVALID_ARG
+    assert L.rgbid_probe_wait_timeout(1000, None, None) == b.ERR_INVALID_ARG
