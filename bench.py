@@ -292,11 +292,10 @@ def native(args):
                     e1 = torch.cuda.Event(enable_timing=True)
                     e0.record(stream)
                 if e2e:
-                    Ik = torch.empty((H, W), dtype=torch.float32, device=dev)
-                    Wk = torch.empty((H, W), dtype=torch.float32, device=dev)
-                    Ik.copy_(I_host[k], non_blocking=True)
-                    Wk.copy_(W_host[k], non_blocking=True)
-                    trk.step(Ik, Wk, stream)
+                    # the frame goes from pinned host memory straight into the tracker's staging pair
+                    trk.I_in.copy_(I_host[k], non_blocking=True)
+                    trk.W_in.copy_(W_host[k], non_blocking=True)
+                    trk.step(trk.I_in, trk.W_in, stream)
                     res_host.copy_(trk.res[0], non_blocking=True)
                 else:
                     trk.step(I_all[k], W_all[k], stream)

@@ -395,6 +395,21 @@ int rgbid_eval_step(const rgbid_pyramid* ref, const rgbid_pyramid* cur, int leve
                     float* r_I, float* r_W, uint8_t* mask_I, uint8_t* mask_W,
                     rgbid_align_result* d_result, void* stream);
 
+/* Chebyshev series (in tau = (nu - m)/h over [nu_lo, nu_hi], m and h the
+ * interval's centre and half-width) of the sample-independent part of the
+ * degrees-of-freedom equation ("Error distribution and robust optimisation",
+ * eq. robustnessValue).  With w_i = (nu + 1)/(nu + x_i^2) the equation
+ * f(nu) = n c(nu) + sum_i (ln w_i - w_i) reads
+ * f(nu) = n g(nu) - sum_i [ln(nu + x_i^2) + w_i], where
+ * g(nu) = psi((nu+1)/2) - psi(nu/2) + 1 + ln nu; the alignment adds g's series
+ * to the series of the sample sums and bisects on the result.  Computed on the host in FP64 (22 terms, interpolation at 64 Chebyshev
+ * nodes) and used by every alignment entry point; exposed so it can be
+ * checked.  Writes min(n_out, 22) coefficients g_0.. (plain convention,
+ * g = sum_k g_k T_k(tau)) to host memory `out` and returns their number, or
+ * -RGBID_ERR_INVALID_ARG, or -RGBID_ERR_UNSUPPORTED for an interval the
+ * alignment rejects too ((lo + hi)/(hi - lo) < 1.4). */
+int rgbid_nu_constant_series(double nu_lo, double nu_hi, float* out, int n_out);
+
 /* Diagnostic of the device-side failure detection (the paper has no
  * counterpart).  Launches one 4-CTA cluster that runs one round of the
  * alignment's cluster reduction with every CTA withholding its partials, so

@@ -61,6 +61,7 @@ struct RobustArgs {
     int update;               // 0: results only (one evaluated step), 1: also update the pose
     int min_valid;
     int finalize_only;        // 1: finish the previous sweep and stop (no robust estimation)
+    float nu_g[kNuGTerms];    // Chebyshev series of the nu equation's constant part on [nu_lo, nu_hi]
 };
 
 struct SweepArgs {
@@ -219,9 +220,8 @@ __global__ void __launch_bounds__(kRobustNT) robust_kernel(RobustArgs a) {
     __shared__ __align__(8) unsigned long long mbar[2];
     __shared__ WarpPose sh_wp;
     __shared__ float nu_out[2];
-    __shared__ float cheb[2][2][kChebK + 1];     // per channel: Clenshaw coefficients a_k, b_k
-    __shared__ unsigned bis_mask[2][4];
-    __shared__ int bis_end[2][2];
+    __shared__ float nuF[2][kNuSeries];          // per channel: f(nu) as one Chebyshev series
+    __shared__ float sh_g[kNuGTerms];            // the host series of f's constant part
     __shared__ F2 fin2[kRobustNT / 32][kSlots];
     __shared__ double T_sh[16];
     __shared__ double totd[kSlots];
@@ -229,6 +229,8 @@ __global__ void __launch_bounds__(kRobustNT) robust_kernel(RobustArgs a) {
     __shared__ float xi_f[6];
     __shared__ double xi_d[6];
     __shared__ int ok_flag;
+    __shared__ RobustParams sh_rob_prev;         // rank 0: the parameters the previous sweep used
+    __shared__ int sh_cnt[4];                    // rank 0: iters_done, iters_skipped, status, timeouts
     if (!a.finalize_only && iteration_skipped(a.level_iters, a.level, a.iter)) {
         pdl_wait();
         return;
@@ -237,6 +239,46 @@ __global__ void __launch_bounds__(kRobustNT) robust_kernel(RobustArgs a) {
         mbar_init(&mbar[0], 1);
         mbar_init(&mbar[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+#pragma unroll
+        for (int k = 0; k < kNuGTerms; ++k) sh_g[k] = a.nu_g[k];
+    }
+    // What this launch reads before the wait comes from grids that completed before
+    // it started (the previous robust launch and the alignment's initialisation,
+    // both ahead of the sweep it waits for): the state fields that CTA 0 writes back,
+    // and the keyframe-side loads of the systematic sample (A's planes do not change
+    // during an alignment).  Only the sweep's partials and the pose need the wait.
+    if (rank == 0) {
+        constexpr int kRobWords = (int)(sizeof(RobustParams) / 4);
+        if (threadIdx.x < kRobWords)
+            reinterpret_cast<int*>(&sh_rob_prev)[threadIdx.x] =
+                __ldcg(reinterpret_cast<const int*>(&a.st->rob) + threadIdx.x);
+        else if (threadIdx.x == 32) sh_cnt[0] = __ldcg(&a.st->iters_done);
+        else if (threadIdx.x == 33) sh_cnt[1] = __ldcg(&a.st->iters_skipped);
+        else if (threadIdx.x == 34) sh_cnt[2] = __ldcg(&a.st->status);
+        else if (threadIdx.x == 35) sh_cnt[3] = __ldcg(&a.st->timeouts);
+    }
+    static_assert(sizeof(WarpPose) == 16 * sizeof(float), "the warp pose is 16 floats");
+    if (threadIdx.x >= 64 && threadIdx.x < 80) T_sh[threadIdx.x - 64] = __ldcg(a.st->T + (threadIdx.x - 64));
+    else if (threadIdx.x >= 96 && threadIdx.x < 112)
+        reinterpret_cast<float*>(&sh_wp)[threadIdx.x - 96] =
+            __ldcg(reinterpret_cast<const float*>(&a.st->wp) + (threadIdx.x - 96));
+    PxA sa[MAXS];
+    int su[MAXS], sv[MAXS];
+    {
+        const int gt = rank * kRobustNT + (int)threadIdx.x;
+#pragma unroll
+        for (int k = 0; k < MAXS; ++k) {
+            const int i = gt + k * (CL * kRobustNT);
+            sa[k].ok = false;
+            su[k] = 0;
+            sv[k] = 0;
+            if (!a.finalize_only && i < a.nsamp) {
+                const int sy = i / a.nsx, sx = i - sy * a.nsx;
+                su[k] = sx * a.s;
+                sv[k] = sy * a.s;
+                stage_a<PREC>(a.A, su[k], sv[k], sa[k]);
+            }
+        }
     }
     cl.sync();   // every barrier of the cluster is initialised before any remote store
     pdl_wait();  // the previous sweep's partials (and the state) are complete and visible
@@ -249,11 +291,18 @@ __global__ void __launch_bounds__(kRobustNT) robust_kernel(RobustArgs a) {
     //      and every CTA solves H xi = -g and updates its copy of the pose
     if (nb) {
         const int t = (int)threadIdx.x, lane = t & 31, grp = t >> 5;
-        if (t < 16) T_sh[t] = __ldcg(a.st->T + t);
         F2 acc{0.f, 0.f};
-        for (unsigned int b = (unsigned)rank + (unsigned)CL * (unsigned)grp; b < nb; b += (unsigned)CL * (kRobustNT / 32)) {
-            const float2 v = __ldcg(a.partials + (size_t)b * kSlots + lane);
-            acc.add(F2{v.x, v.y});
+        // four partials of this thread in flight at once, summed in ascending block order
+        constexpr unsigned kStride = (unsigned)CL * (kRobustNT / 32);
+        for (unsigned int b0 = (unsigned)rank + (unsigned)CL * (unsigned)grp; b0 < nb; b0 += 4u * kStride) {
+            float2 v[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const unsigned int b = b0 + (unsigned)q * kStride;
+                v[q] = b < nb ? __ldcg(a.partials + (size_t)b * kSlots + lane) : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc.add(F2{v[q].x, v[q].y});
         }
         fin2[grp][lane] = acc;
         __syncthreads();
@@ -309,9 +358,7 @@ __global__ void __launch_bounds__(kRobustNT) robust_kernel(RobustArgs a) {
                     warp_apply_update(xi, T_sh);
                 }
                 warp_make_pose(T_sh, &sh_wp);
-            } else if (lane < 16) {
-                reinterpret_cast<float*>(&sh_wp)[lane] = __ldcg(reinterpret_cast<const float*>(&a.st->wp) + lane);
-            }
+            }   // else sh_wp keeps the pose loaded at the start
             __syncwarp();
             if (rank == 0) {
                 // the step's results and the new state (written once, by CTA 0)
@@ -334,7 +381,7 @@ __global__ void __launch_bounds__(kRobustNT) robust_kernel(RobustArgs a) {
                 } else if (lane == kSlotNW) {
                     res->n_valid[1] = (int)tf;
                 } else if (lane == 30) {
-                    const RobustParams rob = st->rob;     // the parameters the sweep used
+                    const RobustParams rob = sh_rob_prev;  // the parameters the sweep used
                     res->mu[0] = rob.mu[0]; res->mu[1] = rob.mu[1];
                     res->sigma[0] = rob.sigma[0]; res->sigma[1] = rob.sigma[1];
                     res->nu[0] = rob.nu[0]; res->nu[1] = rob.nu[1];
@@ -346,14 +393,20 @@ __global__ void __launch_bounds__(kRobustNT) robust_kernel(RobustArgs a) {
                     }
                     if (lane < 16) res->T[lane] = T_sh[lane];
                     if (lane == 0) {
+                        const int done = sh_cnt[0] + 1;
+                        int skipped = sh_cnt[1], status = sh_cnt[2];
                         if (!ok_flag) {
-                            st->iters_skipped += 1;
-                            st->status = RGBID_ERR_DEGENERATE;
+                            skipped += 1;
+                            status = RGBID_ERR_DEGENERATE;
+                            st->iters_skipped = skipped;
+                            st->status = status;
                         }
-                        st->iters_done += 1;
-                        res->iters_done = st->iters_done;
-                        res->iters_skipped = st->iters_skipped;
-                        res->status = st->timeouts ? RGBID_ERR_TIMEOUT : st->status;
+                        st->iters_done = done;
+                        res->iters_done = done;
+                        res->iters_skipped = skipped;
+                        // waits of earlier launches; the closing launch also sees its own
+                        const int to = a.finalize_only ? __ldcg(&st->timeouts) : sh_cnt[3];
+                        res->status = to ? RGBID_ERR_TIMEOUT : status;
                     }
                 }
                 if (lane == 0) st->pending = 0u;
@@ -361,9 +414,7 @@ __global__ void __launch_bounds__(kRobustNT) robust_kernel(RobustArgs a) {
         }
         __syncthreads();
     } else {
-        if (threadIdx.x < 16)
-            reinterpret_cast<float*>(&sh_wp)[threadIdx.x] = __ldcg(reinterpret_cast<const float*>(&a.st->wp) + threadIdx.x);
-        __syncthreads();
+        __syncthreads();   // sh_wp: the pose loaded at the start
     }
     if (a.finalize_only) {
         cl.sync();   // every remote write into this CTA has landed before it exits
@@ -375,24 +426,8 @@ __global__ void __launch_bounds__(kRobustNT) robust_kernel(RobustArgs a) {
     //      thread go through each evaluation stage together so their loads overlap
     float rs[2][MAXS];
     {
-        const int gt = rank * kRobustNT + (int)threadIdx.x;
-        PxA sa[MAXS];
         PxW sw[MAXS];
         PxB sb[MAXS];
-        int su[MAXS], sv[MAXS];
-#pragma unroll
-        for (int k = 0; k < MAXS; ++k) {
-            const int i = gt + k * (CL * kRobustNT);
-            sa[k].ok = false;
-            su[k] = 0;
-            sv[k] = 0;
-            if (i < a.nsamp) {
-                const int sy = i / a.nsx, sx = i - sy * a.nsx;
-                su[k] = sx * a.s;
-                sv[k] = sy * a.s;
-                stage_a<PREC>(a.A, su[k], sv[k], sa[k]);
-            }
-        }
 #pragma unroll
         for (int k = 0; k < MAXS; ++k) stage_w(a.A, a.B, wp, su[k], sv[k], sa[k], sw[k]);
 #pragma unroll
@@ -511,14 +546,12 @@ __global__ void __launch_bounds__(kRobustNT) robust_kernel(RobustArgs a) {
     cl.sync();   // every remote read of this CTA's shared memory is complete
     if (rank != 0) return;
 
-    if (do_nu) {
-        // threads [128 c, 128 c + 128) solve channel c
-        const int c = threadIdx.x >> 7, lt = threadIdx.x & 127;
+    if (do_nu && threadIdx.x < 64) {
+        // warp c solves channel c
+        const int c = threadIdx.x >> 5;
         float nuc = nu0;
-        if (ok[c])
-            nuc = bisect_nu_group(tot + c * kChebVals, n[c], lo0, hi0, a.bisect_steps, lt, 1 + c, cheb[c][0],
-                                  cheb[c][1], bis_mask[c], bis_end[c]);
-        if (lt == 0) nu_out[c] = nuc;
+        if (ok[c]) nuc = bisect_nu_warp(tot + c * kChebVals, n[c], sh_g, lo0, hi0, a.bisect_steps, nuF[c]);
+        if ((threadIdx.x & 31) == 0) nu_out[c] = nuc;
     }
     __syncthreads();
     if (do_nu) {
@@ -548,6 +581,20 @@ __global__ void __launch_bounds__(kSweepNT, 2) sweep_kernel(SweepArgs a) {
         pdl_wait();
         return;
     }
+    // the keyframe-side loads need no wait: A's planes do not change during an alignment
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int u = blockIdx.x * kTileW + lane;
+    // the thread's rows go through each stage together, so the loads of a stage
+    // for all rows are in flight at once
+    constexpr int R = kSweepRowsPerWarp;
+    const int v0 = blockIdx.y * kTileH + warp * R;
+    PxA sa[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int v = v0 + r;
+        sa[r].ok = false;
+        if (u < a.A.w && v < a.A.h) stage_a<PREC>(a.A, u, v, sa[r]);
+    }
     pdl_wait();   // the robust parameters (and pose) of this iteration are complete and visible
     if (threadIdx.x < 16) {
         reinterpret_cast<float*>(&sh_wp)[threadIdx.x] = __ldcg(reinterpret_cast<const float*>(&a.st->wp) + threadIdx.x);
@@ -563,22 +610,9 @@ __global__ void __launch_bounds__(kSweepNT, 2) sweep_kernel(SweepArgs a) {
 #pragma unroll
     for (int i = 0; i < kSlots; ++i) acc[i] = 0.f;
 
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int u = blockIdx.x * kTileW + lane;
     const bool wantI = rob.ok[0] != 0, wantW = rob.ok[1] != 0;
-    // the thread's rows go through each stage together, so the loads of a stage
-    // for all rows are in flight at once
-    constexpr int R = kSweepRowsPerWarp;
-    const int v0 = blockIdx.y * kTileH + warp * R;
-    PxA sa[R];
     PxW sw[R];
     PxB sb[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int v = v0 + r;
-        sa[r].ok = false;
-        if (u < a.A.w && v < a.A.h) stage_a<PREC>(a.A, u, v, sa[r]);
-    }
 #pragma unroll
     for (int r = 0; r < R; ++r) stage_w(a.A, a.B, wp, u, v0 + r, sa[r], sw[r]);
 #pragma unroll
@@ -801,6 +835,8 @@ static RobustArgs robust_args(const rgbid_pyramid* ref, const rgbid_pyramid* cur
     ra.nu0 = (float)p->nu0;
     ra.nu_lo = p->nu_lo;
     ra.nu_hi = p->nu_hi;
+    const float* g = nu_g_series_cached(p->nu_lo, p->nu_hi);
+    for (int k = 0; k < kNuGTerms; ++k) ra.nu_g[k] = g[k];
     ra.level_iters = nullptr;
     ra.level = l;
     ra.iter = 0;
@@ -995,4 +1031,16 @@ extern "C" int rgbid_probe_wait_timeout(long long budget_cycles, int* d_timeouts
         return RGBID_ERR_CUDA;
     }
     return RGBID_OK;
+}
+
+extern "C" int rgbid_nu_constant_series(double nu_lo, double nu_hi, float* out, int n_out) {
+    if (!out || n_out < 1 || !(nu_lo > 0.0) || !(nu_hi > nu_lo) || !(nu_hi < 1e6)) return -RGBID_ERR_INVALID_ARG;
+    // the intervals the alignment accepts: (lo + hi)/(hi - lo) >= 1.4 keeps nu = 0 far enough
+    // from the interval for 22 terms to reach FP32 accuracy
+    if (nu_lo + nu_hi < 1.4 * (nu_hi - nu_lo)) return -RGBID_ERR_UNSUPPORTED;
+    float g[kNuGTerms];
+    nu_g_series(nu_lo, nu_hi, g);
+    const int n = n_out < kNuGTerms ? n_out : kNuGTerms;
+    for (int k = 0; k < n; ++k) out[k] = g[k];
+    return n;
 }

@@ -50,6 +50,7 @@ struct BatchArgs {
     int precision;
     int scale_iters, bisect_steps, sample_cap, estimate_nu, min_valid;
     float nu0, nu_lo, nu_hi;
+    float nu_g[kNuGTerms];    // Chebyshev series of the nu equation's constant part on [nu_lo, nu_hi]
 };
 
 // Per-alignment descriptors held in each CTA's shared memory.
@@ -266,9 +267,8 @@ __global__ void __launch_bounds__(kBatchNT, 2) batch_align_kernel(BatchArgs a) {
     __shared__ double T_sh[16];
     __shared__ __align__(16) WarpPose wp_sh;
     __shared__ __align__(16) RobustParams rob_sh;
-    __shared__ float cheb[2][2][kChebK + 1];
-    __shared__ unsigned bis_mask[2][4];
-    __shared__ int bis_end[2][2];
+    __shared__ float nuF[2][kNuSeries];
+    __shared__ float sh_g[kNuGTerms];
     __shared__ float nu_out[2];
     __shared__ float Hs[36], gs[6];
     __shared__ float xi_f[6];
@@ -282,6 +282,8 @@ __global__ void __launch_bounds__(kBatchNT, 2) batch_align_kernel(BatchArgs a) {
         mbar_init(&mbar[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         failed = 0;
+#pragma unroll
+        for (int k = 0; k < kNuGTerms; ++k) sh_g[k] = a.nu_g[k];
     }
     cl.sync();   // every barrier of the cluster is initialised before any remote store
 
@@ -518,13 +520,15 @@ __global__ void __launch_bounds__(kBatchNT, 2) batch_align_kernel(BatchArgs a) {
                     }
                     __syncthreads();
                     X.next();
-                    // every CTA bisects on the same totals: threads [128 c, 128 c + 128) take channel c
-                    const int cb = tid >> 7, lt = tid & 127;
-                    float nuc = a.nu0;
-                    if (cb ? ok[1] : ok[0])
-                        nuc = bisect_nu_group(tot + cb * kChebVals, cb ? nres[1] : nres[0], a.nu_lo, a.nu_hi, a.bisect_steps, lt, 1 + cb,
-                                              cheb[cb][0], cheb[cb][1], bis_mask[cb], bis_end[cb]);
-                    if (lt == 0) nu_out[cb] = nuc;
+                    // every CTA bisects on the same totals: warp c takes channel c
+                    if (tid < 64) {
+                        const int cb = tid >> 5;
+                        float nuc = a.nu0;
+                        if (cb ? ok[1] : ok[0])
+                            nuc = bisect_nu_warp(tot + cb * kChebVals, cb ? nres[1] : nres[0], sh_g, a.nu_lo, a.nu_hi,
+                                                 a.bisect_steps, nuF[cb]);
+                        if ((tid & 31) == 0) nu_out[cb] = nuc;
+                    }
                     __syncthreads();
                     nu[0] = nu_out[0];
                     nu[1] = nu_out[1];

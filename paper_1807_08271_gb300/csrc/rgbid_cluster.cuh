@@ -6,6 +6,7 @@
 #pragma once
 
 #include "rgbid_device.cuh"
+#include "rgbid_nu.h"
 
 namespace rgbid {
 
@@ -63,30 +64,6 @@ __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.lau
 
 constexpr long long kWaitBudgetCycles = 4000000000LL;   // ~2 s: a wait that exceeds it reports a timeout
 
-// c(nu) = -psi(nu/2) + ln(nu/2) + psi((nu+1)/2) - ln((nu+1)/2) + 1 (eq. robustnessValue),
-// written as D(nu) + 1 - ln(1 + 1/nu) with D(nu) = psi(y + 1/2) - psi(y), y = nu/2.
-// D uses the recurrence psi(z) = psi(z + 1) - 1/z six times (each difference
-// 1/(y+j) - 1/(y+j+1/2) = 0.5/((y+j)(y+j+1/2)) taken in product form) and the
-// asymptotic series of psi (Abramowitz & Stegun 6.3.5, 6.3.18) for the
-// difference at z = y + 6, so no term cancels in FP32.
-__device__ __forceinline__ float nu_const_f(float nu) {
-    const float y = 0.5f * nu;
-    float acc = 0.f;
-#pragma unroll
-    for (int j = 0; j < 6; ++j) {
-        const float z = y + (float)j;
-        acc += __fdividef(0.5f, z * (z + 0.5f));
-    }
-    const float z = y + 6.f, zh = z + 0.5f;
-    const float iz2 = __fdividef(1.f, z * z), ih2 = __fdividef(1.f, zh * zh);
-    // psi(zh) - psi(z) = ln(zh/z) - 1/(2 zh) + 1/(2 z) - sum_k B_2k/(2k) (zh^-2k - z^-2k)
-    auto tail = [](float i2) {
-        return i2 * (1.f / 12.f - i2 * (1.f / 120.f - i2 * (1.f / 252.f - i2 * (1.f / 240.f))));
-    };
-    const float asym = log1pf(__fdividef(0.5f, z)) + __fdividef(0.25f, z * zh) - (tail(ih2) - tail(iz2));
-    return (asym + acc) + 1.f - log1pf(__fdividef(1.f, nu));
-}
-
 // Chebyshev form of the sample sums of eq. robustnessValue.  With
 // nu = m + h tau (tau in [-1, 1] over [nu_lo, nu_hi]) and alpha_i = (m + x_i^2)/h > 1:
 //   ln(nu + x_i^2)  = ln h + ln(beta_i/2) + 2 sum_k (-1)^(k+1) q_i^k / k T_k(tau)
@@ -98,89 +75,88 @@ __device__ __forceinline__ float nu_const_f(float nu) {
 // terms errs by < q_max^(K+1) per sample (q_max = 0.382 for [2, 10], K = 20).
 constexpr int kChebK = 20;
 constexpr int kChebVals = 2 * kChebK + 2;      // SL, P_1..P_K, G_0..G_K per channel
+constexpr int kNuSeries = kChebK + 2;          // terms of f(nu) as one series in tau (degree K + 1)
+static_assert(kNuSeries == kNuGTerms, "the constant part's series has as many terms as f's");
 
-// f(nu) from the Chebyshev coefficients (FP32 Clenshaw): ca[k] = 2 (-1)^(k+1) P_k / k,
-// cb[k] = 2 (-1)^k G_k for k >= 1, so that sum_i ln(alpha_i + tau) = SL + sum_k ca_k T_k(tau)
-// and sum_i 1/(alpha_i + tau) = G_0 + sum_k cb_k T_k(tau).
-__device__ __forceinline__ float nu_equation_cheb(const float* ca, const float* cb, float G0, float n, float SL,
-                                                  float nu, float m, float invh, float lnh) {
-    const float tau = (nu - m) * invh;
+// f(nu) = n g(nu) - n ln h - SL - A(tau) - (nu + 1) B(tau) / h, with
+//   g(nu) = psi((nu+1)/2) - psi(nu/2) + 1 + ln nu = sum_k g_k T_k(tau)   (host series),
+//   A(tau) = sum_i ln(alpha_i + tau) - SL = sum_{k>=1} a_k T_k,   a_k = 2 (-1)^(k+1) P_k / k,
+//   B(tau) = sum_i 1/(alpha_i + tau)      = sum_{k>=0} b_k T_k,   b_0 = G_0, b_k = 2 (-1)^k G_k,
+// and (nu + 1) B / h = ((m + 1)/h) B + tau B, tau T_0 = T_1, tau T_k = (T_{k+1} + T_{k-1})/2.
+// So f is one Chebyshev series F_0 .. F_{K+1} in tau; coefficient j of tau B is
+//   d_j = [j = 1] b_0 + [j >= 2] b_{j-1}/2 + [j + 1 <= K] b_{j+1}/2.
+// Called by the threads lt < kNuSeries of a bisection group; T = the channel's sums.
+__device__ __forceinline__ float nu_series_coefficient(const float* T, float n, const float* g, float m, float h,
+                                                       int j) {
+    auto b = [&](int k) -> float {
+        if (k == 0) return T[1 + kChebK];
+        if (k > kChebK) return 0.f;
+        return ((k & 1) ? -2.f : 2.f) * T[1 + kChebK + k];
+    };
+    const float a = (j >= 1 && j <= kChebK) ? ((j & 1) ? 2.f : -2.f) * __fdividef(T[j], (float)j) : 0.f;
+    float d = 0.f;
+    if (j == 1) d += b(0);
+    if (j >= 2) d += 0.5f * b(j - 1);
+    if (j + 1 <= kChebK) d += 0.5f * b(j + 1);
+    float F = fmaf(n, g[j], -a) - __fdividef(m + 1.f, h) * b(j) - d;
+    if (j == 0) F -= fmaf(n, logf(h), T[0]);
+    return F;
+}
+
+// sum_k F_k T_k(tau) by Clenshaw's recurrence (FP32)
+__device__ __forceinline__ float nu_series_eval(const float* F, float tau) {
     const float t2 = 2.f * tau;
-    float a1 = 0.f, a2 = 0.f, b1 = 0.f, b2 = 0.f;
+    float b1 = 0.f, b2 = 0.f;
 #pragma unroll
-    for (int k = kChebK; k >= 1; --k) {
-        const float an = fmaf(t2, a1, ca[k] - a2);
-        const float bn = fmaf(t2, b1, cb[k] - b2);
-        a2 = a1; a1 = an;
-        b2 = b1; b1 = bn;
+    for (int k = kNuSeries - 1; k >= 1; --k) {
+        const float bn = fmaf(t2, b1, F[k] - b2);
+        b2 = b1;
+        b1 = bn;
     }
-    const float A = fmaf(tau, a1, -a2);            // Clenshaw end with c_0 = 0
-    const float B = fmaf(tau, b1, G0 - b2);
-    // f = n [c(nu) + ln(nu + 1) - ln h] - SL - A - (nu + 1) B / h
-    const float base = n * (nu_const_f(nu) + logf(nu + 1.f) - lnh) - SL;
-    return base - A - (nu + 1.f) * B * invh;
+    return fmaf(tau, b1, F[0] - b2);
 }
 
 // nu of one channel by bisection on eq. robustnessValue over [lo0, hi0], run by
-// a group of 128 threads that synchronise on named barrier `bar_id` (lt = the
-// thread's index in the group).  T holds the channel's cluster sums (SL,
-// P_1..P_K, G_0..G_K), nc its residual count.  The first section evaluates
-// f(hi), f(lo) and 63 interior points (6 halvings), later sections 127 points
-// (7 halvings); each replays exactly the bisection's decisions at the same
-// dyadic midpoints.  ca, cb (K + 1 floats each), mask (4 words) and ends (2
-// ints) are the group's shared-memory scratch.  Every thread of the group
-// returns the same nu.
-__device__ __forceinline__ float bisect_nu_group(const float* T, float nc, float lo0, float hi0, int steps, int lt,
-                                                 int bar_id, float* ca, float* cb, unsigned* mask, int* ends) {
-    const int lane = lt & 31, gw = lt >> 5;
+// one warp (all 32 lanes call; every lane returns the same nu).  T holds the
+// channel's cluster sums (SL, P_1..P_K, G_0..G_K), nc its residual count, g the
+// host series of the constant part; F (kNuSeries floats of shared memory) is
+// the warp's scratch for f's series.  Each round evaluates f at the 31 interior
+// dyadic points of the current bracket (5 halvings; the first round also at
+// hi and lo) and replays the bisection's decisions on the ballot of their signs,
+// so the result is the midpoint of the bracket the plain bisection reaches
+// after `steps` halvings at the same points.
+__device__ __forceinline__ float bisect_nu_warp(const float* T, float nc, const float* g, float lo0, float hi0,
+                                                int steps, float* F) {
+    const int lane = threadIdx.x & 31;
     const float m = 0.5f * (lo0 + hi0), h = 0.5f * (hi0 - lo0);
-    if (lt >= 1 && lt <= kChebK) {
-        const float sgn = (lt & 1) ? 2.f : -2.f;
-        ca[lt] = sgn * __fdividef(T[lt], (float)lt);
-        cb[lt] = -sgn * T[1 + kChebK + lt];
-    }
-    asm volatile("bar.sync %0, 128;" ::"r"(bar_id) : "memory");
-    const float G0 = T[1 + kChebK], SL = T[0];
-    const float invh = 1.f / h, lnh = logf(h);
-    float lo = lo0, hi = hi0, nuc = 0.5f * (lo0 + hi0);
-    int left = steps;
-    bool first = true, done = false;
-    while (!done) {
-        const int st = left < (first ? 6 : 7) ? left : (first ? 6 : 7);
-        const int np = 1 << st;                  // sub-intervals this round
-        const int off = first ? 2 : 0;           // lanes 0, 1 take the endpoints first
+    if (lane < kNuSeries) F[lane] = nu_series_coefficient(T, nc, g, m, h, lane);
+    __syncwarp();
+    const float invh = 1.f / h;
+    // the ends: f(hi) >= 0 -> hi, f(lo) <= 0 -> lo (as the plain bisection decides first)
+    const float fe = nu_series_eval(F, ((lane == 0 ? hi0 : lo0) - m) * invh);
+    const unsigned ends = __ballot_sync(0xffffffffu, lane == 0 ? fe >= 0.f : (lane == 1 && fe <= 0.f));
+    if (ends & 1u) return hi0;
+    if (ends & 2u) return lo0;
+    float lo = lo0, hi = hi0;
+    for (int left = steps; left > 0;) {
+        const int st = left < 5 ? left : 5;
+        const int np = 1 << st;                              // sub-intervals this round
         const float step = (hi - lo) / (float)np;
-        const int j = lt - off + 1;              // interior point index of this lane
-        float x = 0.f;
-        bool eval = false;
-        if (first && lt == 0) { x = hi; eval = true; }
-        else if (first && lt == 1) { x = lo; eval = true; }
-        else if (j >= 1 && j < np) { x = fmaf((float)j, step, lo); eval = true; }
-        const float f = eval ? nu_equation_cheb(ca, cb, G0, nc, SL, x, m, invh, lnh) : 0.f;
-        const unsigned pos = __ballot_sync(0xffffffffu, eval && f > 0.f);
-        if (lane == 0) mask[gw] = pos;
-        if (first && lt == 0) ends[0] = (f >= 0.f) ? 1 : 0;   // f(hi) >= 0
-        if (first && lt == 1) ends[1] = (f <= 0.f) ? 1 : 0;   // f(lo) <= 0
-        asm volatile("bar.sync %0, 128;" ::"r"(bar_id) : "memory");
-        if (first && ends[0]) { nuc = hi0; done = true; }
-        else if (first && ends[1]) { nuc = lo0; done = true; }
-        else {
-            int jl = 0, jh = np;
-            for (int q = 0; q < st; ++q) {
-                const int jm = (jl + jh) >> 1;
-                const int L = jm - 1 + off;
-                if ((mask[L >> 5] >> (L & 31)) & 1u) jl = jm; else jh = jm;
-            }
-            const float nlo = fmaf((float)jl, step, lo), nhi = fmaf((float)jh, step, lo);
-            lo = nlo;
-            hi = nhi;
-            left -= st;
-            first = false;
-            if (left == 0) { nuc = 0.5f * (lo + hi); done = true; }
+        const int j = lane + 1;                              // interior point j of this lane
+        const bool eval = j < np;
+        const float f = eval ? nu_series_eval(F, (fmaf((float)j, step, lo) - m) * invh) : 0.f;
+        const unsigned pos = __ballot_sync(0xffffffffu, eval && f > 0.f);   // bit j-1: f at point j > 0
+        int jl = 0, jh = np;
+        for (int q = 0; q < st; ++q) {
+            const int jm = (jl + jh) >> 1;
+            if ((pos >> (jm - 1)) & 1u) jl = jm; else jh = jm;
         }
-        asm volatile("bar.sync %0, 128;" ::"r"(bar_id) : "memory");   // masks are reused next round
+        const float nlo = fmaf((float)jl, step, lo), nhi = fmaf((float)jh, step, lo);
+        lo = nlo;
+        hi = nhi;
+        left -= st;
     }
-    return nuc;
+    return 0.5f * (lo + hi);
 }
 
 __device__ __forceinline__ void accumulate(float (&acc)[kSlots], const float (&J)[6], float w, float r) {

@@ -425,26 +425,33 @@ __device__ __forceinline__ void warp_apply_update(const float xi[6], double* T) 
         const float sh = sinf(0.5f * t);
         B = 2.f * sh * sh / t2;
     }
-    // Mi = exp(xi)^-1 = [R^T, -R^T v], R = I + A [th]x + B ([th][th]^T - t2 I), row i of R^T = column i of R
+    // Mi = exp(xi)^-1 = [R^T, -R^T v], R = I + A [th]x + B ([th][th]^T - t2 I), row i of R^T = column i of R.
+    // With R^T = I + D the new 3x4 block is T + (D T_{:,j} - [j = 3] (v + D v)): the correction is
+    // formed in FP32 (|D| <= |theta|, so its rounding stays near 1e-8 of the pose's scale) and added
+    // to the FP64 pose once, one FP64 add per entry instead of a 3x3 FP64 product.
     double Tn = 0.0;
     if (lane < 12) {
-        const int i = lane / 4, j = lane % 4;
-        const double th[3] = {(double)tx, (double)ty, (double)tz};
-        const double Ad = A, Bd = B, t2d = (double)tx * tx + (double)ty * ty + (double)tz * tz;
-        double Rt[3];   // row i of R^T = (R_0i, R_1i, R_2i)
+        const int i = lane >> 2, j = lane & 3;
+        const float thi = i == 0 ? tx : (i == 1 ? ty : tz);
+        const float th[3] = {tx, ty, tz};
+        float D[3];   // row i of R^T - I: D_ik = R_ki - delta_ki
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            double cross = 0.0;    // ([th]x)_ki
-            if (k == 0 && i == 1) cross = -th[2];
-            if (k == 0 && i == 2) cross = th[1];
-            if (k == 1 && i == 0) cross = th[2];
-            if (k == 1 && i == 2) cross = -th[0];
-            if (k == 2 && i == 0) cross = -th[1];
-            if (k == 2 && i == 1) cross = th[0];
-            Rt[k] = (k == i ? 1.0 : 0.0) + Ad * cross + Bd * (th[k] * th[i] - (k == i ? t2d : 0.0));
+            float cross = 0.f;    // ([th]x)_ki
+            if (k == 0 && i == 1) cross = -tz;
+            if (k == 0 && i == 2) cross = ty;
+            if (k == 1 && i == 0) cross = tz;
+            if (k == 1 && i == 2) cross = -tx;
+            if (k == 2 && i == 0) cross = -ty;
+            if (k == 2 && i == 1) cross = tx;
+            D[k] = fmaf(A, cross, B * fmaf(th[k], thi, k == i ? -t2 : 0.f));
         }
-        Tn = Rt[0] * T[0 * 4 + j] + Rt[1] * T[1 * 4 + j] + Rt[2] * T[2 * 4 + j];
-        if (j == 3) Tn -= Rt[0] * (double)xi[0] + Rt[1] * (double)xi[1] + Rt[2] * (double)xi[2];
+        float c = fmaf(D[0], (float)T[0 * 4 + j], fmaf(D[1], (float)T[1 * 4 + j], D[2] * (float)T[2 * 4 + j]));
+        if (j == 3) {
+            const float vi = i == 0 ? xi[0] : (i == 1 ? xi[1] : xi[2]);
+            c -= vi + fmaf(D[0], xi[0], fmaf(D[1], xi[1], D[2] * xi[2]));
+        }
+        Tn = T[i * 4 + j] + (double)c;
     }
     __syncwarp();
     if (lane < 12) T[lane] = Tn;

@@ -112,6 +112,7 @@ SIGNATURES = [
     ("rgbid_batch_autotune", c_int, [c_void_p, c_int, c_int, POINTER(AlignParams), c_void_p, c_size_t, c_int,
                                      POINTER(BatchConfig), POINTER(ctypes.c_float), c_void_p]),
     ("rgbid_probe_wait_timeout", c_int, [ctypes.c_longlong, c_void_p, c_void_p]),
+    ("rgbid_nu_constant_series", c_int, [c_double, c_double, POINTER(ctypes.c_float), c_int]),
     ("rgbid_net_param_count", c_size_t, []),
     ("rgbid_net_param_offset", c_size_t, [c_int, c_int]),
     ("rgbid_net_workspace_bytes", c_size_t, [c_int]),
@@ -327,6 +328,15 @@ def rgbid_batch_autotune(d_items, n_items: int, precision: int, params: AlignPar
                                       ctypes.byref(ms), _stream_ptr(stream))
     _check("rgbid_batch_autotune", code)
     return best, float(ms.value)
+
+
+def rgbid_nu_constant_series(nu_lo: float = 2.0, nu_hi: float = 10.0, n: int = 22):
+    """Host-computed Chebyshev coefficients of the nu equation's constant part (see rgbid.h)."""
+    out = (ctypes.c_float * n)()
+    k = lib().rgbid_nu_constant_series(nu_lo, nu_hi, out, n)
+    if k < 0:
+        _check("rgbid_nu_constant_series", -k)
+    return list(out)[:k]
 
 
 def rgbid_probe_wait_timeout(budget_cycles: int, d_timeouts, stream=None):

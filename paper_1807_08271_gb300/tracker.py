@@ -13,6 +13,15 @@ Per frame k, entirely enqueued on one CUDA stream (no host round trip):
   5. rebuild the keyframe's pyramid.
 Each frame's result (pose relative to its keyframe, robust parameters, ...) is
 copied to a device array so that the host reads them once at the end.
+
+With ``graphs=True`` (the default) steps 1-5 of a frame are one CUDA graph
+replay: a fusing frame and a keyframe-switching frame each have a graph,
+captured after the first eager frame of its kind, which reads the frame from a
+fixed staging pair; per frame the host then copies the frame into staging,
+replays the graph and copies the frame's result into the result array, instead
+of enqueueing some fifty launches.  The per-launch timing hook of the
+alignment (``params.timing``) needs the eager path, which step() takes while
+it is attached.
 """
 from __future__ import annotations
 
@@ -24,7 +33,7 @@ from . import rgbid as R
 class Tracker:
     def __init__(self, width: int, height: int, K, levels: int = 4, iters=(5, 5, 5, 10), kf_every: int = 20,
                  precision: int = R.PLANES_F32, fuse_intensity: bool = True, max_frames: int = 4096,
-                 device="cuda"):
+                 device="cuda", graphs: bool = True):
         import torch
         self.torch = torch
         self.w, self.h, self.K = width, height, tuple(float(k) for k in K)
@@ -46,9 +55,14 @@ class Tracker:
         self.T2 = eye.clone()      # kf_T_{k-2}
         self.Tinit = eye.clone()
         self.Tnew = eye.clone()
+        self.eye16 = eye.clone()
         self.ws = None
         self.k = 0
         self.is_kf = np.zeros(max_frames, dtype=bool)
+        self.graphs = graphs
+        self._graph = {}          # frame kind (True: keyframe switch) -> CUDA graph of steps 1-5
+        self.I_in = torch.zeros((height, width), **f32) if graphs else None   # staging for the graphs
+        self.W_in = torch.zeros((height, width), **f32) if graphs else None
 
     def _T_view(self):
         return self.res[0, 0:128].view(self.torch.float64)
@@ -58,7 +72,8 @@ class Tracker:
         return self.res[0, off:off + 8].view(self.torch.float64)
 
     def step(self, I, W, stream=None):
-        """Process one frame (float32 CUDA tensors [h, w])."""
+        """Process one frame (float32 CUDA tensors [h, w]) on ``stream`` (a
+        torch.cuda.Stream; None: the current stream)."""
         torch = self.torch
         k = self.k
         if k == 0:
@@ -66,29 +81,56 @@ class Tracker:
             self.kfp.build(self.I_kf, self.W_kf, self.K, stream)
             if self.ws is None:
                 self.ws = R.new_workspace(self.kfp.desc, self.params, self.device)
-            self.T1.copy_(torch.eye(4, dtype=torch.float64, device=self.device).reshape(16))
+            self.T1.copy_(self.eye16)
             self.T2.copy_(self.T1)
             self.is_kf[0] = True
             self.k = 1
             return
+        kf = k % self.kf_every == 0
+        s = stream if stream is not None else torch.cuda.current_stream()
+        with torch.cuda.stream(s):
+            eager = not self.graphs or bool(self.params.timing)   # a NULL timing pointer is falsy
+            g = None if eager else self._graph.get(kf)
+            if g is not None:
+                if I is not self.I_in:      # a caller may fill the staging pair itself
+                    self.I_in.copy_(I, non_blocking=True)
+                if W is not self.W_in:
+                    self.W_in.copy_(W, non_blocking=True)
+                g.replay()
+            else:
+                self._frame(I, W, kf, s)
+            self.results[k].copy_(self.res[0], non_blocking=True)
+        if self.graphs and not self.params.timing and kf not in self._graph:
+            self._capture(kf)
+        self.is_kf[k] = kf
+        self.k = k + 1
+
+    def _frame(self, I, W, kf: bool, stream):
+        """Steps 1-5 for frame data I, W; touches no host state, so it can be captured."""
         self.cur.build(I, W, self.K, stream)
         R.rgbid_predict_pose(self.T1, self.T2, self.Tinit, stream)
         R.rgbid_align(self.kfp.desc, self.cur.desc, self.Tinit, self.params, self.ws, self.res, stream)
-        self.results[k].copy_(self.res[0])
-        if k % self.kf_every == 0:
+        if kf:
             # new keyframe = this frame; poses of frames k-1 and k re-expressed in it
             R.rgbid_compose_pose(self._T_view(), True, self.T1, self.Tnew, stream)   # k_T_{k-1}
             self.T2.copy_(self.Tnew)
-            self.T1.copy_(torch.eye(4, dtype=torch.float64, device=self.device).reshape(16))
+            self.T1.copy_(self.eye16)
             R.rgbid_init_keyframe(self.I_kf, self.W_kf, self.C_kf, I, W, stream)
-            self.is_kf[k] = True
         else:
             R.rgbid_fuse_keyframe(self.I_kf, self.W_kf, self.C_kf, I, W, self.K, self._T_view(),
                                   self._sigmaW_view(), self.fuse_intensity, stream)
             self.T2.copy_(self.T1)
             self.T1.copy_(self._T_view())
         self.kfp.build(self.I_kf, self.W_kf, self.K, stream)
-        self.k = k + 1
+
+    def _capture(self, kf: bool):
+        """Capture steps 1-5 of a frame of this kind, reading the staging pair (nothing runs)."""
+        torch = self.torch
+        torch.cuda.synchronize(self.device)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self._frame(self.I_in, self.W_in, kf, torch.cuda.current_stream())
+        self._graph[kf] = g
 
     def trajectory(self):
         """World-from-camera poses of the processed frames (frame 0 = identity), on the host."""

@@ -239,3 +239,21 @@ def test_misaligned_and_nonfinite_arguments_are_rejected_on_the_host(binding):
     # the wait-timeout probe's own arguments
     assert L.rgbid_probe_wait_timeout(-1, f[0], None) == b.ERR_INVALID_ARG
     assert L.rgbid_probe_wait_timeout(1000, None, None) == b.ERR_INVALID_ARG
+
+
+def test_nu_constant_series_matches_digamma(binding):
+    """The host series of the degrees-of-freedom equation's constant part
+    (psi((nu+1)/2) - psi(nu/2) + 1 + ln nu) against scipy's digamma."""
+    from scipy.special import digamma
+    # every interval the alignment accepts has (lo + hi)/(hi - lo) >= 1.4
+    for lo, hi in ((2.0, 10.0), (2.0, 12.0), (1.0, 5.0), (3.0, 4.0)):
+        g = np.array(binding.rgbid_nu_constant_series(lo, hi), dtype=np.float64)
+        assert len(g) == 22
+        nu = np.linspace(lo, hi, 997)
+        tau = (nu - 0.5 * (lo + hi)) / (0.5 * (hi - lo))
+        want = digamma(0.5 * (nu + 1)) - digamma(0.5 * nu) + 1 + np.log(nu)
+        got = np.polynomial.chebyshev.chebval(tau, g)
+        # float32 coefficients: a few ulps of the largest one
+        assert np.abs(got - want).max() < 1e-6 * max(1.0, np.abs(g).max()), (lo, hi)
+    assert binding.lib().rgbid_nu_constant_series(10.0, 2.0, (ctypes.c_float * 4)(), 4) == -binding.ERR_INVALID_ARG
+    assert binding.lib().rgbid_nu_constant_series(1.5, 30.0, (ctypes.c_float * 4)(), 4) == -binding.ERR_UNSUPPORTED

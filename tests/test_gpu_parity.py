@@ -256,6 +256,29 @@ def test_tracking_sequence_prefix_matches_oracle():
     assert np.allclose(Ig[both], Io[both], atol=1e-4)
 
 
+def test_tracking_graph_replay_equals_eager_enqueue():
+    """The CUDA-graph form of the tracker's frame step (one replay per frame) gives
+    the same bits as enqueueing every launch, across two keyframe switches."""
+    from paper_1807_08271_gb300.tracker import Tracker
+    n = 45
+    seq = synth.render_sequence(1, n_frames=n)
+    I_all = torch.from_numpy(seq["I"]).cuda()
+    W_all = torch.from_numpy(seq["W"]).cuda()
+    out = []
+    for graphs in (False, True):
+        trk = Tracker(640, 480, seq["K"], levels=4, iters=(5, 5, 5, 10), kf_every=20, max_frames=n, graphs=graphs)
+        s = torch.cuda.Stream()
+        for k in range(n):
+            trk.step(I_all[k], W_all[k], s)
+        torch.cuda.synchronize()
+        out.append((trk.results.cpu().numpy(), trk.I_kf.cpu().numpy(), trk.W_kf.cpu().numpy(),
+                    trk.C_kf.cpu().numpy(), trk.is_kf.copy()))
+        if graphs:
+            assert set(trk._graph) == {False, True}
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
+
+
 def test_tracking_full_sequence_stays_on_ground_truth():
     """300 frames of the benchmark sequence: every frame's pose stays close to the
     ground truth (no drift from the constant-velocity composition)."""
