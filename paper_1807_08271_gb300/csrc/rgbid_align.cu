@@ -172,12 +172,48 @@ struct ClusterSum {
 #pragma unroll
         for (int step = 1; step < CL; step <<= 1)
 #pragma unroll
-            for (int r = 0; r + step < CL; r += 2 * step) acc[r].add(acc[r + step]);
+            for (int r = 0; r < CL; ++r)      // constant trip count: acc stays in registers
+                if (r % (2 * step) == 0 && r + step < CL) acc[r].add(acc[r + step]);
         return acc[0];
     }
     __device__ __forceinline__ void next() { ++round; }
 
+    // The same round towards CTA 0 alone: every CTA pushes its partial of value t
+    // into CTA 0, which waits and returns the total (the same tree over the ranks);
+    // the other CTAs return at once.  For sums only CTA 0 consumes.
     template <int NV>
+    __device__ __forceinline__ F2 gather(int t, F2 s) {
+        const int par = round & 1;
+        const uint32_t phase = (uint32_t)(round >> 1) & 1u;
+        if (rank == 0 && t == 0) mbar_arrive_expect_tx(&mbar[par], (uint32_t)(CL * NV * sizeof(float2)));
+        st_async_f2(map_to_rank(smem_addr(&recv[par][rank][t]), 0), s.hi, s.lo, map_to_rank(smem_addr(&mbar[par]), 0));
+        if (rank != 0) return F2{0.f, 0.f};
+        const long long t0 = clock64();
+        while (!mbar_try_wait(&mbar[par], phase)) {
+            if (clock64() - t0 > budget) {
+                atomicAdd(timeouts, 1);
+                break;
+            }
+        }
+        F2 acc[CL];
+#pragma unroll
+        for (int r = 0; r < CL; ++r) {
+            const float2 p = recv[par][r][t];
+            acc[r] = F2{p.x, p.y};
+        }
+#pragma unroll
+        for (int step = 1; step < CL; step <<= 1)
+#pragma unroll
+            for (int r = 0; r < CL; ++r)
+                if (r % (2 * step) == 0 && r + step < CL) acc[r].add(acc[r + step]);
+        return acc[0];
+    }
+
+    // Block reduction of per-thread partials v[0..NV) (NV <= 8: one warp sum each;
+    // a multiple of 32: reduce-scatter chunks); then values t < NSEND go through the
+    // cluster: to every CTA (ROOT = false; out[] bit-identical in all CTAs) or to
+    // CTA 0 alone (ROOT = true; out[] valid in CTA 0 only).
+    template <int NV, int NSEND = NV, bool ROOT = false>
     __device__ __forceinline__ void run(float (&v)[NV]) {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
         if constexpr (NV <= 8) {
@@ -198,11 +234,12 @@ struct ClusterSum {
         }
         __syncthreads();
         const int t = threadIdx.x;
-        if (t < NV) {
+        if (t < NSEND) {
             F2 s{0.f, 0.f};
 #pragma unroll
             for (int w = 0; w < kRobustNT / 32; ++w) s.add(red_w[w][t]);
-            out[t] = exchange<NV>(t, s).value();
+            if constexpr (ROOT) out[t] = gather<NSEND>(t, s).value();
+            else out[t] = exchange<NSEND>(t, s).value();
         }
         __syncthreads();
         next();
@@ -225,12 +262,11 @@ __global__ void __launch_bounds__(kRobustNT) robust_kernel(RobustArgs a) {
     __shared__ F2 fin2[kRobustNT / 32][kSlots];
     __shared__ double T_sh[16];
     __shared__ double totd[kSlots];
-    __shared__ float Hs[36], gs[6];
     __shared__ float xi_f[6];
     __shared__ double xi_d[6];
     __shared__ int ok_flag;
     __shared__ RobustParams sh_rob_prev;         // rank 0: the parameters the previous sweep used
-    __shared__ int sh_cnt[4];                    // rank 0: iters_done, iters_skipped, status, timeouts
+    __shared__ int sh_cnt[3];                    // rank 0: iters_done, iters_skipped, status
     if (!a.finalize_only && iteration_skipped(a.level_iters, a.level, a.iter)) {
         pdl_wait();
         return;
@@ -242,6 +278,9 @@ __global__ void __launch_bounds__(kRobustNT) robust_kernel(RobustArgs a) {
 #pragma unroll
         for (int k = 0; k < kNuGTerms; ++k) sh_g[k] = a.nu_g[k];
     }
+    // No CTA stores into another before every barrier of the cluster is
+    // initialised: arrive now, wait once the dependent-launch wait is over.
+    cluster_arrive();
     // What this launch reads before the wait comes from grids that completed before
     // it started (the previous robust launch and the alignment's initialisation,
     // both ahead of the sweep it waits for): the state fields that CTA 0 writes back,
@@ -255,7 +294,6 @@ __global__ void __launch_bounds__(kRobustNT) robust_kernel(RobustArgs a) {
         else if (threadIdx.x == 32) sh_cnt[0] = __ldcg(&a.st->iters_done);
         else if (threadIdx.x == 33) sh_cnt[1] = __ldcg(&a.st->iters_skipped);
         else if (threadIdx.x == 34) sh_cnt[2] = __ldcg(&a.st->status);
-        else if (threadIdx.x == 35) sh_cnt[3] = __ldcg(&a.st->timeouts);
     }
     static_assert(sizeof(WarpPose) == 16 * sizeof(float), "the warp pose is 16 floats");
     if (threadIdx.x >= 64 && threadIdx.x < 80) T_sh[threadIdx.x - 64] = __ldcg(a.st->T + (threadIdx.x - 64));
@@ -280,8 +318,8 @@ __global__ void __launch_bounds__(kRobustNT) robust_kernel(RobustArgs a) {
             }
         }
     }
-    cl.sync();   // every barrier of the cluster is initialised before any remote store
     pdl_wait();  // the previous sweep's partials (and the state) are complete and visible
+    cluster_wait();
     pdl_trigger();
     ClusterSum<CL> R{red_w, recv, tot, mbar, &a.st->timeouts, (uint32_t)rank, 0};
     const unsigned int nb = __ldcg(&a.st->pending);   // the same value in every CTA
@@ -312,33 +350,24 @@ __global__ void __launch_bounds__(kRobustNT) robust_kernel(RobustArgs a) {
             for (int w = 0; w < kRobustNT / 32; ++w) c.add(fin2[w][t]);
             const F2 T2 = R.template exchange<kSlots>(t, c);
             tot[t] = T2.value();
-            totd[t] = (double)T2.hi + (double)T2.lo;
+            if (a.finalize_only) totd[t] = (double)T2.hi + (double)T2.lo;   // for the result record
         }
         __syncthreads();
         R.next();
+        if (a.finalize_only) cluster_arrive();   // the launch's only exchange is over
         if (t < 32) {
-            if (lane < 21) {
-                int i = 0, rem = lane;
-                while (rem >= 6 - i) { rem -= 6 - i; ++i; }
-                const int j = i + rem;
-                Hs[i * 6 + j] = tot[lane];
-                Hs[j * 6 + i] = tot[lane];
-            } else if (lane < 27) {
-                gs[lane - kSlotG] = tot[lane];
-            }
-            __syncwarp();
             if (lane == 0) {
                 const int nI = (int)tot[kSlotNI], nW = (int)tot[kSlotNW];
                 bool okl = a.update && (nI + nW) >= a.min_valid;
                 if constexpr (PREC == RGBID_PLANES_BF16_F16) {
                     // reduced-precision planes: the 6x6 solve runs in FP64
                     double xi[6];
-                    okl = okl && cholesky_solve6_packed_d(Hs, gs, xi);
+                    okl = okl && cholesky_solve6_slots(tot, xi);
 #pragma unroll
                     for (int i = 0; i < 6; ++i) xi_d[i] = okl ? xi[i] : 0.0;
                 } else {
                     float xi[6];
-                    okl = okl && cholesky_solve6_packed(Hs, gs, xi);
+                    okl = okl && cholesky_solve6_slots(tot, xi);
 #pragma unroll
                     for (int i = 0; i < 6; ++i) xi_f[i] = okl ? xi[i] : 0.f;
                 }
@@ -361,37 +390,41 @@ __global__ void __launch_bounds__(kRobustNT) robust_kernel(RobustArgs a) {
             }   // else sh_wp keeps the pose loaded at the start
             __syncwarp();
             if (rank == 0) {
-                // the step's results and the new state (written once, by CTA 0)
+                // the new state (written once, by CTA 0), and in the alignment's closing
+                // launch the result record (no other launch's record would survive)
                 AlignState* st = a.st;
                 rgbid_align_result* res = a.res;
-                const double td = totd[lane];
+                const bool rec = a.finalize_only != 0;
+                const double td = rec ? totd[lane] : 0.0;
                 const float tf = tot[lane];
-                if (lane < 21) {
-                    int i = 0, rem = lane;
-                    while (rem >= 6 - i) { rem -= 6 - i; ++i; }
-                    const int j = i + rem;
-                    res->H[i * 6 + j] = td;
-                    res->H[j * 6 + i] = td;
-                } else if (lane < 27) {
-                    res->g[lane - kSlotG] = td;
-                } else if (lane == kSlotCost) {
-                    res->cost = td;
-                } else if (lane == kSlotNI) {
-                    res->n_valid[0] = (int)tf;
-                } else if (lane == kSlotNW) {
-                    res->n_valid[1] = (int)tf;
-                } else if (lane == 30) {
-                    const RobustParams rob = sh_rob_prev;  // the parameters the sweep used
-                    res->mu[0] = rob.mu[0]; res->mu[1] = rob.mu[1];
-                    res->sigma[0] = rob.sigma[0]; res->sigma[1] = rob.sigma[1];
-                    res->nu[0] = rob.nu[0]; res->nu[1] = rob.nu[1];
+                if (rec) {
+                    if (lane < 21) {
+                        int i = 0, rem = lane;
+                        while (rem >= 6 - i) { rem -= 6 - i; ++i; }
+                        const int j = i + rem;
+                        res->H[i * 6 + j] = td;
+                        res->H[j * 6 + i] = td;
+                    } else if (lane < 27) {
+                        res->g[lane - kSlotG] = td;
+                    } else if (lane == kSlotCost) {
+                        res->cost = td;
+                    } else if (lane == kSlotNI) {
+                        res->n_valid[0] = (int)tf;
+                    } else if (lane == kSlotNW) {
+                        res->n_valid[1] = (int)tf;
+                    } else if (lane == 30) {
+                        const RobustParams rob = sh_rob_prev;  // the parameters the sweep used
+                        res->mu[0] = rob.mu[0]; res->mu[1] = rob.mu[1];
+                        res->sigma[0] = rob.sigma[0]; res->sigma[1] = rob.sigma[1];
+                        res->nu[0] = rob.nu[0]; res->nu[1] = rob.nu[1];
+                    }
                 }
                 if (a.update) {
                     if (ok_flag && lane < 16) {
                         reinterpret_cast<float*>(&st->wp)[lane] = reinterpret_cast<const float*>(&sh_wp)[lane];
                         st->T[lane] = T_sh[lane];
                     }
-                    if (lane < 16) res->T[lane] = T_sh[lane];
+                    if (rec && lane < 16) res->T[lane] = T_sh[lane];
                     if (lane == 0) {
                         const int done = sh_cnt[0] + 1;
                         int skipped = sh_cnt[1], status = sh_cnt[2];
@@ -402,11 +435,12 @@ __global__ void __launch_bounds__(kRobustNT) robust_kernel(RobustArgs a) {
                             st->status = status;
                         }
                         st->iters_done = done;
-                        res->iters_done = done;
-                        res->iters_skipped = skipped;
-                        // waits of earlier launches; the closing launch also sees its own
-                        const int to = a.finalize_only ? __ldcg(&st->timeouts) : sh_cnt[3];
-                        res->status = to ? RGBID_ERR_TIMEOUT : status;
+                        if (rec) {
+                            res->iters_done = done;
+                            res->iters_skipped = skipped;
+                            // expired waits of every launch of the alignment, this one included
+                            res->status = __ldcg(&st->timeouts) ? RGBID_ERR_TIMEOUT : status;
+                        }
                     }
                 }
                 if (lane == 0) st->pending = 0u;
@@ -415,9 +449,13 @@ __global__ void __launch_bounds__(kRobustNT) robust_kernel(RobustArgs a) {
         __syncthreads();
     } else {
         __syncthreads();   // sh_wp: the pose loaded at the start
+        if (a.finalize_only) cluster_arrive();
     }
+    // No CTA leaves before every CTA is past its last exchange (a split barrier:
+    // each arrives once its exchanges are over and waits only when it leaves, so
+    // CTA 0's solve, bisection and writes overlap the barrier's latency).
     if (a.finalize_only) {
-        cl.sync();   // every remote write into this CTA has landed before it exits
+        cluster_wait();
         return;
     }
     const WarpPose wp = sh_wp;
@@ -512,39 +550,63 @@ __global__ void __launch_bounds__(kRobustNT) robust_kernel(RobustArgs a) {
     const float lo0 = (float)a.nu_lo, hi0 = (float)a.nu_hi;
     const float m = 0.5f * (lo0 + hi0), h = 0.5f * (hi0 - lo0);
     if (do_nu) {
-        float v[96];
+        // Both channels' sums advance together in packed pairs (low half: I, high
+        // half: W): this phase is bound by instruction issue on the cluster's 16 SMs,
+        // and the pairs halve the instructions of the 20-term power sums.  A masked
+        // sample contributes exact zeros (q = gamma = 0, no log term).
+        unsigned long long V[kChebVals];
 #pragma unroll
-        for (int i = 0; i < 96; ++i) v[i] = 0.f;
+        for (int i = 0; i < kChebVals; ++i) V[i] = 0ull;
+        const float is0 = ok[0] ? __fdividef(1.f, sig[0]) : 0.f;
+        const float is1 = ok[1] ? __fdividef(1.f, sig[1]) : 0.f;
+#pragma unroll 1
+        for (int k = 0; k < MAXS; ++k) {
+            float r0 = rs[0][0], r1 = rs[1][0];
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            if (!ok[c]) continue;
-            const float is = __fdividef(1.f, sig[c]);
-#pragma unroll
-            for (int k = 0; k < MAXS; ++k) {
-                const float x = (rs[c][k] - mu[c]) * is;
-                if (x == x) {
-                    const float al = __fdividef(fmaf(x, x, m), h);
-                    const float s2 = fmaf(al, al, -1.f);
-                    const float gam = rsqrtf(s2);
-                    const float be = fmaf(s2, gam, al);
-                    const float q = __fdividef(1.f, be);
-                    float* V = v + c * kChebVals;
-                    V[0] += logf(0.5f * be);
-                    V[1 + kChebK] += gam;              // G_0
-                    float qk = q;
-#pragma unroll
-                    for (int kk = 1; kk <= kChebK; ++kk) {
-                        V[kk] += qk;                   // P_k
-                        V[1 + kChebK + kk] = fmaf(gam, qk, V[1 + kChebK + kk]);   // G_k
-                        qk *= q;
-                    }
+            for (int q = 1; q < MAXS; ++q)
+                if (k == q) {
+                    r0 = rs[0][q];
+                    r1 = rs[1][q];
                 }
+            float q2[2], g2[2], l2[2];
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const float x = ((c ? r1 : r0) - mu[c]) * (c ? is1 : is0);
+                const bool use = ok[c] && x == x;
+                const float al = __fdividef(fmaf(x, x, m), h);
+                const float s2 = fmaf(al, al, -1.f);
+                const float gam = rsqrtf(s2);
+                const float be = fmaf(s2, gam, al);
+                q2[c] = use ? __fdividef(1.f, be) : 0.f;
+                g2[c] = use ? gam : 0.f;
+                l2[c] = use ? __logf(0.5f * be) : 0.f;
+            }
+            const unsigned long long Q = f2_pack(q2[0], q2[1]), G = f2_pack(g2[0], g2[1]);
+            V[0] = f2_add(V[0], f2_pack(l2[0], l2[1]));
+            V[1 + kChebK] = f2_add(V[1 + kChebK], G);          // G_0
+            unsigned long long qk = Q;
+#pragma unroll
+            for (int kk = 1; kk <= kChebK; ++kk) {
+                V[kk] = f2_add(V[kk], qk);                       // P_k
+                V[1 + kChebK + kk] = f2_fma(G, qk, V[1 + kChebK + kk]);   // G_k
+                qk = f2_mul(qk, Q);
             }
         }
-        R.run(v);
+        float v[96];
+#pragma unroll
+        for (int i = 0; i < kChebVals; ++i) {
+            v[i] = f2_lo(V[i]);
+            v[kChebVals + i] = f2_hi(V[i]);
+        }
+#pragma unroll
+        for (int i = 2 * kChebVals; i < 96; ++i) v[i] = 0.f;
+        R.template run<96, 2 * kChebVals, true>(v);   // only CTA 0 bisects: the sums go to it alone
     }
-    cl.sync();   // every remote read of this CTA's shared memory is complete
-    if (rank != 0) return;
+    cluster_arrive();
+    if (rank != 0) {
+        cluster_wait();
+        return;
+    }
 
     if (do_nu && threadIdx.x < 64) {
         // warp c solves channel c
@@ -569,6 +631,7 @@ __global__ void __launch_bounds__(kRobustNT) robust_kernel(RobustArgs a) {
             rp.ok[c] = ok[c] ? 1 : 0;
         }
     }
+    cluster_wait();
 }
 
 // ---------------------------------------------------------------- sweep + solve

@@ -155,7 +155,8 @@ struct BatchXchg {
 #pragma unroll
         for (int step = 1; step < CL; step <<= 1)
 #pragma unroll
-            for (int r = 0; r + step < CL; r += 2 * step) acc[r].add(acc[r + step]);
+            for (int r = 0; r < CL; ++r)      // constant trip count: acc stays in registers
+                if (r % (2 * step) == 0 && r + step < CL) acc[r].add(acc[r + step]);
         return acc[0];
     }
     __device__ __forceinline__ void next() { ++round; }
@@ -270,7 +271,6 @@ __global__ void __launch_bounds__(kBatchNT, 2) batch_align_kernel(BatchArgs a) {
     __shared__ float nuF[2][kNuSeries];
     __shared__ float sh_g[kNuGTerms];
     __shared__ float nu_out[2];
-    __shared__ float Hs[36], gs[6];
     __shared__ float xi_f[6];
     __shared__ double xi_d[6];
     __shared__ int ok_flag, n_done, n_skipped, j_status;
@@ -632,27 +632,17 @@ __global__ void __launch_bounds__(kBatchNT, 2) batch_align_kernel(BatchArgs a) {
 
                 // ======== solve and update (warp 0 of every CTA, identical inputs)
                 if (warp == 0) {
-                    if (lane < 21) {
-                        int i = 0, rem = lane;
-                        while (rem >= 6 - i) { rem -= 6 - i; ++i; }
-                        const int j = i + rem;
-                        Hs[i * 6 + j] = tot[lane];
-                        Hs[j * 6 + i] = tot[lane];
-                    } else if (lane < 27) {
-                        gs[lane - kSlotG] = tot[lane];
-                    }
-                    __syncwarp();
                     if (lane == 0) {
                         const int nI = (int)tot[kSlotNI], nW = (int)tot[kSlotNW];
                         bool okl = (nI + nW) >= a.min_valid;
                         if constexpr (PREC == RGBID_PLANES_BF16_F16) {
                             double xi[6];
-                            okl = okl && cholesky_solve6_packed_d(Hs, gs, xi);
+                            okl = okl && cholesky_solve6_slots(tot, xi);
 #pragma unroll
                             for (int i = 0; i < 6; ++i) xi_d[i] = okl ? xi[i] : 0.0;
                         } else {
                             float xi[6];
-                            okl = okl && cholesky_solve6_packed(Hs, gs, xi);
+                            okl = okl && cholesky_solve6_slots(tot, xi);
 #pragma unroll
                             for (int i = 0; i < 6; ++i) xi_f[i] = okl ? xi[i] : 0.f;
                         }

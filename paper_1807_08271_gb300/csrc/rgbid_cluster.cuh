@@ -59,6 +59,13 @@ __device__ __forceinline__ void st_async_f2(uint32_t remote_addr, float a, float
 // serialisation may start while its predecessor is still running; it must wait
 // (griddepcontrol.wait) before reading anything the predecessor writes, and it
 // lets its own successor start early with griddepcontrol.launch_dependents.
+// Split cluster barrier: every thread of every CTA arrives and later waits, so the
+// latency between the two is hidden behind other work.  The arrive is relaxed (it
+// orders no memory: mbarrier initialisation is published by its own
+// fence.mbarrier_init, and the barrier at exit carries no data); the wait acquires.
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
@@ -73,6 +80,29 @@ constexpr long long kWaitBudgetCycles = 4000000000LL;   // ~2 s: a wait that exc
 // reduction of the power sums P_k = sum q^k, G_k = sum gamma q^k and sum ln(beta/2)
 // then gives f(nu) at any nu without revisiting the samples; truncating at K
 // terms errs by < q_max^(K+1) per sample (q_max = 0.382 for [2, 10], K = 20).
+// Packed pairs of FP32 (Blackwell's f32x2 arithmetic): element-wise, round to
+// nearest, so each half is exactly the scalar fmaf / + / * of its operands.
+__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi) {
+    return (unsigned long long)__float_as_uint(lo) | ((unsigned long long)__float_as_uint(hi) << 32);
+}
+__device__ __forceinline__ float f2_lo(unsigned long long v) { return __uint_as_float((unsigned)v); }
+__device__ __forceinline__ float f2_hi(unsigned long long v) { return __uint_as_float((unsigned)(v >> 32)); }
+__device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b, unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
 constexpr int kChebK = 20;
 constexpr int kChebVals = 2 * kChebK + 2;      // SL, P_1..P_K, G_0..G_K per channel
 constexpr int kNuSeries = kChebK + 2;          // terms of f(nu) as one series in tau (degree K + 1)
@@ -103,8 +133,8 @@ __device__ __forceinline__ float nu_series_coefficient(const float* T, float n, 
     return F;
 }
 
-// sum_k F_k T_k(tau) by Clenshaw's recurrence (FP32)
-__device__ __forceinline__ float nu_series_eval(const float* F, float tau) {
+// sum_k F_k T_k(tau) by Clenshaw's recurrence (FP32; F held in registers)
+__device__ __forceinline__ float nu_series_eval(const float (&F)[kNuSeries], float tau) {
     const float t2 = 2.f * tau;
     float b1 = 0.f, b2 = 0.f;
 #pragma unroll
@@ -131,9 +161,12 @@ __device__ __forceinline__ float bisect_nu_warp(const float* T, float nc, const 
     const float m = 0.5f * (lo0 + hi0), h = 0.5f * (hi0 - lo0);
     if (lane < kNuSeries) F[lane] = nu_series_coefficient(T, nc, g, m, h, lane);
     __syncwarp();
+    float Fr[kNuSeries];       // every lane's own copy: no shared-memory load on the recurrence
+#pragma unroll
+    for (int k = 0; k < kNuSeries; ++k) Fr[k] = F[k];
     const float invh = 1.f / h;
     // the ends: f(hi) >= 0 -> hi, f(lo) <= 0 -> lo (as the plain bisection decides first)
-    const float fe = nu_series_eval(F, ((lane == 0 ? hi0 : lo0) - m) * invh);
+    const float fe = nu_series_eval(Fr, ((lane == 0 ? hi0 : lo0) - m) * invh);
     const unsigned ends = __ballot_sync(0xffffffffu, lane == 0 ? fe >= 0.f : (lane == 1 && fe <= 0.f));
     if (ends & 1u) return hi0;
     if (ends & 2u) return lo0;
@@ -144,7 +177,7 @@ __device__ __forceinline__ float bisect_nu_warp(const float* T, float nc, const 
         const float step = (hi - lo) / (float)np;
         const int j = lane + 1;                              // interior point j of this lane
         const bool eval = j < np;
-        const float f = eval ? nu_series_eval(F, (fmaf((float)j, step, lo) - m) * invh) : 0.f;
+        const float f = eval ? nu_series_eval(Fr, (fmaf((float)j, step, lo) - m) * invh) : 0.f;
         const unsigned pos = __ballot_sync(0xffffffffu, eval && f > 0.f);   // bit j-1: f at point j > 0
         int jl = 0, jh = np;
         for (int q = 0; q < st; ++q) {

@@ -277,58 +277,8 @@ struct F2 {
     __device__ __forceinline__ float value() const { return hi + lo; }
 };
 
-// Same Jacobi-scaled Cholesky solve for one thread with a small register
-// footprint: H and g are read from (shared) memory, L is kept packed (lower
-// triangle, 21 values) and the pivots as reciprocals, so nothing spills to
-// local memory in a kernel with a tight register budget.
-__device__ __forceinline__ bool cholesky_solve6_packed(const float* H, const float* g, float xi[6]) {
-    float D[6], L[21], iL[6], y[6];
-#define LIDX(i, j) ((i) * ((i) + 1) / 2 + (j))
-#pragma unroll
-    for (int i = 0; i < 6; ++i) {
-        const float hii = H[i * 6 + i];
-        if (!(hii > 0.f)) return false;
-        D[i] = rsqrtf(hii);
-    }
-#pragma unroll
-    for (int j = 0; j < 6; ++j) {
-        float d = H[j * 6 + j] * D[j] * D[j];
-#pragma unroll
-        for (int k = 0; k < j; ++k) d = fmaf(-L[LIDX(j, k)], L[LIDX(j, k)], d);
-        if (!(d > 1e-7f)) return false;
-        const float r = rsqrtf(d);
-        L[LIDX(j, j)] = d * r;
-        iL[j] = r;
-#pragma unroll
-        for (int i = j + 1; i < 6; ++i) {
-            float t = H[i * 6 + j] * D[i] * D[j];
-#pragma unroll
-            for (int k = 0; k < j; ++k) t = fmaf(-L[LIDX(i, k)], L[LIDX(j, k)], t);
-            L[LIDX(i, j)] = t * r;
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < 6; ++i) {
-        float t = -g[i] * D[i];
-#pragma unroll
-        for (int k = 0; k < i; ++k) t = fmaf(-L[LIDX(i, k)], y[k], t);
-        y[i] = t * iL[i];
-    }
-#pragma unroll
-    for (int i = 5; i >= 0; --i) {
-        float t = y[i];
-#pragma unroll
-        for (int k = i + 1; k < 6; ++k) t = fmaf(-L[LIDX(k, i)], xi[k], t);
-        xi[i] = t * iL[i];
-    }
-#pragma unroll
-    for (int i = 0; i < 6; ++i) xi[i] *= D[i];
-#undef LIDX
-    return true;
-}
-
-// FP64 version for the reduced-precision form: reciprocal square roots from an
-// FP32 seed refined by two Newton steps y <- y (3 - x y^2) / 2 in FP64.
+// FP64 reciprocal square root for the reduced-precision form's solve: an FP32
+// seed refined by two Newton steps y <- y (3 - x y^2) / 2 in FP64.
 __device__ __forceinline__ double rsqrt_d(double x) {
     double y = (double)rsqrtf((float)x);
     y = y * (1.5 - 0.5 * x * y * y);
@@ -336,50 +286,91 @@ __device__ __forceinline__ double rsqrt_d(double x) {
     return y;
 }
 
-__device__ __forceinline__ bool cholesky_solve6_packed_d(const float* H, const float* g, double xi[6]) {
-    double D[6], L[21], iL[6], y[6];
-#define LIDX(i, j) ((i) * ((i) + 1) / 2 + (j))
+// Solve of the normal equations H xi = -g ("Iterative optimisation") for one
+// thread: H is Jacobi-scaled to unit diagonal (D = diag(H)^-1/2, solve
+// (D H D) y = -D g, xi = D y) and factorised by Cholesky, in FP32 with pivot
+// tolerance 1e-7 or in FP64 with 1e-12 for the reduced-precision form; a
+// non-positive pivot reports a degenerate step.  H and g are read straight
+// from the reduction slots `s` (H's upper triangle row by row in slots 0..20,
+// g in kSlotG..kSlotG+5).  All 27 values are loaded into registers before the
+// factorisation starts, so no shared-memory latency sits on its dependent
+// chains.
+template <typename Real>
+struct CholTraits;
+template <>
+struct CholTraits<float> {
+    static __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+    static __device__ __forceinline__ float fma3(float a, float b, float c) { return fmaf(a, b, c); }
+    static constexpr float kPivotMin = 1e-7f;
+};
+template <>
+struct CholTraits<double> {
+    static __device__ __forceinline__ double rsq(double x) { return rsqrt_d(x); }
+    static __device__ __forceinline__ double fma3(double a, double b, double c) { return fma(a, b, c); }
+    static constexpr double kPivotMin = 1e-12;
+};
+
+__host__ __device__ constexpr int upper_slot(int i, int j) { return i * (11 - i) / 2 + j; }   // i <= j
+
+// Every loop below has a constant trip count and tests its bounds inside, so
+// full unrolling turns each array index into a constant and the arrays live
+// in registers.
+template <typename Real>
+__device__ __forceinline__ bool cholesky_solve6_slots(const float* s, Real xi[6]) {
+    using C = CholTraits<Real>;
+    float Hp[21], gp[6];
+#pragma unroll
+    for (int k = 0; k < 21; ++k) Hp[k] = s[k];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) gp[i] = s[kSlotG + i];
+    Real D[6], L[6][6], iL[6], y[6];
+    bool ok = true;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-        const double hii = H[i * 6 + i];
-        if (!(hii > 0.0)) return false;
-        D[i] = rsqrt_d(hii);
+        const Real hii = (Real)Hp[upper_slot(i, i)];
+        ok = ok && hii > (Real)0;
+        D[i] = C::rsq(hii);
     }
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
-        double d = (double)H[j * 6 + j] * D[j] * D[j];
+        Real d = (Real)Hp[upper_slot(j, j)] * D[j] * D[j];
 #pragma unroll
-        for (int k = 0; k < j; ++k) d = fma(-L[LIDX(j, k)], L[LIDX(j, k)], d);
-        if (!(d > 1e-12)) return false;
-        const double r = rsqrt_d(d);
-        L[LIDX(j, j)] = d * r;
+        for (int k = 0; k < 6; ++k)
+            if (k < j) d = C::fma3(-L[j][k], L[j][k], d);
+        ok = ok && d > C::kPivotMin;
+        const Real r = C::rsq(d);
+        L[j][j] = d * r;
         iL[j] = r;
 #pragma unroll
-        for (int i = j + 1; i < 6; ++i) {
-            double t = (double)H[i * 6 + j] * D[i] * D[j];
+        for (int i = 0; i < 6; ++i) {
+            if (i > j) {
+                Real t = (Real)Hp[upper_slot(j, i)] * D[i] * D[j];
 #pragma unroll
-            for (int k = 0; k < j; ++k) t = fma(-L[LIDX(i, k)], L[LIDX(j, k)], t);
-            L[LIDX(i, j)] = t * r;
+                for (int k = 0; k < 6; ++k)
+                    if (k < j) t = C::fma3(-L[i][k], L[j][k], t);
+                L[i][j] = t * r;
+            }
         }
     }
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-        double t = -(double)g[i] * D[i];
+        Real t = -(Real)gp[i] * D[i];
 #pragma unroll
-        for (int k = 0; k < i; ++k) t = fma(-L[LIDX(i, k)], y[k], t);
+        for (int k = 0; k < 6; ++k)
+            if (k < i) t = C::fma3(-L[i][k], y[k], t);
         y[i] = t * iL[i];
     }
 #pragma unroll
     for (int i = 5; i >= 0; --i) {
-        double t = y[i];
+        Real t = y[i];
 #pragma unroll
-        for (int k = i + 1; k < 6; ++k) t = fma(-L[LIDX(k, i)], xi[k], t);
+        for (int k = 0; k < 6; ++k)
+            if (k > i) t = C::fma3(-L[k][i], xi[k], t);
         xi[i] = t * iL[i];
     }
 #pragma unroll
     for (int i = 0; i < 6; ++i) xi[i] *= D[i];
-#undef LIDX
-    return true;
+    return ok;
 }
 
 // ---------------------------------------------------------------- warp-parallel pose arithmetic (double)
@@ -388,18 +379,22 @@ __device__ __forceinline__ bool cholesky_solve6_packed_d(const float* H, const f
 // chain of <= 4 FP64 operations per lane).
 
 // out = warp pose of T (all 32 lanes call; T and out may be in shared or global memory).
+// Every lane < 16 evaluates one field as a0 b0 + a1 b1 + a2 b2 + c with operands
+// chosen by its index, so the warp issues the same three FP64 FMAs and one
+// conversion whatever the field (divergent branches would each issue their own):
+//   E_l (l < 9, i = l/3, j = l%3) = T_ji - delta_ij,   s_i (l = 9 + i) = sum_k T_ki T_k3,
+//   R2_k (l = 12 + k) = T_2k,   tz (l = 15) = T_23.
 __device__ __forceinline__ void warp_make_pose(const double* T, WarpPose* out) {
     const int lane = threadIdx.x & 31;
-    if (lane < 9) {
-        const int i = lane / 3, j = lane % 3;
-        out->E[lane] = (float)(T[j * 4 + i] - (i == j ? 1.0 : 0.0));
-    } else if (lane < 12) {
-        const int i = lane - 9;
-        out->s[i] = (float)(T[0 * 4 + i] * T[3] + T[1 * 4 + i] * T[7] + T[2 * 4 + i] * T[11]);
-    } else if (lane < 15) {
-        out->R2[lane - 12] = (float)T[8 + lane - 12];
-    } else if (lane == 15) {
-        out->tz = (float)T[11];
+    if (lane < 16) {
+        const bool e = lane < 9, sl = lane >= 9 && lane < 12;
+        const int i = e ? lane / 3 : lane - 9, j = lane % 3;
+        const int i0 = e ? j * 4 + i : (sl ? i : (lane < 15 ? 8 + (lane - 12) : 11));
+        const double a0 = T[i0], b0 = sl ? T[3] : 1.0;
+        const double a1 = sl ? T[4 + i] : 0.0, b1 = sl ? T[7] : 0.0;
+        const double a2 = sl ? T[8 + i] : 0.0, b2 = sl ? T[11] : 0.0;
+        const double c = (e && i == j) ? -1.0 : 0.0;
+        reinterpret_cast<float*>(out)[lane] = (float)fma(a0, b0, fma(a1, b1, fma(a2, b2, c)));
     }
 }
 
