@@ -126,6 +126,21 @@ __global__ void init_kernel(InitArgs a) {
 // of the cluster with compensated (TwoSum) pairs), so every thread of every
 // CTA sees bit-identical totals and takes identical branches.
 
+// Sum of the NW per-warp partials of value t in a fixed pairwise tree (depth
+// log2 NW instead of a chain of NW compensated adds); the same order everywhere.
+template <int NW, typename Row>
+__device__ __forceinline__ F2 warp_tree(const Row* rows, int t) {
+    F2 a[NW];
+#pragma unroll
+    for (int w = 0; w < NW; ++w) a[w] = as_f2(rows[w][t]);
+#pragma unroll
+    for (int step = 1; step < NW; step <<= 1)
+#pragma unroll
+        for (int w = 0; w < NW; ++w)
+            if (w % (2 * step) == 0 && w + step < NW) a[w].add(a[w + step]);
+    return a[0];
+}
+
 template <int CL>
 struct ClusterSum {
     float (*red_w)[kRobustMaxNV];             // per-warp partials [8][NV]
@@ -137,24 +152,27 @@ struct ClusterSum {
     int round;
     long long budget = kWaitBudgetCycles;     // clock64 cycles a wait may take before it gives up
 
-    // v: per-thread partials of NV values (NV <= 8: one warp sum each; NV = 96: three
-    // reduce-scatter chunks).  On return out[0..NV) holds the cluster totals,
-    // bit-identical in every CTA (same data, same combine order).
-    // Threads t < NV of every CTA call this with the CTA's compensated partial of
-    // value t; each returns the cluster total (same pairwise tree over the ranks
-    // in every CTA).  The caller separates rounds with __syncthreads and next().
-    // (`send` = false withholds this CTA's partials: used only by the wait-timeout probe.)
+    // One all-to-all round in three parts.  arm<NV>(): thread 0 announces the round's
+    // bytes (CL sources x NV values) on this CTA's barrier.  send(t, r, s): the calling
+    // thread pushes this CTA's compensated partial of value t into CTA r (st.async
+    // completes the bytes on r's barrier).  receive<NV>(t): threads t < NV wait for
+    // value t from every CTA and return the total, summed over the ranks in the same
+    // pairwise tree in every CTA, so every CTA holds bit-identical totals.  Spreading
+    // the CL x NV sends over the threads keeps the issue of the round's stores short.
+    // The caller separates rounds with __syncthreads and next().
     template <int NV>
-    __device__ __forceinline__ F2 exchange(int t, F2 s, bool send = true) {
+    __device__ __forceinline__ void arm() {
+        if (threadIdx.x == 0) mbar_arrive_expect_tx(&mbar[round & 1], (uint32_t)(CL * NV * sizeof(float2)));
+    }
+    __device__ __forceinline__ void send(int t, int r, F2 s) {
+        const int par = round & 1;
+        st_async_f2(map_to_rank(smem_addr(&recv[par][rank][t]), (uint32_t)r), s.hi, s.lo,
+                    map_to_rank(smem_addr(&mbar[par]), (uint32_t)r));
+    }
+    template <int NV>
+    __device__ __forceinline__ F2 receive(int t) {
         const int par = round & 1;
         const uint32_t phase = (uint32_t)(round >> 1) & 1u;
-        if (t == 0) mbar_arrive_expect_tx(&mbar[par], (uint32_t)(CL * NV * sizeof(float2)));
-        const uint32_t src = smem_addr(&recv[par][rank][t]);
-        const uint32_t bar = smem_addr(&mbar[par]);
-        if (send) {
-#pragma unroll
-            for (int r = 0; r < CL; ++r) st_async_f2(map_to_rank(src, r), s.hi, s.lo, map_to_rank(bar, r));
-        }
         const long long t0 = clock64();
         while (!mbar_try_wait(&mbar[par], phase)) {
             if (clock64() - t0 > budget) {
@@ -176,6 +194,25 @@ struct ClusterSum {
                 if (r % (2 * step) == 0 && r + step < CL) acc[r].add(acc[r + step]);
         return acc[0];
     }
+    // All CL x NV sends of a round, value t's partial given by part(t).
+    template <int NV, typename Part>
+    __device__ __forceinline__ void send_all(Part part) {
+        for (int p = (int)threadIdx.x; p < NV * CL; p += kRobustNT) {
+            const int t = p / CL, r = p - t * CL;
+            send(t, r, part(t));
+        }
+    }
+    // A round by one thread per value t < NV, which sends to every CTA itself
+    // (`do_send` = false withholds this CTA's partials: the wait-timeout probe).
+    template <int NV>
+    __device__ __forceinline__ F2 exchange(int t, F2 s, bool do_send = true) {
+        if (t == 0) mbar_arrive_expect_tx(&mbar[round & 1], (uint32_t)(CL * NV * sizeof(float2)));
+        if (do_send) {
+#pragma unroll
+            for (int r = 0; r < CL; ++r) send(t, r, s);
+        }
+        return receive<NV>(t);
+    }
     __device__ __forceinline__ void next() { ++round; }
 
     // The same round towards CTA 0 alone: every CTA pushes its partial of value t
@@ -183,36 +220,17 @@ struct ClusterSum {
     // the other CTAs return at once.  For sums only CTA 0 consumes.
     template <int NV>
     __device__ __forceinline__ F2 gather(int t, F2 s) {
-        const int par = round & 1;
-        const uint32_t phase = (uint32_t)(round >> 1) & 1u;
-        if (rank == 0 && t == 0) mbar_arrive_expect_tx(&mbar[par], (uint32_t)(CL * NV * sizeof(float2)));
-        st_async_f2(map_to_rank(smem_addr(&recv[par][rank][t]), 0), s.hi, s.lo, map_to_rank(smem_addr(&mbar[par]), 0));
+        if (rank == 0 && t == 0) mbar_arrive_expect_tx(&mbar[round & 1], (uint32_t)(CL * NV * sizeof(float2)));
+        send(t, 0, s);
         if (rank != 0) return F2{0.f, 0.f};
-        const long long t0 = clock64();
-        while (!mbar_try_wait(&mbar[par], phase)) {
-            if (clock64() - t0 > budget) {
-                atomicAdd(timeouts, 1);
-                break;
-            }
-        }
-        F2 acc[CL];
-#pragma unroll
-        for (int r = 0; r < CL; ++r) {
-            const float2 p = recv[par][r][t];
-            acc[r] = F2{p.x, p.y};
-        }
-#pragma unroll
-        for (int step = 1; step < CL; step <<= 1)
-#pragma unroll
-            for (int r = 0; r < CL; ++r)
-                if (r % (2 * step) == 0 && r + step < CL) acc[r].add(acc[r + step]);
-        return acc[0];
+        return receive<NV>(t);
     }
 
     // Block reduction of per-thread partials v[0..NV) (NV <= 8: one warp sum each;
-    // a multiple of 32: reduce-scatter chunks); then values t < NSEND go through the
-    // cluster: to every CTA (ROOT = false; out[] bit-identical in all CTAs) or to
-    // CTA 0 alone (ROOT = true; out[] valid in CTA 0 only).
+    // a multiple of 32: reduce-scatter chunks) into per-warp partials, summed over the
+    // warps in a fixed pairwise tree; then values t < NSEND go through the cluster: to
+    // every CTA (ROOT = false; out[] bit-identical in all CTAs) or to CTA 0 alone
+    // (ROOT = true; out[] valid in CTA 0 only).
     template <int NV, int NSEND = NV, bool ROOT = false>
     __device__ __forceinline__ void run(float (&v)[NV]) {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -233,13 +251,14 @@ struct ClusterSum {
             }
         }
         __syncthreads();
+        const auto part = [&](int t) { return warp_tree<kRobustNT / 32>(red_w, t); };
         const int t = threadIdx.x;
-        if (t < NSEND) {
-            F2 s{0.f, 0.f};
-#pragma unroll
-            for (int w = 0; w < kRobustNT / 32; ++w) s.add(red_w[w][t]);
-            if constexpr (ROOT) out[t] = gather<NSEND>(t, s).value();
-            else out[t] = exchange<NSEND>(t, s).value();
+        if constexpr (ROOT) {
+            if (t < NSEND) out[t] = gather<NSEND>(t, part(t)).value();
+        } else {
+            arm<NSEND>();
+            send_all<NSEND>(part);
+            if (t < NSEND) out[t] = receive<NSEND>(t).value();
         }
         __syncthreads();
         next();
@@ -345,10 +364,8 @@ __global__ void __launch_bounds__(kRobustNT) robust_kernel(RobustArgs a) {
         fin2[grp][lane] = acc;
         __syncthreads();
         if (t < kSlots) {
-            F2 c{0.f, 0.f};
-#pragma unroll
-            for (int w = 0; w < kRobustNT / 32; ++w) c.add(fin2[w][t]);
-            const F2 T2 = R.template exchange<kSlots>(t, c);
+            // one sender per slot: with 32 slots, spreading the sends would cost a block barrier
+            const F2 T2 = R.template exchange<kSlots>(t, warp_tree<kRobustNT / 32>(fin2, t));
             tot[t] = T2.value();
             if (a.finalize_only) totd[t] = (double)T2.hi + (double)T2.lo;   // for the result record
         }
@@ -486,8 +503,12 @@ __global__ void __launch_bounds__(kRobustNT) robust_kernel(RobustArgs a) {
         for (int k = 0; k < MAXS; ++k) {
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
+                // masked samples (NaN) add exact zeros: selects, not branches
                 const float r = rs[c][k];
-                if (r == r) { v4[2 * c] += 1.f; v4[2 * c + 1] = fmaf(r, r, v4[2 * c + 1]); }
+                const bool use = r == r;
+                const float rv = use ? r : 0.f;
+                v4[2 * c] += use ? 1.f : 0.f;
+                v4[2 * c + 1] = fmaf(rv, rv, v4[2 * c + 1]);
             }
         }
         R.run(v4);
@@ -519,13 +540,13 @@ __global__ void __launch_bounds__(kRobustNT) robust_kernel(RobustArgs a) {
 #pragma unroll
             for (int k = 0; k < MAXS; ++k) {
                 const float r = rs[c][k];
-                if (r == r) {
-                    const float d = r - m;
-                    const float w = __fdividef(num, fmaf(d, d, s2nu));   // omega((r - mu)/sigma, nu0)
-                    v6[3 * c] += w;
-                    v6[3 * c + 1] = fmaf(w, d, v6[3 * c + 1]);
-                    v6[3 * c + 2] = fmaf(w * d, d, v6[3 * c + 2]);
-                }
+                const bool use = r == r;                  // masked samples add exact zeros
+                const float dr = r - m;
+                const float wr = __fdividef(num, fmaf(dr, dr, s2nu));   // omega((r - mu)/sigma, nu0)
+                const float w = use ? wr : 0.f, d = use ? dr : 0.f;
+                v6[3 * c] += w;
+                v6[3 * c + 1] = fmaf(w, d, v6[3 * c + 1]);
+                v6[3 * c + 2] = fmaf(w * d, d, v6[3 * c + 2]);
             }
         }
         R.run(v6);
@@ -898,8 +919,7 @@ static RobustArgs robust_args(const rgbid_pyramid* ref, const rgbid_pyramid* cur
     ra.nu0 = (float)p->nu0;
     ra.nu_lo = p->nu_lo;
     ra.nu_hi = p->nu_hi;
-    const float* g = nu_g_series_cached(p->nu_lo, p->nu_hi);
-    for (int k = 0; k < kNuGTerms; ++k) ra.nu_g[k] = g[k];
+    nu_device_series(p->nu_lo, p->nu_hi, ra.nu_g);
     ra.level_iters = nullptr;
     ra.level = l;
     ra.iter = 0;

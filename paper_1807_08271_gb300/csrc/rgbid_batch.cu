@@ -139,8 +139,7 @@ extern "C" int rgbid_align_batched(const rgbid_batch_item* d_items, int n_items,
     a.nu0 = (float)params->nu0;
     a.nu_lo = (float)params->nu_lo;
     a.nu_hi = (float)params->nu_hi;
-    const float* g = nu_g_series_cached(params->nu_lo, params->nu_hi);
-    for (int k = 0; k < kNuGTerms; ++k) a.nu_g[k] = g[k];
+    nu_device_series(params->nu_lo, params->nu_hi, a.nu_g);
 
     cudaStream_t stream = (cudaStream_t)stream_;
     rgbid_timing* tm = params->timing;

@@ -108,8 +108,8 @@ constexpr int kChebVals = 2 * kChebK + 2;      // SL, P_1..P_K, G_0..G_K per cha
 constexpr int kNuSeries = kChebK + 2;          // terms of f(nu) as one series in tau (degree K + 1)
 static_assert(kNuSeries == kNuGTerms, "the constant part's series has as many terms as f's");
 
-// f(nu) = n g(nu) - n ln h - SL - A(tau) - (nu + 1) B(tau) / h, with
-//   g(nu) = psi((nu+1)/2) - psi(nu/2) + 1 + ln nu = sum_k g_k T_k(tau)   (host series),
+// f(nu) = n (g(nu) - ln h) - SL - A(tau) - (nu + 1) B(tau) / h, with
+//   g(nu) - ln h = sum_k g_k T_k(tau)   (host series, g = psi((nu+1)/2) - psi(nu/2) + 1 + ln nu),
 //   A(tau) = sum_i ln(alpha_i + tau) - SL = sum_{k>=1} a_k T_k,   a_k = 2 (-1)^(k+1) P_k / k,
 //   B(tau) = sum_i 1/(alpha_i + tau)      = sum_{k>=0} b_k T_k,   b_0 = G_0, b_k = 2 (-1)^k G_k,
 // and (nu + 1) B / h = ((m + 1)/h) B + tau B, tau T_0 = T_1, tau T_k = (T_{k+1} + T_{k-1})/2.
@@ -129,7 +129,7 @@ __device__ __forceinline__ float nu_series_coefficient(const float* T, float n, 
     if (j >= 2) d += 0.5f * b(j - 1);
     if (j + 1 <= kChebK) d += 0.5f * b(j + 1);
     float F = fmaf(n, g[j], -a) - __fdividef(m + 1.f, h) * b(j) - d;
-    if (j == 0) F -= fmaf(n, logf(h), T[0]);
+    if (j == 0) F -= T[0];
     return F;
 }
 
@@ -174,15 +174,18 @@ __device__ __forceinline__ float bisect_nu_warp(const float* T, float nc, const 
     for (int left = steps; left > 0;) {
         const int st = left < 5 ? left : 5;
         const int np = 1 << st;                              // sub-intervals this round
-        const float step = (hi - lo) / (float)np;
+        const float step = (hi - lo) * __int_as_float((127 - st) << 23);   // exact: times 2^-st
         const int j = lane + 1;                              // interior point j of this lane
         const bool eval = j < np;
         const float f = eval ? nu_series_eval(Fr, (fmaf((float)j, step, lo) - m) * invh) : 0.f;
         const unsigned pos = __ballot_sync(0xffffffffu, eval && f > 0.f);   // bit j-1: f at point j > 0
         int jl = 0, jh = np;
-        for (int q = 0; q < st; ++q) {
-            const int jm = (jl + jh) >> 1;
-            if ((pos >> (jm - 1)) & 1u) jl = jm; else jh = jm;
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            if (q < st) {
+                const int jm = (jl + jh) >> 1;
+                if ((pos >> (jm - 1)) & 1u) jl = jm; else jh = jm;
+            }
         }
         const float nlo = fmaf((float)jl, step, lo), nhi = fmaf((float)jh, step, lo);
         lo = nlo;

@@ -276,6 +276,8 @@ struct F2 {
     }
     __device__ __forceinline__ float value() const { return hi + lo; }
 };
+__device__ __forceinline__ F2 as_f2(float x) { return F2{x, 0.f}; }
+__device__ __forceinline__ F2 as_f2(const F2& x) { return x; }
 
 // FP64 reciprocal square root for the reduced-precision form's solve: an FP32
 // seed refined by two Newton steps y <- y (3 - x y^2) / 2 in FP64.

@@ -66,4 +66,13 @@ static inline const float* nu_g_series_cached(double lo, double hi) {
     return c_g;
 }
 
+// The series the kernels take: g's, with ln h (h the interval's half-width as the
+// kernels form it in FP32) folded into the constant term, since f carries -n ln h.
+static inline void nu_device_series(double lo, double hi, float out[kNuGTerms]) {
+    const float* g = nu_g_series_cached(lo, hi);
+    const float h = 0.5f * ((float)hi - (float)lo);
+    for (int k = 0; k < kNuGTerms; ++k) out[k] = g[k];
+    out[0] = (float)((double)g[0] - std::log((double)h));
+}
+
 }  // namespace rgbid
