@@ -126,21 +126,6 @@ __global__ void init_kernel(InitArgs a) {
 // of the cluster with compensated (TwoSum) pairs), so every thread of every
 // CTA sees bit-identical totals and takes identical branches.
 
-// Sum of the NW per-warp partials of value t in a fixed pairwise tree (depth
-// log2 NW instead of a chain of NW compensated adds); the same order everywhere.
-template <int NW, typename Row>
-__device__ __forceinline__ F2 warp_tree(const Row* rows, int t) {
-    F2 a[NW];
-#pragma unroll
-    for (int w = 0; w < NW; ++w) a[w] = as_f2(rows[w][t]);
-#pragma unroll
-    for (int step = 1; step < NW; step <<= 1)
-#pragma unroll
-        for (int w = 0; w < NW; ++w)
-            if (w % (2 * step) == 0 && w + step < NW) a[w].add(a[w + step]);
-    return a[0];
-}
-
 template <int CL>
 struct ClusterSum {
     float (*red_w)[kRobustMaxNV];             // per-warp partials [8][NV]

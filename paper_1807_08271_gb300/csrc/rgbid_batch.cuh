@@ -126,18 +126,32 @@ struct BatchXchg {
     uint32_t rank;
     int round;
 
-    // Called by threads t < NV with the CTA's partial of value t; returns the
-    // cluster total of value t, summed in rank order by the same pairwise tree
-    // in every CTA.  The caller ends the round with __syncthreads and next().
+    // A round in three parts, as in the per-iteration kernel: thread 0 arms this
+    // CTA's barrier for CL x NV values; send(t, r, s) pushes this CTA's partial of
+    // value t into CTA r; threads t < NV receive the total of value t, summed in
+    // rank order by the same pairwise tree in every CTA.  The caller ends the round
+    // with __syncthreads and next().
+    template <int NV>
+    __device__ __forceinline__ void arm() {
+        if (threadIdx.x == 0) mbar_arrive_expect_tx(&mbar[round & 1], (uint32_t)(CL * NV * sizeof(float2)));
+    }
+    __device__ __forceinline__ void send(int t, int r, F2 s) {
+        const int par = round & 1;
+        st_async_f2(map_to_rank(smem_addr(&recv[par][rank][t]), (uint32_t)r), s.hi, s.lo,
+                    map_to_rank(smem_addr(&mbar[par]), (uint32_t)r));
+    }
+    // One thread per value t < NV sends it to every CTA itself and receives.
     template <int NV>
     __device__ __forceinline__ F2 exchange(int t, F2 s) {
+        if (t == 0) mbar_arrive_expect_tx(&mbar[round & 1], (uint32_t)(CL * NV * sizeof(float2)));
+#pragma unroll
+        for (int r = 0; r < CL; ++r) send(t, r, s);
+        return receive<NV>(t);
+    }
+    template <int NV>
+    __device__ __forceinline__ F2 receive(int t) {
         const int par = round & 1;
         const uint32_t phase = (uint32_t)(round >> 1) & 1u;
-        if (t == 0) mbar_arrive_expect_tx(&mbar[par], (uint32_t)(CL * NV * sizeof(float2)));
-        const uint32_t src = smem_addr(&recv[par][rank][t]);
-        const uint32_t bar = smem_addr(&mbar[par]);
-#pragma unroll
-        for (int r = 0; r < CL; ++r) st_async_f2(map_to_rank(src, (uint32_t)r), s.hi, s.lo, map_to_rank(bar, (uint32_t)r));
         const long long budget = *failed ? 0 : kWaitBudgetCycles;
         const long long t0 = clock64();
         while (!mbar_try_wait(&mbar[par], phase)) {
@@ -163,7 +177,8 @@ struct BatchXchg {
 };
 
 // A round of NV <= 8 cluster sums of per-thread values (warp sums, then a
-// compensated sum over the warps, then the exchange); totals land in tot[0, NV).
+// compensated pairwise tree over the warps, then the exchange with its CL x NV
+// stores spread over the threads); totals land in tot[0, NV).
 template <int CL, int NV>
 __device__ __forceinline__ void batch_round_small(BatchXchg<CL>& X, float (&v)[NV], float (*red_w)[64], float* tot) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -173,12 +188,12 @@ __device__ __forceinline__ void batch_round_small(BatchXchg<CL>& X, float (&v)[N
         if (lane == 0) red_w[warp][j] = x;
     }
     __syncthreads();
-    if ((int)threadIdx.x < NV) {
-        F2 s{0.f, 0.f};
-#pragma unroll
-        for (int w = 0; w < kBatchNT / 32; ++w) s.add(red_w[w][threadIdx.x]);
-        tot[threadIdx.x] = X.template exchange<NV>((int)threadIdx.x, s).value();
+    X.template arm<NV>();
+    for (int p = (int)threadIdx.x; p < NV * CL; p += kBatchNT) {
+        const int t = p / CL, r = p - t * CL;
+        X.send(t, r, warp_tree<kBatchNT / 32>(red_w, t));
     }
+    if ((int)threadIdx.x < NV) tot[threadIdx.x] = X.template receive<NV>((int)threadIdx.x).value();
     __syncthreads();
     X.next();
 }
@@ -410,9 +425,14 @@ __global__ void __launch_bounds__(kBatchNT, 2) batch_align_kernel(BatchArgs a) {
                     float v4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll 2
                     for (int k = 0; k < MAXS; ++k) {
+                        // masked samples (NaN) add exact zeros: selects, not branches
                         const float r0 = rsI[k * NT + tid], r1 = rsW[k * NT + tid];
-                        if (r0 == r0) { v4[0] += 1.f; v4[1] = fmaf(r0, r0, v4[1]); }
-                        if (r1 == r1) { v4[2] += 1.f; v4[3] = fmaf(r1, r1, v4[3]); }
+                        const bool u0 = r0 == r0, u1 = r1 == r1;
+                        const float a0 = u0 ? r0 : 0.f, a1 = u1 ? r1 : 0.f;
+                        v4[0] += u0 ? 1.f : 0.f;
+                        v4[1] = fmaf(a0, a0, v4[1]);
+                        v4[2] += u1 ? 1.f : 0.f;
+                        v4[3] = fmaf(a1, a1, v4[3]);
                     }
                     batch_round_small<CL, 4>(X, v4, red_w, tot);
                 }
@@ -439,13 +459,13 @@ __global__ void __launch_bounds__(kBatchNT, 2) batch_align_kernel(BatchArgs a) {
 #pragma unroll 2
                         for (int k = 0; k < MAXS; ++k) {
                             const float r = rc[k * NT + tid];
-                            if (r == r) {
-                                const float d = r - m;
-                                const float w = __fdividef(num, fmaf(d, d, s2nu));
-                                v6[3 * c] += w;
-                                v6[3 * c + 1] = fmaf(w, d, v6[3 * c + 1]);
-                                v6[3 * c + 2] = fmaf(w * d, d, v6[3 * c + 2]);
-                            }
+                            const bool use = r == r;
+                            const float dr = r - m;
+                            const float wr = __fdividef(num, fmaf(dr, dr, s2nu));
+                            const float w = use ? wr : 0.f, d = use ? dr : 0.f;
+                            v6[3 * c] += w;
+                            v6[3 * c + 1] = fmaf(w, d, v6[3 * c + 1]);
+                            v6[3 * c + 2] = fmaf(w * d, d, v6[3 * c + 2]);
                         }
                     }
                     batch_round_small<CL, 6>(X, v6, red_w, tot);
@@ -488,7 +508,7 @@ __global__ void __launch_bounds__(kBatchNT, 2) batch_align_kernel(BatchArgs a) {
                                     const float gam = rsqrtf(s2);
                                     const float be = fmaf(s2, gam, al);
                                     const float q = __fdividef(1.f, be);
-                                    v[0] += logf(0.5f * be);
+                                    v[0] += __logf(0.5f * be);
                                     v[1 + kChebK] += gam;
                                     float qk = q;
 #pragma unroll

@@ -195,6 +195,21 @@ __device__ __forceinline__ float bisect_nu_warp(const float* T, float nc, const 
     return 0.5f * (lo + hi);
 }
 
+// Sum of the NW per-warp partials of value t in a fixed pairwise tree (depth
+// log2 NW instead of a chain of NW compensated adds); the same order everywhere.
+template <int NW, typename Row>
+__device__ __forceinline__ F2 warp_tree(const Row* rows, int t) {
+    F2 a[NW];
+#pragma unroll
+    for (int w = 0; w < NW; ++w) a[w] = as_f2(rows[w][t]);
+#pragma unroll
+    for (int step = 1; step < NW; step <<= 1)
+#pragma unroll
+        for (int w = 0; w < NW; ++w)
+            if (w % (2 * step) == 0 && w + step < NW) a[w].add(a[w + step]);
+    return a[0];
+}
+
 __device__ __forceinline__ void accumulate(float (&acc)[kSlots], const float (&J)[6], float w, float r) {
     float wj[6];
 #pragma unroll
