@@ -10,9 +10,10 @@
 //                  optimisation"); CTA 0 writes the new state and the step's
 //                  results.  It then warps the <= 19200 systematic sample pixels
 //                  with the new pose and estimates the Student-t (mu, sigma) at
-//                  nu0 by the lagged-weight fixed point and nu by bisection on the
-//                  robustness equation, every reduction exchanged across the
-//                  cluster ("Error distribution and robust optimisation").
+//                  nu0 by the lagged-weight fixed point (every round exchanged
+//                  across the cluster), then gathers the sums of the robustness
+//                  equation to CTA 0, which finds nu by bisection ("Error
+//                  distribution and robust optimisation").
 //   sweep_kernel   the whole level: warp, residuals, Jacobians, weights and the
 //                  per-block compensated partials of the 27 normal-equation terms
 //                  (plus cost and counts).
