@@ -20,6 +20,7 @@
 // A closing robust_kernel launch (finalize_only) finishes the last sweep of an
 // alignment.
 #include <cooperative_groups.h>
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 
@@ -34,9 +35,11 @@ namespace rgbid {
 constexpr int kRobustNT = 256;      // threads per CTA of the robust-scale cluster
 constexpr int kRobustMaxNV = 96;    // widest cluster reduction (the Chebyshev sums of both channels)
 constexpr int kSweepNT = 256;       // 8 warps
-constexpr int kSweepRowsPerWarp = 4;
 constexpr int kTileW = 32;
-constexpr int kTileH = 8 * kSweepRowsPerWarp;
+// Rows per thread of the sweep: 4 on a level of at least kSweepWidePixels (its blocks
+// still fill the GPU in one wave), else 1, so a coarse level's blocks are four times
+// as many and each thread's serial work a quarter as long.
+constexpr long long kSweepWidePixels = 250000;
 
 struct InitArgs {
     AlignState* st;
@@ -642,8 +645,9 @@ __global__ void __launch_bounds__(kRobustNT) robust_kernel(RobustArgs a) {
 }
 
 // ---------------------------------------------------------------- sweep + solve
-template <int PREC>
+template <int PREC, int R>
 __global__ void __launch_bounds__(kSweepNT, 2) sweep_kernel(SweepArgs a) {
+    constexpr int kTileH = 8 * R;
     __shared__ float red[kSweepNT / 32][kSlots];
     __shared__ WarpPose sh_wp;
     __shared__ RobustParams sh_rob;
@@ -656,7 +660,6 @@ __global__ void __launch_bounds__(kSweepNT, 2) sweep_kernel(SweepArgs a) {
     const int u = blockIdx.x * kTileW + lane;
     // the thread's rows go through each stage together, so the loads of a stage
     // for all rows are in flight at once
-    constexpr int R = kSweepRowsPerWarp;
     const int v0 = blockIdx.y * kTileH + warp * R;
     PxA sa[R];
 #pragma unroll
@@ -779,10 +782,18 @@ static int sample_stride(int w, int h, int cap) {
     return s;
 }
 
-static int sweep_blocks(int w, int h) { return ((w + kTileW - 1) / kTileW) * ((h + kTileH - 1) / kTileH); }
+static int sweep_rows(int w, int h) { return (long long)w * h >= kSweepWidePixels ? 4 : 1; }
+static int sweep_blocks(int w, int h) {
+    const int th = 8 * sweep_rows(w, h);
+    return ((w + kTileW - 1) / kTileW) * ((h + th - 1) / th);
+}
 
-static size_t workspace_bytes_for(int w0, int h0) {
-    return align_up(sizeof(AlignState), 256) + align_up((size_t)sweep_blocks(w0, h0) * kSlots * sizeof(float2), 256);
+// The block partials of the largest sweep over the levels of `ref`.
+static size_t workspace_bytes_for(const rgbid_pyramid& ref) {
+    int nb = 1;
+    for (int l = 0; l < ref.levels && l < RGBID_MAX_LEVELS; ++l)
+        nb = std::max(nb, sweep_blocks(ref.lv[l].width, ref.lv[l].height));
+    return align_up(sizeof(AlignState), 256) + align_up((size_t)nb * kSlots * sizeof(float2), 256);
 }
 
 static int check_pyramids(const rgbid_pyramid* ref, const rgbid_pyramid* cur, const rgbid_align_params* p) {
@@ -870,8 +881,9 @@ static cudaError_t launch_robust(const RobustArgs& ra, cudaStream_t stream) {
 
 template <int PREC>
 static cudaError_t launch_sweep(const SweepArgs& sa, cudaStream_t stream) {
+    const int R = sweep_rows(sa.A.w, sa.A.h);
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((sa.A.w + kTileW - 1) / kTileW, (sa.A.h + kTileH - 1) / kTileH, 1);
+    cfg.gridDim = dim3((sa.A.w + kTileW - 1) / kTileW, (sa.A.h + 8 * R - 1) / (8 * R), 1);
     cfg.blockDim = dim3(kSweepNT, 1, 1);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = stream;
@@ -880,7 +892,7 @@ static cudaError_t launch_sweep(const SweepArgs& sa, cudaStream_t stream) {
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, sweep_kernel<PREC>, sa);
+    return R == 4 ? cudaLaunchKernelEx(&cfg, sweep_kernel<PREC, 4>, sa) : cudaLaunchKernelEx(&cfg, sweep_kernel<PREC, 1>, sa);
 }
 
 static cudaError_t launch_robust_any(int prec, const RobustArgs& ra, cudaStream_t s) {
@@ -923,8 +935,8 @@ using namespace rgbid;
 
 extern "C" size_t rgbid_align_workspace_bytes(const rgbid_pyramid* ref, const rgbid_align_params* params) {
     (void)params;
-    if (!ref || ref->levels < 1) return 0;
-    return workspace_bytes_for(ref->lv[0].width, ref->lv[0].height);
+    if (!ref || ref->levels < 1 || ref->levels > RGBID_MAX_LEVELS) return 0;
+    return workspace_bytes_for(*ref);
 }
 
 extern "C" int rgbid_align(const rgbid_pyramid* ref, const rgbid_pyramid* cur, const double* T_init, int T_init_on_device,
