@@ -15,11 +15,12 @@ Each frame's result (pose relative to its keyframe, robust parameters, ...) is
 copied to a device array so that the host reads them once at the end.
 
 With ``graphs=True`` (the default) steps 1-5 of a frame are one CUDA graph
-replay: a fusing frame and a keyframe-switching frame each have a graph,
-captured after the first eager frame of its kind, which reads the frame from a
-fixed staging pair; per frame the host then copies the frame into staging,
-replays the graph and copies the frame's result into the result array, instead
-of enqueueing some fifty launches.  The per-launch timing hook of the
+replay: each frame kind (fusing, keyframe-switching) and staging slot has a
+graph, captured after the first eager frame of its kind, which reads the frame
+from that slot's fixed staging pair; per frame the host then copies the frame
+into staging (or finds it there), replays the graph and copies the frame's
+result into the result array, instead of enqueueing some fifty launches.  Two
+slots let a caller upload frame k+1 (``staging(slot)``) while frame k runs.  The per-launch timing hook of the
 alignment (``params.timing``) needs the eager path, which step() takes while
 it is attached.
 """
@@ -60,9 +61,11 @@ class Tracker:
         self.k = 0
         self.is_kf = np.zeros(max_frames, dtype=bool)
         self.graphs = graphs
-        self._graph = {}          # frame kind (True: keyframe switch) -> CUDA graph of steps 1-5
-        self.I_in = torch.zeros((height, width), **f32) if graphs else None   # staging for the graphs
-        self.W_in = torch.zeros((height, width), **f32) if graphs else None
+        self._graph = {}          # (frame kind (True: keyframe switch), staging slot) -> CUDA graph of steps 1-5
+        # two staging pairs for the graphs (slot 0 also takes frames passed from elsewhere)
+        self._stage = [(torch.zeros((height, width), **f32), torch.zeros((height, width), **f32))
+                       for _ in range(2)] if graphs else []
+        self.I_in, self.W_in = self._stage[0] if graphs else (None, None)
 
     def _T_view(self):
         return self.res[0, 0:128].view(self.torch.float64)
@@ -70,6 +73,11 @@ class Tracker:
     def _sigmaW_view(self):
         off = 8 * (16 + 36 + 6 + 2 + 1)
         return self.res[0, off:off + 8].view(self.torch.float64)
+
+    def staging(self, slot: int):
+        """The (I, W) staging pair of ``slot`` (0 or 1): a frame copied there may be
+        passed to step() as is, and is read by the graph without another copy."""
+        return self._stage[slot]
 
     def step(self, I, W, stream=None):
         """Process one frame (float32 CUDA tensors [h, w]) on ``stream`` (a
@@ -88,20 +96,22 @@ class Tracker:
             return
         kf = k % self.kf_every == 0
         s = stream if stream is not None else torch.cuda.current_stream()
+        slot = 1 if self.graphs and I is self._stage[1][0] and W is self._stage[1][1] else 0
         with torch.cuda.stream(s):
             eager = not self.graphs or bool(self.params.timing)   # a NULL timing pointer is falsy
-            g = None if eager else self._graph.get(kf)
+            g = None if eager else self._graph.get((kf, slot))
             if g is not None:
-                if I is not self.I_in:      # a caller may fill the staging pair itself
-                    self.I_in.copy_(I, non_blocking=True)
-                if W is not self.W_in:
-                    self.W_in.copy_(W, non_blocking=True)
+                SI, SW = self._stage[slot]
+                if I is not SI:             # a caller may fill the staging pair itself
+                    SI.copy_(I, non_blocking=True)
+                if W is not SW:
+                    SW.copy_(W, non_blocking=True)
                 g.replay()
             else:
                 self._frame(I, W, kf, s)
             self.results[k].copy_(self.res[0], non_blocking=True)
-        if self.graphs and not self.params.timing and kf not in self._graph:
-            self._capture(kf)
+        if self.graphs and not self.params.timing and (kf, slot) not in self._graph:
+            self._capture(kf, slot)
         self.is_kf[k] = kf
         self.k = k + 1
 
@@ -123,14 +133,15 @@ class Tracker:
             self.T1.copy_(self._T_view())
         self.kfp.build(self.I_kf, self.W_kf, self.K, stream)
 
-    def _capture(self, kf: bool):
-        """Capture steps 1-5 of a frame of this kind, reading the staging pair (nothing runs)."""
+    def _capture(self, kf: bool, slot: int):
+        """Capture steps 1-5 of a frame of this kind, reading staging pair ``slot`` (nothing runs)."""
         torch = self.torch
         torch.cuda.synchronize(self.device)
         g = torch.cuda.CUDAGraph()
+        SI, SW = self._stage[slot]
         with torch.cuda.graph(g):
-            self._frame(self.I_in, self.W_in, kf, torch.cuda.current_stream())
-        self._graph[kf] = g
+            self._frame(SI, SW, kf, torch.cuda.current_stream())
+        self._graph[(kf, slot)] = g
 
     def trajectory(self):
         """World-from-camera poses of the processed frames (frame 0 = identity), on the host."""

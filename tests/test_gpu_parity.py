@@ -274,7 +274,7 @@ def test_tracking_graph_replay_equals_eager_enqueue():
         out.append((trk.results.cpu().numpy(), trk.I_kf.cpu().numpy(), trk.W_kf.cpu().numpy(),
                     trk.C_kf.cpu().numpy(), trk.is_kf.copy()))
         if graphs:
-            assert set(trk._graph) == {False, True}
+            assert set(trk._graph) == {(False, 0), (True, 0)}
     for a, b in zip(*out):
         assert np.array_equal(a, b)
 
