@@ -262,9 +262,9 @@ def native(args):
     launches = {"n": 0}
 
     def kernels_in_step(k):
-        # pyramid (levels) + predict + init + 2 per iteration + the closing reduction
-        # + fuse, or switch (compose + init_kf) + kf pyramid
-        n = LEVELS + 1 + 1 + 2 * per_step_launches + 1 + LEVELS
+        # frame pyramid (one launch, every level) + predict + init + 2 per iteration
+        # + the closing reduction + fuse, or switch (compose + init_kf) + kf pyramid
+        n = 1 + 1 + 1 + 2 * per_step_launches + 1 + 1
         n += 2 if k % KF_EVERY == 0 else 1
         return n
 

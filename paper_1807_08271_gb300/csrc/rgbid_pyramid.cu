@@ -79,29 +79,55 @@ __device__ __forceinline__ void store_iw<RGBID_PLANES_BF16_F16>(void* base, size
     reinterpret_cast<unsigned int*>(base)[idx] = (unsigned int)bi | ((unsigned int)hw << 16);
 }
 
-template <int PREC, int L>
-__global__ void pyramid_level_kernel(PyrSrc src, void* dst, int w, int h, int pitch) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= w || y >= h) return;
-    const IWf v = Down<L>::at(src, x, y);
-    store_iw<PREC>(dst, (size_t)y * pitch + x, v.i, v.w);
-}
+// Every level in one launch: block b belongs to the level whose block range holds
+// it (the coarsest levels, whose pixels cost the most loads, come first), and
+// each thread computes one pixel exactly as the per-level kernel does.
+struct PyrLevelOut {
+    void* dst;
+    int w, h, pitch, bx, first_block;
+};
+struct PyrAll {
+    PyrSrc src;
+    int levels;
+    PyrLevelOut lv[RGBID_MAX_LEVELS];
+};
 
 template <int PREC>
-static cudaError_t launch_level(int l, const PyrSrc& src, void* dst, int w, int h, int pitch, cudaStream_t st) {
-    dim3 blk(32, 8);
-    dim3 grd((w + 31) / 32, (h + 7) / 8);
+__global__ void __launch_bounds__(256) pyramid_all_kernel(PyrAll a) {
+    const int b = blockIdx.x;
+    int l = 0, best = -1;      // the level with the largest first block <= b
+#pragma unroll
+    for (int k = 0; k < RGBID_MAX_LEVELS; ++k)
+        if (k < a.levels && a.lv[k].first_block <= b && a.lv[k].first_block > best) {
+            best = a.lv[k].first_block;
+            l = k;
+        }
+    void* dst = a.lv[0].dst;
+    int w = a.lv[0].w, h = a.lv[0].h, pitch = a.lv[0].pitch, bx = a.lv[0].bx, fb = a.lv[0].first_block;
+#pragma unroll
+    for (int k = 1; k < RGBID_MAX_LEVELS; ++k)
+        if (k == l) {
+            dst = a.lv[k].dst;
+            w = a.lv[k].w;
+            h = a.lv[k].h;
+            pitch = a.lv[k].pitch;
+            bx = a.lv[k].bx;
+            fb = a.lv[k].first_block;
+        }
+    const int lb = b - fb;
+    const int x = (lb % bx) * 32 + (int)(threadIdx.x & 31);
+    const int y = (lb / bx) * 8 + (int)(threadIdx.x >> 5);
+    if (x >= w || y >= h) return;
+    IWf v;
     switch (l) {
-        case 0: pyramid_level_kernel<PREC, 0><<<grd, blk, 0, st>>>(src, dst, w, h, pitch); break;
-        case 1: pyramid_level_kernel<PREC, 1><<<grd, blk, 0, st>>>(src, dst, w, h, pitch); break;
-        case 2: pyramid_level_kernel<PREC, 2><<<grd, blk, 0, st>>>(src, dst, w, h, pitch); break;
-        case 3: pyramid_level_kernel<PREC, 3><<<grd, blk, 0, st>>>(src, dst, w, h, pitch); break;
-        case 4: pyramid_level_kernel<PREC, 4><<<grd, blk, 0, st>>>(src, dst, w, h, pitch); break;
-        case 5: pyramid_level_kernel<PREC, 5><<<grd, blk, 0, st>>>(src, dst, w, h, pitch); break;
-        default: return cudaErrorInvalidValue;
+        case 0: v = Down<0>::at(a.src, x, y); break;
+        case 1: v = Down<1>::at(a.src, x, y); break;
+        case 2: v = Down<2>::at(a.src, x, y); break;
+        case 3: v = Down<3>::at(a.src, x, y); break;
+        case 4: v = Down<4>::at(a.src, x, y); break;
+        default: v = Down<5>::at(a.src, x, y); break;
     }
-    return cudaGetLastError();
+    store_iw<PREC>(dst, (size_t)y * pitch + x, v.i, v.w);
 }
 
 static int level_pitch(int w) { return (w + 15) / 16 * 16; }
@@ -139,7 +165,10 @@ extern "C" int rgbid_build_pyramid(const float* I0, const float* W0, int pitch0,
     memset(&P, 0, sizeof(P));
     P.levels = levels;
     P.precision = precision;
-    PyrSrc src{I0, W0, pitch0};
+    PyrAll all;
+    memset(&all, 0, sizeof(all));
+    all.src = PyrSrc{I0, W0, pitch0};
+    all.levels = levels;
     char* base = (char*)storage;
     int w = width, h = height;
     rgbid_intrinsics K = K0;
@@ -150,10 +179,7 @@ extern "C" int rgbid_build_pyramid(const float* I0, const float* W0, int pitch0,
         L.pitch = level_pitch(w);
         L.K = K;
         L.IW = base;
-        cudaError_t e = precision == RGBID_PLANES_F32
-                            ? launch_level<RGBID_PLANES_F32>(l, src, base, w, h, L.pitch, stream)
-                            : launch_level<RGBID_PLANES_BF16_F16>(l, src, base, w, h, L.pitch, stream);
-        if (e != cudaSuccess) return RGBID_ERR_CUDA;
+        all.lv[l] = PyrLevelOut{base, w, h, L.pitch, (w + 31) / 32, 0};
         base += align_up((size_t)L.pitch * h * bytes_per_px(precision), 256);
         w /= 2;
         h /= 2;
@@ -162,6 +188,15 @@ extern "C" int rgbid_build_pyramid(const float* I0, const float* W0, int pitch0,
         K.cx = (K.cx + 0.5) * 0.5 - 0.5;
         K.cy = (K.cy + 0.5) * 0.5 - 0.5;
     }
+    // block ranges, coarsest level first
+    int nblocks = 0;
+    for (int l = levels - 1; l >= 0; --l) {
+        all.lv[l].first_block = nblocks;
+        nblocks += all.lv[l].bx * ((all.lv[l].h + 7) / 8);
+    }
+    if (precision == RGBID_PLANES_F32) pyramid_all_kernel<RGBID_PLANES_F32><<<nblocks, 256, 0, stream>>>(all);
+    else pyramid_all_kernel<RGBID_PLANES_BF16_F16><<<nblocks, 256, 0, stream>>>(all);
+    if (cudaGetLastError() != cudaSuccess) return RGBID_ERR_CUDA;
     *out = P;
     return RGBID_OK;
 }
