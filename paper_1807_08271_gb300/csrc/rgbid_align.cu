@@ -292,8 +292,9 @@ __global__ void __launch_bounds__(kRobustNT) robust_kernel(RobustArgs a) {
     // What this launch reads before the wait comes from grids that completed before
     // it started (the previous robust launch and the alignment's initialisation,
     // both ahead of the sweep it waits for): the state fields that CTA 0 writes back,
-    // and the keyframe-side loads of the systematic sample (A's planes do not change
-    // during an alignment).  Only the sweep's partials and the pose need the wait.
+    // the pose and its FP32 warp form, and the keyframe-side loads of the systematic
+    // sample (A's planes do not change during an alignment).  Only the sweep's
+    // partials and their count need the wait.
     if (rank == 0) {
         constexpr int kRobWords = (int)(sizeof(RobustParams) / 4);
         if (threadIdx.x < kRobWords)
