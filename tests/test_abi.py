@@ -257,3 +257,28 @@ def test_nu_constant_series_matches_digamma(binding):
         assert np.abs(got - want).max() < 1e-6 * max(1.0, np.abs(g).max()), (lo, hi)
     assert binding.lib().rgbid_nu_constant_series(10.0, 2.0, (ctypes.c_float * 4)(), 4) == -binding.ERR_INVALID_ARG
     assert binding.lib().rgbid_nu_constant_series(1.5, 30.0, (ctypes.c_float * 4)(), 4) == -binding.ERR_UNSUPPORTED
+
+
+def test_workspace_covers_the_largest_sweep_over_the_levels(binding):
+    """The alignment workspace holds the state plus one 32-slot compensated pair per
+    block of the largest sweep over the reference's levels (32-pixel-wide tiles of
+    8 rows on levels under 250K pixels, 32 rows on larger ones).  Descriptor-only
+    pyramids: nothing is read or launched."""
+    b = binding
+
+    def blocks(w, h):
+        th = 32 if w * h >= 250000 else 8
+        return ((w + 31) // 32) * ((h + th - 1) // th)
+
+    for w0, h0, levels in ((640, 480, 4), (160, 120, 3), (97, 75, 3), (1280, 960, 5), (32, 24, 1)):
+        P = b.Pyramid()
+        P.levels, P.precision = levels, b.PLANES_F32
+        w, h = w0, h0
+        nb = 0
+        for l in range(levels):
+            P.lv[l].width, P.lv[l].height, P.lv[l].pitch = w, h, w
+            nb = max(nb, blocks(w, h))
+            w, h = w // 2, h // 2
+        got = b.rgbid_align_workspace_bytes(P, b.rgbid_default_params(levels=levels, iters=[1] * levels))
+        assert got >= nb * 32 * 8, (w0, h0, got, nb)
+        assert got <= nb * 32 * 8 + 4096, (w0, h0, got, nb)   # the state header and alignment padding only
