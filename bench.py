@@ -73,6 +73,39 @@ def alu_roofline(kernel: str, units_per_launch: float, ms_per_launch: float) -> 
 TRAFFIC_PER_UNIT = {"robust_kernel": 3166208 / 19200, "sweep_kernel": 6767616 / 307200}
 
 
+# ----------------------------------------------------------------------------- ranks
+def ranks_from_env():
+    """(rank, world size, local rank) from the launcher's environment; one process: (0, 1, 0)."""
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def init_ranks(world: int, backend: str, device=None):
+    """The process group when world > 1, else None.  Every rank works on its own,
+    independent data (weak scaling); the group carries only the barriers around the
+    timed region and the timing reduction, never data."""
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    kw = {"device_id": device} if device is not None else {}
+    dist.init_process_group(backend, **kw)
+    return dist
+
+
+def max_over_ranks(values, dist, device) -> list:
+    """Each timing's maximum over the ranks: the slowest rank bounds the whole job."""
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def whole_job_rate(world: int, units_per_rank: float, ms: float) -> float:
+    """Units processed by all ranks per second of the slowest rank."""
+    return world * units_per_rank / (ms / 1000.0)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -186,8 +219,7 @@ def run_oracle_sample(n_frames: int, reduced: bool = False) -> dict:
 
 # ----------------------------------------------------------------------------- reference arm
 def reference(args):
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
+    if ranks_from_env()[0] != 0:      # rank 0 alone runs the reference arm
         return
     n_timed = max(1, min(args.steps, 24))
     r = run_oracle_sample(n_timed + 1, reduced=(args.precision == "bf16"))
@@ -230,14 +262,9 @@ def native(args):
     from paper_1807_08271_gb300 import synth
     from paper_1807_08271_gb300.tracker import Tracker
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank, world, local = ranks_from_env()
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dist = init_ranks(world, "nccl", torch.device("cuda", local))
 
     seq = synth.render_sequence(seed=rank, n_frames=N_FRAMES)
     dev = torch.device("cuda", local)
@@ -389,15 +416,12 @@ def native(args):
     E = [np.linalg.inv(seq["T_wc"][0] @ traj[i]) @ seq["T_wc"][i] for i in range(1, n_ok)]
     rot = max(float(np.arccos(np.clip((np.trace(e[:3, :3]) - 1) / 2, -1, 1))) for e in E) if E else 0.0
 
-    t = torch.tensor([total_ms, e2e_ms], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms, e2e_ms = t.tolist()
+    total_ms, e2e_ms = max_over_ranks([total_ms, e2e_ms], dist, dev)
     if rank != 0:
         dist.destroy_process_group()
         return
-    value = world * args.steps / (total_ms / 1000.0)
-    e2e_val = world * args.steps / (e2e_ms / 1000.0)
+    value = whole_job_rate(world, args.steps, total_ms)
+    e2e_val = whole_job_rate(world, args.steps, e2e_ms)
     peak, peak_kind = measured_peaks()
     rooflines = {}
     for name, (k_ms, k_units, k_count, region_ms) in kern.items():
@@ -505,8 +529,7 @@ def batch_config_dict(precision="f32", shape=None):
 
 
 def reference_batch(args):
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
+    if ranks_from_env()[0] != 0:      # rank 0 alone runs the reference arm
         return
     r = run_oracle_batch_sample(reduced=(args.precision == "bf16"))
     value = r["alignments"] / r["seconds"]
@@ -528,14 +551,9 @@ def native_batch(args):
     from paper_1807_08271_gb300 import synth
     from paper_1807_08271_gb300.batch import BatchAligner
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank, world, local = ranks_from_env()
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dist = init_ranks(world, "nccl", torch.device("cuda", local))
     dev = torch.device("cuda", local)
     prec = R.PLANES_BF16_F16 if args.precision == "bf16" else R.PLANES_F32
     pairs = synth.make_batch(seed=rank, n=BATCH_N)
@@ -651,15 +669,12 @@ def native_batch(args):
     d_plain = [pose_err(a["T"], b["T"]) for a, b in zip(res_b, res_p)]
     d_truth = [pose_err(a["T"], p["T_gt"])[0] for a, p in zip(res_b, pairs)]
 
-    t = torch.tensor([total_ms, e2e_ms], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms, e2e_ms = t.tolist()
+    total_ms, e2e_ms = max_over_ranks([total_ms, e2e_ms], dist, dev)
     if rank != 0:
         dist.destroy_process_group()
         return
     step_ms = total_ms / args.steps
-    value = world * BATCH_N * args.steps / (total_ms / 1000.0)
+    value = whole_job_rate(world, BATCH_N * args.steps, total_ms)
     peak, peak_kind = measured_peaks()
     achieved = bytes_per_unit * units / (step_ms / 1000.0) / 1e9
     cpu = None
@@ -673,7 +688,7 @@ def native_batch(args):
         "warmup": max(3, args.warmup), "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": batch_config_dict(args.precision, shape),
-        "e2e": {"value": world * BATCH_N / (e2e_ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "e2e": {"value": whole_job_rate(world, BATCH_N, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": int(B.results.numel())},
         "roofline": {"bound": "hbm", "kernel": "batch_align_kernel", "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
@@ -738,8 +753,7 @@ def learned_config_dict(meta=None):
 
 
 def reference_learned(args):
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
+    if ranks_from_env()[0] != 0:      # rank 0 alone runs the reference arm
         return
     r = run_oracle_learned_sample()
     value = r["alignments"] / r["seconds"]
@@ -761,14 +775,9 @@ def native_learned(args):
     from paper_1807_08271_gb300.learned_train import EvalSet, pose_diff, _sized
     from paper_1807_08271_gb300.synth import gpu as G
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank, world, local = ranks_from_env()
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dist = init_ranks(world, "nccl", torch.device("cuda", local))
     net = Lm.InitNet.load(Lm.WEIGHTS, max_batch=LEARNED_N)
     thr = net.meta["thresholds"]
     bank = G.TextureBank(4242 + rank, n=16)
@@ -856,10 +865,7 @@ def native_learned(args):
     from paper_1807_08271_gb300.learned import LearnedPlanner
     res_l, ms_l, _ = ev.run(lambda m, prec: LearnedPlanner(_sized(net, m), m, prec, thr), reps=5)
 
-    t = torch.tensor([out["learned"]["ms"], e2e_ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    learned_ms, e2e_ms = t.tolist()
+    learned_ms, e2e_ms = max_over_ranks([out["learned"]["ms"], e2e_ms], dist, "cuda")
     if rank != 0:
         dist.destroy_process_group()
         return
@@ -873,11 +879,11 @@ def native_learned(args):
                "sample": "two 640x480 pairs aligned from the identity with the plain schedule, one thread, "
                          "numpy float64"}
     line = {
-        "metric": LEARNED_METRIC, "value": world * n_steps / (learned_ms / 1000.0), "unit": UNIT, "n_gpus": world,
+        "metric": LEARNED_METRIC, "value": whole_job_rate(world, n_steps, learned_ms), "unit": UNIT, "n_gpus": world,
         "steps": n_steps, "warmup": max(3, args.warmup), "ms_per_step": learned_ms / n_steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 alignment, bf16 network",
         "data": "synthetic", "config": learned_config_dict(net.meta),
-        "e2e": {"value": world * n_steps / (e2e_ms / 1000.0), "unit": UNIT,
+        "e2e": {"value": whole_job_rate(world, n_steps, e2e_ms), "unit": UNIT,
                 "h2d_bytes_per_step": 4 * 640 * 480 * 4, "d2h_bytes_per_step": R.RESULT_BYTES},
         "roofline": {"bound": "hbm", "kernel": "robust_kernel", "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak if peak else None,
