@@ -76,7 +76,12 @@ class Tracker:
 
     def staging(self, slot: int):
         """The (I, W) staging pair of ``slot`` (0 or 1): a frame copied there may be
-        passed to step() as is, and is read by the graph without another copy."""
+        passed to step() as is, and is read by the graph without another copy.
+        Staging exists only with ``graphs=True``."""
+        if not self.graphs:
+            raise ValueError("staging slots exist only for a tracker built with graphs=True")
+        if slot not in (0, 1):
+            raise ValueError(f"staging slot must be 0 or 1, got {slot}")
         return self._stage[slot]
 
     def step(self, I, W, stream=None):
