@@ -21,6 +21,7 @@
 // alignment.
 #include <cooperative_groups.h>
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 
@@ -1068,11 +1069,13 @@ extern "C" int rgbid_eval_step(const rgbid_pyramid* ref, const rgbid_pyramid* cu
 // Scratch of rgbid_align_noalloc: a fixed device array that every GPU loading this
 // library holds until the process exits.  Its host-side name is only a stand-in
 // for the symbol; the device address is fetched with cudaGetSymbolAddress once
-// per device and cached.
+// per device and cached.  The cache is atomic: host threads making their first
+// call on one device at the same time each look the address up and store the
+// same value.
 namespace rgbid {
 constexpr size_t kNoallocScratchBytes = 1024u * 1024u;  // RGBID_NOALLOC_SCRATCH_BYTES
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
-static void* g_noalloc_ptr[64];
+static std::atomic<void*> g_noalloc_ptr[64];
 }  // namespace rgbid
 
 extern "C" int rgbid_align_noalloc(const rgbid_pyramid* ref, const rgbid_pyramid* cur, const double* T_init,
@@ -1081,18 +1084,17 @@ extern "C" int rgbid_align_noalloc(const rgbid_pyramid* ref, const rgbid_pyramid
     if (!ref || !params) return RGBID_ERR_INVALID_ARG;
     const size_t need = rgbid_align_workspace_bytes(ref, params);
     if (need == 0) return RGBID_ERR_INVALID_ARG;
-    if (need > kNoallocScratchBytes) return RGBID_ERR_WORKSPACE;     // level 0 too large for the fixed scratch
+    if (need > kNoallocScratchBytes) return RGBID_ERR_WORKSPACE;     // the largest level sweep does not fit
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return RGBID_ERR_CUDA;
-    if (!g_noalloc_ptr[dev]) {
+    void* scratch = g_noalloc_ptr[dev].load(std::memory_order_acquire);
+    if (!scratch) {
         // set-up on the first call on this device (the device is current here)
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return RGBID_ERR_CUDA;
-        g_noalloc_ptr[dev] = p;
+        if (cudaGetSymbolAddress(&scratch, g_noalloc_scratch) != cudaSuccess || !scratch) return RGBID_ERR_CUDA;
+        g_noalloc_ptr[dev].store(scratch, std::memory_order_release);
     }
     // the alignment's init kernel resets every scratch field that must start at zero
-    return rgbid_align(ref, cur, T_init, T_init_on_device, params, g_noalloc_ptr[dev], kNoallocScratchBytes,
-                       d_result, stream);
+    return rgbid_align(ref, cur, T_init, T_init_on_device, params, scratch, kNoallocScratchBytes, d_result, stream);
 }
 
 extern "C" int rgbid_probe_wait_timeout(long long budget_cycles, int* d_timeouts, void* stream) {
