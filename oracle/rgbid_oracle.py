@@ -58,6 +58,29 @@ Readings taken where the paper is silent, ambiguous or garbled (R1..R17):
       it enters the pyramid and the keyframe as a hole, W = 0, with I = 0
       where I is not finite; in fusion such a keyframe pixel or frame-k tap is
       not a measurement.
+  R20 covariance: the extra iteration runs at the finest level at the final
+      pose, estimates (mu, sigma, nu) on the systematic sample like any
+      iteration, and takes the bilateral-filtered planes only where the paper
+      names them, in the gradients of {I_A, W_A} (the Jacobians and lambda_n);
+      the warp, residuals, masks and W_A itself stay unfiltered.  The bilateral
+      filter (parameters unstated: radius, sigma_s and the range sigmas are
+      configuration) weighs the (2r+1)^2 window inside the image by
+      exp(-d^2 / 2 sigma_s^2) exp(-(f(p) - f(q))^2 / 2 sigma_r^2); W only over
+      valid (> 0) neighbours, holes stay holes.
+  R21 covisibility: S_V counts a valid pixel of A whose transfer lies in front
+      of B and whose nearest pixel of B, floor(p_B + 1/2), lies in the image,
+      holds a valid W_B and passes |W_B - w_B| < 3 sigma_W with w_B = 1 / Z_B
+      (the ratio only counts, so no interpolation of W_B is needed; with four
+      valid taps required, 10 % scattered holes alone would cut every ratio to
+      about 0.65); sigma_W is the frame's final one (as R14).  The tracker
+      switches keyframe, optionally, when min(vr_AB, vr_BA) between the
+      keyframe and the aligned frame falls below the threshold (0.7 in the
+      paper); the switch frame is handled as in R15.
+  R22 warp-then-downsample mode: B is warped at level 0 with K_0; the warped
+      maps I_B*, W_B* (valid where mask_I's, resp. mask_W's warp conditions
+      hold at level 0) are reduced to level l by R1's rule applied to both,
+      each with its own validity (mean of the valid children, valid when one
+      is); level l's masks are A's conditions there plus that validity.
 """
 from __future__ import annotations
 
@@ -352,7 +375,8 @@ def estimate_nu(r, mu: float, sigma: float, lo: float = 2.0, hi: float = 10.0, s
 
 @dataclass
 class AlignParams:
-    """Alignment schedule and robust-estimation constants."""
+    """Alignment schedule and robust-estimation constants (``warp_mode``: "level"
+    warps B at each level, "full" warps at level 0 and downsamples, reading R22)."""
     levels: int = 3
     iters: tuple = (5, 5, 10)          # per level, index 0 = finest (reading R12)
     scale_iters: int = 10              # reading R9
@@ -364,6 +388,7 @@ class AlignParams:
     nu_hi: float = 10.0
     min_valid: int = 60                # reading R16
     sigma_floor: float = 1e-12
+    warp_mode: str = "level"
 
 
 def robust_params(rI, rW, P: AlignParams):
@@ -397,22 +422,61 @@ def sample_stride(w: int, h: int, cap: int = 19200) -> int:
 
 
 # ----------------------------------------------------------------------------- one IRLS step
-def eval_step(pyrA, pyrB, level: int, T, robust=None, P: AlignParams | None = None):
+def downsample_valid(X, valid):
+    """R1's reduction of a map with its own validity: each coarse pixel is the mean
+    of its valid children, summed (a+b)+(c+d), and valid when one child is (reading R22)."""
+    X = np.where(valid, np.asarray(X, dtype=np.float64), 0.0)
+    h2, w2 = X.shape[0] // 2, X.shape[1] // 2
+    kids = [(X[0:2 * h2:2, 0:2 * w2:2], valid[0:2 * h2:2, 0:2 * w2:2]),
+            (X[0:2 * h2:2, 1:2 * w2:2], valid[0:2 * h2:2, 1:2 * w2:2]),
+            (X[1:2 * h2:2, 0:2 * w2:2], valid[1:2 * h2:2, 0:2 * w2:2]),
+            (X[1:2 * h2:2, 1:2 * w2:2], valid[1:2 * h2:2, 1:2 * w2:2])]
+    n = kids[0][1].astype(np.float64) + kids[1][1] + kids[2][1] + kids[3][1]
+    s = (kids[0][0] + kids[1][0]) + (kids[2][0] + kids[3][0])
+    return np.where(n > 0, s / np.where(n > 0, n, 1.0), 0.0), n > 0
+
+
+def warped_full_resolution(pyrA, pyrB, level: int, T):
+    """The warped maps of "Iterative optimisation" read literally (reading R22): B
+    warped towards A at level 0, then downsampled to ``level``.  Returns
+    (I_B*, valid_I, W_B*, valid_W) at that level."""
+    wp = inverse_geometric_warp(pyrA[0], pyrB[0], T)
+    vI = wp["validA"] & wp["front"] & wp["bil_valid"]
+    vW = vI & wp["all4"] & (wp["Zp"] > 0)
+    I_s, W_s = np.where(vI, wp["I_Bw"], 0.0), np.where(vW, wp["W_Bw"], 0.0)
+    for _ in range(level):
+        I_s, vI = downsample_valid(I_s, vI)
+        W_s, vW = downsample_valid(W_s, vW)
+    return I_s, vI, W_s, vW
+
+
+def eval_step(pyrA, pyrB, level: int, T, robust=None, P: AlignParams | None = None, grad_planes=None):
     """Residuals, Jacobians, weights and normal equations at one level and pose.
 
     Residuals r(p, 0) of eqs. res_int / res_depth; Jacobians of the same
     equations, J = g M(p) with M(p) = [I3 | -[X_A]x] (eq. DeltaX); weights of
     eq. minimisationIRLS; H = sum w J^T J and g = sum w J^T r(p, 0), so that the
     step solves H xi = -g.  ``robust`` = dict(mu, sigma, nu) per channel, or
-    None to estimate it on the systematic sample."""
+    None to estimate it on the systematic sample.  ``grad_planes`` = (I, W) at
+    this level whose gradients replace A's (the covariance iteration, reading
+    R20); ``P.warp_mode`` "full" takes the warped maps of reading R22."""
     P = P or AlignParams()
     A, B = pyrA[level], pyrB[level]
     fx, fy, cx, cy = A.K
     h, w = A.W.shape
     wp = inverse_geometric_warp(A, B, T)
-    gIx, gIy, gWx, gWy, interior, gW_valid = gradients(A.I, A.W)
-    mask_I = wp["validA"] & interior & wp["front"] & wp["bil_valid"]
-    mask_W = mask_I & wp["all4"] & gW_valid & (wp["Zp"] > 0)
+    if grad_planes is None:
+        gIx, gIy, gWx, gWy, interior, gW_valid = gradients(A.I, A.W)
+    else:
+        gIx, gIy, gWx, gWy, interior, gW_valid = gradients(*grad_planes)
+    if P.warp_mode == "full":
+        I_s, vI, W_s, vW = warped_full_resolution(pyrA, pyrB, level, T)
+        wp["I_Bw"], wp["W_Bw"] = I_s, W_s
+        mask_I = wp["validA"] & interior & vI
+        mask_W = mask_I & vW & gW_valid
+    else:
+        mask_I = wp["validA"] & interior & wp["front"] & wp["bil_valid"]
+        mask_W = mask_I & wp["all4"] & gW_valid & (wp["Zp"] > 0)
     r_I = np.where(mask_I, wp["I_Bw"] - A.I, 0.0)
     r_W = np.where(mask_W, wp["W_Bw"] - A.W, 0.0)
 
@@ -556,16 +620,123 @@ def fuse(I_kf, W_kf, C_kf, I_k, W_k, K, T, sigma_W: float, fuse_intensity: bool 
 
 
 
+# ----------------------------------------------------------------------------- covariance of the estimate
+@dataclass
+class BilateralParams:
+    """Bilateral filter of the covariance iteration (reading R20; the paper gives no values)."""
+    radius: int = 2
+    sigma_s: float = 1.5        # pixels
+    sigma_r_I: float = 0.1      # intensity units
+    sigma_r_W: float = 0.01     # inverse depth, 1/m
+
+
+def bilateral_filter(I, W, F: BilateralParams):
+    """Bilateral filter of {I_A, W_A} (reading R20), one output pixel at a time:
+    out(p) = sum_q k(p, q) f(q) / sum_q k(p, q) over the window q = p + (dx, dy),
+    |dx|, |dy| <= radius, inside the image, with
+    k = exp(-(dx^2 + dy^2) / (2 sigma_s^2)) exp(-(f(p) - f(q))^2 / (2 sigma_r^2));
+    for W only neighbours with W > 0 take part and a hole stays a hole."""
+    I = np.asarray(I, dtype=np.float64)
+    W = np.asarray(W, dtype=np.float64)
+    h, w = I.shape
+    r = int(F.radius)
+    num_I = np.zeros((h, w)); den_I = np.zeros((h, w))
+    num_W = np.zeros((h, w)); den_W = np.zeros((h, w))
+    validW = W > 0
+    for dy in range(-r, r + 1):
+        for dx in range(-r, r + 1):
+            gs = np.exp(-(dx * dx + dy * dy) / (2.0 * F.sigma_s ** 2))
+            # q = p + (dx, dy) for every p whose q lies inside the image
+            ys, ye = max(0, -dy), min(h, h - dy)
+            xs, xe = max(0, -dx), min(w, w - dx)
+            P_I, Q_I = I[ys:ye, xs:xe], I[ys + dy:ye + dy, xs + dx:xe + dx]
+            kI = gs * np.exp(-(P_I - Q_I) ** 2 / (2.0 * F.sigma_r_I ** 2))
+            num_I[ys:ye, xs:xe] += kI * Q_I
+            den_I[ys:ye, xs:xe] += kI
+            P_W, Q_W = W[ys:ye, xs:xe], W[ys + dy:ye + dy, xs + dx:xe + dx]
+            kW = np.where(validW[ys + dy:ye + dy, xs + dx:xe + dx],
+                          gs * np.exp(-(P_W - Q_W) ** 2 / (2.0 * F.sigma_r_W ** 2)), 0.0)
+            num_W[ys:ye, xs:xe] += kW * Q_W
+            den_W[ys:ye, xs:xe] += kW
+    I_f = num_I / den_I
+    W_f = np.where(validW, num_W / np.where(validW, den_W, 1.0), 0.0)
+    return I_f, W_f
+
+
+def covariance(pyrA, pyrB, T, P: AlignParams | None = None, F: BilateralParams | None = None):
+    """Covariance of the motion estimate ("Dense motion estimation", the paragraph
+    after the update rule): one more iteration at the final pose T, not updating
+    it, with {I_A, W_A} bilateral-filtered before their gradients are taken;
+    Sigma = H_filt^-1 (reading R20).  Returns dict(H, Sigma, robust, n_valid, ok);
+    ok is False (Sigma = 0) when H_filt is not positive definite (reading R16)."""
+    P = P or AlignParams()
+    F = F or BilateralParams()
+    A0 = pyrA[0]
+    I_f, W_f = bilateral_filter(A0.I, A0.W, F)
+    st = eval_step(pyrA, pyrB, 0, T, None, P, grad_planes=(I_f, W_f))
+    H = st["H"]
+    ok = st["n_valid"][0] + st["n_valid"][1] >= P.min_valid
+    try:
+        np.linalg.cholesky(H)
+    except np.linalg.LinAlgError:
+        ok = False
+    Sigma = np.linalg.inv(H) if ok else np.zeros((6, 6))
+    return dict(H=H, Sigma=Sigma, robust=st["robust"], n_valid=st["n_valid"], ok=ok, step=st)
+
+
+# ----------------------------------------------------------------------------- covisibility
+def covisible_counts(A: Level, B: Level, T, sigma_W: float):
+    """|S_V| and |S_H| of "Dense frame covisibility ratio" with A's pixels transferred
+    into B by eq. 3d_registration, T = A_T_B (reading R21): p_B is read at its
+    nearest pixel, which must lie in the image and hold a valid W_B within
+    3 sigma_W of the transferred w_B = 1 / Z_B."""
+    T = np.asarray(T, dtype=np.float64)
+    R, t = T[:3, :3], T[:3, 3]
+    fx, fy, cx, cy = A.K
+    h, w = A.W.shape
+    hb, wb = B.W.shape
+    v, u = np.mgrid[0:h, 0:w].astype(np.float64)
+    validA = A.W > 0
+    q = np.stack([(u - cx) / fx, (v - cy) / fy, np.ones((h, w))], axis=-1)
+    X_B = (q / np.where(validA, A.W, 1.0)[..., None] - t) @ R
+    Z_B = X_B[..., 2]
+    front = Z_B > 0
+    Zs = np.where(front, Z_B, 1.0)
+    xn = np.floor(fx * X_B[..., 0] / Zs + cx + 0.5)
+    yn = np.floor(fy * X_B[..., 1] / Zs + cy + 0.5)
+    inside = front & (xn >= 0) & (xn <= wb - 1) & (yn >= 0) & (yn <= hb - 1)
+    Wn = B.W[np.where(inside, yn, 0).astype(np.int64), np.where(inside, xn, 0).astype(np.int64)]
+    visible = validA & inside & (Wn > 0) & (np.abs(Wn - 1.0 / Zs) < 3.0 * sigma_W)
+    return int(visible.sum()), int(validA.sum())
+
+
+def covisibility_ratio(I_A, W_A, I_B, W_B, K, T, sigma_W: float):
+    """vr = min(vr_AB, vr_BA), vr_AB = |S_V| / |S_H| (reading R21, R19 for the planes).
+    Returns dict(vr, vr_AB, vr_BA, counts=((S_V, S_H) A->B, (S_V, S_H) B->A))."""
+    K = tuple(float(k) for k in K)
+    A = Level(*measurement_planes(I_A, W_A), K)
+    B = Level(*measurement_planes(I_B, W_B), K)
+    ab = covisible_counts(A, B, T, sigma_W)
+    ba = covisible_counts(B, A, se3_inv(T), sigma_W)
+    vr_ab = ab[0] / ab[1] if ab[1] else 0.0
+    vr_ba = ba[0] / ba[1] if ba[1] else 0.0
+    return dict(vr=min(vr_ab, vr_ba), vr_AB=vr_ab, vr_BA=vr_ba, counts=(ab, ba))
+
+
 # ----------------------------------------------------------------------------- tracking front-end
-def track_sequence(I_frames, W_frames, K, levels: int = 4, iters=(5, 5, 5, 10), kf_every: int = 20,
-                   fuse_intensity: bool = True, n_frames: int | None = None, reduced: bool = False):
+def track_sequence(I_frames, W_frames, K, levels: int = 4, iters=(5, 5, 5, 10), kf_every: int | None = 20,
+                   fuse_intensity: bool = True, n_frames: int | None = None, reduced: bool = False,
+                   kf_covisibility: float | None = None):
     """Frame-to-keyframe tracking with fusion ("Camera tracking", "Keyframe fusion").
 
     Frame 0 initialises the keyframe (C_kf = 1).  Frame k is aligned to the
     keyframe from the constant-velocity guess kf_T_k(0) = kf_T_{k-1} (kf_T_{k-2})^-1
     kf_T_{k-1}; every ``kf_every`` frames the aligned frame becomes the new
     keyframe (reading R15), otherwise it is fused into the keyframe with the
-    final sigma_W of its alignment (reading R14).  With ``reduced`` the pyramids
+    final sigma_W of its alignment (reading R14).  With ``kf_covisibility`` the
+    switch happens instead when the covisibility ratio between the keyframe and
+    the aligned frame falls below that value (0.7 in the paper; reading R21), and
+    the ratios are returned under "covisibility".  With ``reduced`` the pyramids
     are those of the reduced-precision form (bfloat16 I, binary16 W per level;
     the keyframe planes themselves stay float).  Returns dict(T_world [n,4,4]
     camera-to-world with frame 0 at the identity, results (per-frame align
@@ -581,6 +752,7 @@ def track_sequence(I_frames, W_frames, K, levels: int = 4, iters=(5, 5, 5, 10), 
     T_wkf = np.eye(4)
     T_world = [np.eye(4)]
     results = []
+    covis = []
     for k in range(1, n):
         cur = pyramid(I_frames[k], W_frames[k], K, levels)
         T_init = se3_project(T1 @ se3_inv(T2) @ T1)
@@ -588,7 +760,13 @@ def track_sequence(I_frames, W_frames, K, levels: int = 4, iters=(5, 5, 5, 10), 
         results.append(r)
         Tk = r["T"]
         T_world.append(T_wkf @ Tk)
-        if k % kf_every == 0:
+        if kf_covisibility is not None:
+            c = covisibility_ratio(I_kf, W_kf, I_frames[k], W_frames[k], K, Tk, r["robust"]["sigma"][1])
+            covis.append(c["vr"])
+            switch = c["vr"] < kf_covisibility
+        else:
+            switch = k % kf_every == 0
+        if switch:
             T2 = se3_inv(Tk) @ T1
             T1 = np.eye(4)
             T_wkf = T_wkf @ Tk
@@ -600,4 +778,4 @@ def track_sequence(I_frames, W_frames, K, levels: int = 4, iters=(5, 5, 5, 10), 
             T2 = T1
             T1 = Tk
         kfp = pyramid(I_kf, W_kf, K, levels)
-    return dict(T_world=np.stack(T_world), results=results, keyframe=(I_kf, W_kf, C_kf))
+    return dict(T_world=np.stack(T_world), results=results, keyframe=(I_kf, W_kf, C_kf), covisibility=covis)
