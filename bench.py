@@ -106,6 +106,39 @@ def whole_job_rate(world: int, units_per_rank: float, ms: float) -> float:
     return world * units_per_rank / (ms / 1000.0)
 
 
+def pose_err(Ta, Tb):
+    """(rotation angle, translation norm) of Ta^-1 Tb.  The angle is
+    atan2(|axial part|, (tr - 1)/2) of the relative rotation, which stays exact
+    for tiny angles; arccos((tr - 1)/2) alone turns a 1e-10 departure from
+    orthonormality of an FP64 pose into ~1e-5 rad."""
+    import numpy as np
+    E = np.linalg.inv(np.asarray(Ta, dtype=np.float64)) @ np.asarray(Tb, dtype=np.float64)
+    Rm = E[:3, :3]
+    ax = 0.5 * np.array([Rm[2, 1] - Rm[1, 2], Rm[0, 2] - Rm[2, 0], Rm[1, 0] - Rm[0, 1]])
+    ang = float(np.arctan2(np.linalg.norm(ax), 0.5 * (np.trace(Rm) - 1.0)))
+    return ang, float(np.linalg.norm(E[:3, 3]))
+
+
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+def golden(name: str):
+    """A stored oracle result (written by the scripts beside it, which call only the
+    oracle), or None when absent."""
+    try:
+        with open(os.path.join(GOLDEN, name)) as f:
+            return json.load(f)
+    except OSError:
+        return None
+
+
+def err_stats(errs) -> dict:
+    import numpy as np
+    e = np.asarray(errs, dtype=np.float64).reshape(-1, 2)
+    return {"n": int(e.shape[0]), "max_rad": float(e[:, 0].max()), "p99_rad": float(np.percentile(e[:, 0], 99)),
+            "max_m": float(e[:, 1].max()), "p99_m": float(np.percentile(e[:, 1], 99))}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -113,6 +146,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extensions", action="store_true",
+                    help="leave out the batched, bf16 and learned forms that the default line summarises")
     ap.add_argument("--workload", choices=["sequence", "batch", "learned"], default="sequence",
                     help="sequence: the 640x480 tracking sequence (default); batch: 64 uneven loop-closure "
                          "pairs in one persistent launch; learned: held-out 640x480 pairs with the learned "
@@ -317,16 +352,19 @@ def native(args):
             f = 0
         return 1 if f == 0 else f
 
-    # end to end, frames go from pinned host memory straight into the tracker's two
-    # staging slots: frame k+1 is uploaded on a copy stream while frame k runs, gated
-    # on frame k's start, so every copy lies inside a timed interval and none
-    # overlaps the L2 flush between steps; frame k+1 waits for its copy
+    # Every pass feeds the tracker through its two staging slots: frame k+1 is copied
+    # on a copy stream into the slot it will read while frame k runs, gated on frame
+    # k's start, so every copy lies inside a timed interval and none overlaps the L2
+    # flush between steps; frame k+1 waits for its copy.  The device-resident pass
+    # copies from the sequence held in HBM, the end-to-end pass from pinned host
+    # memory (and reads each frame's result back to pinned host memory).
     copy_stream = torch.cuda.Stream(device=dev)
     copied = [torch.cuda.Event(), torch.cuda.Event()]
-    pipe = {"slot": 0, "ready": None}   # ready: (frame, slot) uploaded ahead
+    pipe = {"slot": 0, "ready": None}   # ready: (frame, slot, source) uploaded ahead
 
     def run_steps(n, timed, e2e=False, res_host=None):
         evs = []
+        src_I, src_W = (I_host, W_host) if e2e else (I_all, W_all)
         for _ in range(n):
             k = next_frame()
             with torch.cuda.stream(stream):
@@ -335,37 +373,36 @@ def native(args):
                     e0 = torch.cuda.Event(enable_timing=True)
                     e1 = torch.cuda.Event(enable_timing=True)
                     e0.record(stream)
-                if e2e:
-                    gate = torch.cuda.Event()
-                    gate.record(stream)          # the previous frame is done reading the other slot
-                    slot = pipe["slot"]
-                    SI, SW = trk.staging(slot)
-                    if pipe["ready"] == (k, slot):
-                        stream.wait_event(copied[slot])
-                    else:
-                        SI.copy_(I_host[k], non_blocking=True)
-                        SW.copy_(W_host[k], non_blocking=True)
-                    trk.step(SI, SW, stream)
-                    nk, other = peek_next(), slot ^ 1
-                    copy_stream.wait_event(gate)
-                    with torch.cuda.stream(copy_stream):
-                        OI, OW = trk.staging(other)
-                        OI.copy_(I_host[nk], non_blocking=True)
-                        OW.copy_(W_host[nk], non_blocking=True)
-                        copied[other].record(copy_stream)
-                    pipe["slot"], pipe["ready"] = other, (nk, other)
-                    res_host.copy_(trk.res[0], non_blocking=True)
+                gate = torch.cuda.Event()
+                gate.record(stream)          # the previous frame is done reading the other slot
+                slot = pipe["slot"]
+                SI, SW = trk.staging(slot)
+                if pipe["ready"] == (k, slot, e2e):
+                    stream.wait_event(copied[slot])
                 else:
-                    trk.step(I_all[k], W_all[k], stream)
+                    SI.copy_(src_I[k], non_blocking=True)
+                    SW.copy_(src_W[k], non_blocking=True)
+                trk.step(SI, SW, stream)
+                nk, other = peek_next(), slot ^ 1
+                copy_stream.wait_event(gate)
+                with torch.cuda.stream(copy_stream):
+                    OI, OW = trk.staging(other)
+                    OI.copy_(src_I[nk], non_blocking=True)
+                    OW.copy_(src_W[nk], non_blocking=True)
+                    copied[other].record(copy_stream)
+                pipe["slot"], pipe["ready"] = other, (nk, other, e2e)
+                if e2e:
+                    res_host.copy_(trk.res[0], non_blocking=True)
                 if timed:
                     e1.record(stream)
                     evs.append((e0, e1))
                     launches["n"] += kernels_in_step(k)
         return evs
 
-    # warm-up (also builds the library on first use)
+    # warm-up (also builds the library on first use and captures the frame graphs)
     run_steps(args.warmup, timed=False)
     torch.cuda.synchronize()
+    pipe["ready"] = None      # the first timed frame uploads inside its own interval
 
     # ---- device-resident timed region (no per-launch events: they would break the
     #      programmatic dependent launches between the kernels)
@@ -413,8 +450,7 @@ def native(args):
     # pose sanity: frames of the last pass vs ground truth
     traj = trk.trajectory()
     n_ok = trk.k
-    E = [np.linalg.inv(seq["T_wc"][0] @ traj[i]) @ seq["T_wc"][i] for i in range(1, n_ok)]
-    rot = max(float(np.arccos(np.clip((np.trace(e[:3, :3]) - 1) / 2, -1, 1))) for e in E) if E else 0.0
+    rot = max((pose_err(seq["T_wc"][0] @ traj[i], seq["T_wc"][i])[0] for i in range(1, n_ok)), default=0.0)
 
     total_ms, e2e_ms = max_over_ranks([total_ms, e2e_ms], dist, dev)
     if rank != 0:
@@ -439,32 +475,36 @@ def native(args):
     roofline = rooflines[dominant]
     others = {n: r for n, r in rooflines.items() if n != dominant}
     cpu = None
-    pose_check = None
     if not args.no_cpu_baseline:
         n_cmp = 7
         r = run_oracle_sample(n_cmp, reduced=(args.precision == "bf16"))
         cpu = {"value": r["frames"] / r["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"frames 1..{r['frames']} of the sequence (align + fuse), one thread, numpy float64"
-                         + (", bf16/fp16-rounded pyramids" if args.precision == "bf16" else "")}
-        # per-frame pose error of a fresh GPU pass over the same frames against the oracle
-        chk = Tracker(W, H, K, levels=LEVELS, iters=ITERS, kf_every=KF_EVERY, max_frames=n_cmp, device=dev,
+                         + (", bf16/fp16-rounded pyramids" if args.precision == "bf16" else ""),
+               "host": host_info()}
+    # every frame of a fresh GPU pass over the whole sequence against the FP64 oracle's
+    # tracking of it (stored; seed 0): alignment poses kf_T_k and world poses
+    pose_check = None
+    gold = golden("seq640_oracle.json")
+    if gold is not None and rank == 0:
+        chk = Tracker(W, H, K, levels=LEVELS, iters=ITERS, kf_every=KF_EVERY, max_frames=N_FRAMES, device=dev,
                       precision=prec)
-        for k in range(n_cmp):
+        for k in range(N_FRAMES):
             chk.step(I_all[k], W_all[k])
         torch.cuda.synchronize()
-        gT = chk.trajectory()
-
-        def errs(oT):
-            out = []
-            for k in range(1, n_cmp):
-                E = np.linalg.inv(np.asarray(oT[k])) @ gT[k]
-                c = float(np.clip((np.trace(E[:3, :3]) - 1) / 2, -1, 1))
-                out.append([float(np.arccos(c)), float(np.linalg.norm(E[:3, 3]))])
-            return out
-        pose_check = {"frames": f"1..{n_cmp - 1}", "vs_oracle_same_planes_rad_m": errs(r["T_world"])}
-        if args.precision == "bf16":
-            rf = run_oracle_sample(n_cmp, reduced=False)
-            pose_check["vs_oracle_fp32_planes_rad_m"] = errs(rf["T_world"])
+        gT, gr = chk.trajectory(), chk.frame_results()
+        pose_check = {"frames": f"1..{N_FRAMES - 1}",
+                      "status": sorted(set(int(x["status"]) for x in gr)),
+                      "max_rot_err_vs_truth_rad": max(pose_err(seq["T_wc"][0] @ gT[k], seq["T_wc"][k])[0]
+                                                      for k in range(N_FRAMES))}
+        planes = (("reduced_planes", "fp32_planes") if args.precision == "bf16" else ("fp32_planes",))
+        for name in planes:
+            fr = gold[name]["frames"]
+            pose_check[f"alignment_vs_oracle_{name}"] = err_stats(
+                [pose_err(np.array(o["T"]).reshape(4, 4), x["T"]) for o, x in zip(fr, gr)])
+            pose_check[f"world_vs_oracle_{name}"] = err_stats(
+                [pose_err(np.array(o["T_world"]).reshape(4, 4), gT[o["k"]]) for o in fr])
+        pose_check["oracle"] = "stored FP64 oracle tracking of this sequence (tests/golden/seq640_oracle.json)"
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -478,9 +518,58 @@ def native(args):
         "cpu_baseline": cpu, "clocks": clk, "gpu_launches": gpu_launches,
         "wall_s_timed": t_wall, "max_rot_err_vs_truth_rad": rot, "pose_check": pose_check,
     }
+    if world == 1 and args.precision == "f32" and not args.no_extensions:
+        line["extensions"] = run_extensions(args)
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- extensions
+EXTENSION_RUNS = {
+    # name: (arguments, summary keys taken from the form's own line)
+    "batched": (["--workload", "batch", "--steps", "120"], ("per_pair_form",)),
+    "precision_bf16": (["--precision", "bf16", "--steps", "120"], ()),
+    "learned": (["--workload", "learned", "--steps", "256"], ("per_pair", "batched")),
+}
+
+
+def run_extensions(args) -> dict:
+    """The batched, reduced-precision and learned forms, each measured by its own
+    run of this script on the same GPU (one line each, no CPU baseline, no nested
+    extensions), summarised under the default line so that every form's throughput,
+    roofline, pose check and clocks come from the same command."""
+    out = {}
+    for name, (extra, keys) in EXTENSION_RUNS.items():
+        cmd = [sys.executable, os.path.abspath(__file__), "--no-cpu-baseline", "--no-extensions",
+               "--warmup", str(max(3, args.warmup))] + extra
+        try:
+            r = subprocess.run(cmd, capture_output=True, text=True, timeout=900)
+            d = json.loads(r.stdout.strip().splitlines()[-1])
+        except (subprocess.TimeoutExpired, ValueError, IndexError) as e:
+            out[name] = {"error": f"{type(e).__name__}: {e}"[:300]}
+            continue
+        summ = {k: d.get(k) for k in ("metric", "value", "unit", "ms_per_step", "steps", "e2e", "roofline",
+                                       "alu_roofline", "pose_check", "clocks", "gpu_launches")}
+        summ["config"] = d.get("config")
+        for k in keys:
+            summ[k] = d.get(k)
+        out[name] = summ
+    return out
+
+
+def host_info() -> dict:
+    """Core count and CPU model of the host the CPU baseline ran on."""
+    model = None
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+        for ln in r.stdout.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.TimeoutExpired):
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model}
 
 # ----------------------------------------------------------------------------- batched workload
 BATCH_N = 64
@@ -662,12 +751,14 @@ def native_batch(args):
         plain_ms.append(e0.elapsed_time(e1))
     res_p = [R.parse_result(r) for r in rs]
 
-    def pose_err(Ta, Tb):
-        E = np.linalg.inv(Ta) @ Tb
-        return (float(np.arccos(np.clip((np.trace(E[:3, :3]) - 1) / 2, -1, 1))), float(np.linalg.norm(E[:3, 3])))
-
     d_plain = [pose_err(a["T"], b["T"]) for a, b in zip(res_b, res_p)]
     d_truth = [pose_err(a["T"], p["T_gt"])[0] for a, p in zip(res_b, pairs)]
+    # against the FP64 oracle's alignment of every pair of this batch (seed 0 only)
+    gold = golden("c3_oracle_poses_reduced.json" if args.precision == "bf16" else "c3_oracle_poses.json")
+    d_oracle = None
+    if gold is not None and rank == 0:
+        d_oracle = [pose_err(np.array(gold["pairs"][str(i)]["T"]).reshape(4, 4), r["T"]) for i, r in enumerate(res_b)]
+        d_oracle_pp = [pose_err(np.array(gold["pairs"][str(i)]["T"]).reshape(4, 4), r["T"]) for i, r in enumerate(res_p)]
 
     total_ms, e2e_ms = max_over_ranks([total_ms, e2e_ms], dist, dev)
     if rank != 0:
@@ -699,6 +790,11 @@ def native_batch(args):
                           "ms_per_batch": float(np.median(plain_ms))},
         "pose_check": {"max_vs_per_pair_form_rad": max(d[0] for d in d_plain),
                        "max_vs_per_pair_form_m": max(d[1] for d in d_plain),
+                       "batched_vs_oracle": err_stats(d_oracle) if d_oracle else None,
+                       "per_pair_form_vs_oracle": err_stats(d_oracle_pp) if d_oracle else None,
+                       "oracle": ("stored FP64 oracle poses of every pair (tests/golden/"
+                                  + ("c3_oracle_poses_reduced.json, reduced-precision pyramids)" if args.precision == "bf16"
+                                     else "c3_oracle_poses.json)")) if d_oracle else None,
                        "median_vs_truth_rad": float(np.median(d_truth)), "max_vs_truth_rad": float(np.max(d_truth)),
                        "status": sorted(set(r["status"] for r in res_b))},
         "cpu_baseline": cpu, "clocks": clk, "gpu_launches": args.steps, "wall_s_timed": t_wall,
