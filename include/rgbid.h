@@ -106,6 +106,20 @@ typedef struct {
     long long units;             /* in/out: algorithmic units of the timed launches */
 } rgbid_timing;
 
+/* Where B is warped ("Iterative optimisation": the maps of B warped towards A
+ * are downsampled to the level of the current iteration).
+ * RGBID_WARP_PER_LEVEL warps B's level-l map with K_l at level l (the default).
+ * RGBID_WARP_FULL_RESOLUTION warps B at level 0 for every iteration and reduces
+ * the warped maps to level l by the pyramid's rule, each with its own validity
+ * (a level-l value is the mean of its valid children and is valid when one
+ * child is); a level-l pixel's masks are A's conditions there plus that
+ * validity.  Every iteration then warps all level-0 pixels.  rgbid_align and
+ * rgbid_eval_step take both; the batched form takes the default only. */
+typedef enum {
+    RGBID_WARP_PER_LEVEL = 0,
+    RGBID_WARP_FULL_RESOLUTION = 1
+} rgbid_warp_mode;
+
 /* Alignment schedule and robust-estimation constants. */
 typedef struct {
     int levels;                  /* levels used, coarse to fine (<= pyramid levels) */
@@ -115,7 +129,7 @@ typedef struct {
     int sample_cap;              /* systematic sample size cap, 1..RGBID_MAX_SAMPLES; default 19200 */
     int estimate_nu;             /* 1: bisection for nu per channel; 0: nu = nu0 */
     int min_valid;               /* minimum count of valid residuals (I and W together) for a step */
-    int pad_;
+    int warp_mode;               /* rgbid_warp_mode; default RGBID_WARP_PER_LEVEL */
     double nu0, nu_lo, nu_hi;    /* 5, 2, 10; needs (nu_lo + nu_hi) >= 1.4 (nu_hi - nu_lo) */
     rgbid_timing* timing;        /* optional kernel timing (NULL: none) */
     const int* level_iters;      /* optional DEVICE array of RGBID_MAX_LEVELS ints read by the kernels
@@ -177,7 +191,9 @@ int rgbid_build_pyramid(const float* I0, const float* W0, int pitch0, int width,
  * and T <- exp(xi)^-1 T with the decoupled SE(3) exponential.
  */
 
-/* Workspace bytes needed by rgbid_align / rgbid_eval_step for this reference. */
+/* Workspace bytes needed by rgbid_align / rgbid_eval_step for this reference
+ * (more with RGBID_WARP_FULL_RESOLUTION, whose sweeps take one row per thread
+ * on every level). */
 size_t rgbid_align_workspace_bytes(const rgbid_pyramid* ref, const rgbid_align_params* params);
 
 /* Align `cur` (B) to `ref` (A).  Both pyramids must have the same size,
@@ -206,7 +222,8 @@ int rgbid_align(const rgbid_pyramid* ref, const rgbid_pyramid* cur,
  * with that device current, looks up the array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.
  * Returns RGBID_ERR_WORKSPACE when the reference's finest level needs more
- * scratch than the array holds (about 4 million pixels), RGBID_ERR_CUDA if the
+ * scratch than the array holds (about 4 million pixels; about 1 million with
+ * RGBID_WARP_FULL_RESOLUTION), RGBID_ERR_CUDA if the
  * look-up fails.  Every call shares the one array: calls whose work overlaps on
  * the GPU (other streams, other host threads) race and must be serialised by
  * the caller.  Each call resets the scratch fields that must start at zero. */
@@ -395,6 +412,49 @@ int rgbid_eval_step(const rgbid_pyramid* ref, const rgbid_pyramid* cur, int leve
                     float* r_I, float* r_W, uint8_t* mask_I, uint8_t* mask_W,
                     rgbid_align_result* d_result, void* stream);
 
+/* ---------------------------------------------------------------- covariance
+ * Covariance of a motion estimate ("Dense motion estimation", the paragraph
+ * after the update rule): one more iteration at the final pose, which does not
+ * update it, in which the reference's level 0 {I_A, W_A} is bilateral-filtered
+ * before its gradients are taken; Sigma = H_filt^-1.  The iteration estimates
+ * (mu, sigma, nu) on the systematic sample at that pose like any other; only
+ * the central differences (the Jacobians and the normal weight) read the
+ * filtered planes, while the warp, residuals and masks use the unfiltered
+ * ones.  The filter's parameters are not given by the paper. */
+#define RGBID_BILATERAL_MAX_RADIUS 5
+typedef struct {
+    int radius;                  /* window half-width in pixels, 0..RGBID_BILATERAL_MAX_RADIUS (0: no filtering) */
+    int pad_;
+    double sigma_s;              /* spatial sigma, pixels */
+    double sigma_r_I;            /* range sigma of intensity */
+    double sigma_r_W;            /* range sigma of inverse depth, 1/m */
+} rgbid_bilateral;
+
+/* Defaults: radius 2, sigma_s 1.5 px, sigma_r_I 0.1, sigma_r_W 0.01 1/m. */
+void rgbid_default_bilateral(rgbid_bilateral* f);
+
+/* Workspace bytes of rgbid_covariance: the alignment workspace plus a float
+ * (I, W) plane of the reference's level 0. */
+size_t rgbid_covariance_workspace_bytes(const rgbid_pyramid* ref);
+
+/* The covariance iteration of `cur` (B) against `ref` (A) at pose `T` (16
+ * doubles, host when `T_on_device` is 0, device when 1, e.g. &d_result->T of
+ * the alignment), level 0, with the robust-estimation constants of `params`.
+ * Each output pixel of the filter is the mean of its (2r+1)^2 window inside
+ * the image weighted by exp(-d^2 / 2 sigma_s^2) exp(-(f(p) - f(q))^2 / 2 sigma_r^2);
+ * inverse depth only over valid neighbours, and holes stay holes.
+ * Writes `d_result` (device: T, H = H_filt, g, cost, robust parameters and
+ * counts of that iteration; status RGBID_ERR_DEGENERATE when H_filt is not
+ * positive definite or fewer than params->min_valid residuals are valid) and
+ * `d_sigma` (device, 36 doubles row-major: H_filt^-1 in the twist coordinates
+ * (t, theta) of the update, or zeros when degenerate).
+ * Errors: INVALID_ARG (pyramids and params as rgbid_align; filter values),
+ * WORKSPACE, CUDA. */
+int rgbid_covariance(const rgbid_pyramid* ref, const rgbid_pyramid* cur, const double* T, int T_on_device,
+                     const rgbid_align_params* params, const rgbid_bilateral* filter,
+                     void* workspace, size_t workspace_bytes, rgbid_align_result* d_result,
+                     double* d_sigma, void* stream);
+
 /* Chebyshev series (in tau = (nu - m)/h over [nu_lo, nu_hi], m and h the
  * interval's centre and half-width) of the sample-independent part of the
  * degrees-of-freedom equation ("Error distribution and robust optimisation",
@@ -443,6 +503,56 @@ int rgbid_fuse_keyframe(float* I_kf, float* W_kf, float* C_kf, int pitch_kf,
 int rgbid_init_keyframe(float* I_kf, float* W_kf, float* C_kf, int pitch_kf,
                         const float* I_k, const float* W_k, int pitch_k,
                         int width, int height, void* stream);
+
+/* Fusion or keyframe switch decided on the device: as rgbid_fuse_keyframe with
+ * its pose and sigma_W read from device memory, except that when the device
+ * int *d_switch is non-zero (written by rgbid_keyframe_decide) the keyframe is
+ * re-initialised from frame k as rgbid_init_keyframe does ("Keyframe fusion":
+ * the frame that fails the covisibility test starts the next keyframe).  Lets
+ * a tracking loop be enqueued, or replayed as one CUDA graph, without reading
+ * the decision back.  Errors: INVALID_ARG (as rgbid_fuse_keyframe; d_switch
+ * NULL or misaligned), CUDA. */
+int rgbid_fuse_or_switch_keyframe(float* I_kf, float* W_kf, float* C_kf, int pitch_kf,
+                                  const float* I_k, const float* W_k, int pitch_k,
+                                  int width, int height, rgbid_intrinsics K,
+                                  const double* T_kf_k, const double* sigma_W,
+                                  int fuse_intensity, const int* d_switch, void* stream);
+
+/* ---------------------------------------------------------------- covisibility
+ * Dense covisibility ratio ("Dense frame covisibility ratio"): every pixel of A
+ * with a measurement (S_H: W_A > 0, I_A and W_A finite) is transferred into B
+ * with T_AB = A_T_B (eq. 3d_registration); it is visible (S_V) when it lies in
+ * front of B, its nearest pixel of B, floor(p_B + 1/2), is inside the image and
+ * holds a measurement, and |W_B - w_B| < 3 sigma_W with w_B = 1 / Z_B of the
+ * transferred point (otherwise it is occluded or out of view).  The same is
+ * done from B to A with T_AB^-1, and the ratio is
+ * min(|S_V(A->B)| / |S_H(A)|, |S_V(B->A)| / |S_H(B)|).
+ * Planes are planar float (device, `pitch` elements per row) of equal size,
+ * seen with the same intrinsics K.  `T_AB` (16 doubles) and `sigma_W`
+ * (1 double) are host pointers read during the call (`params_on_device` 0) or
+ * device pointers read by the kernel (1, e.g. &d_result->T and
+ * &d_result->sigma[1] of the alignment).  Writes d_counts[4] (device unsigned
+ * ints, zeroed by the call) = {|S_V(A->B)|, |S_H(A)|, |S_V(B->A)|, |S_H(B)|}
+ * and, when d_ratio is not NULL, the ratio to the device float *d_ratio.
+ * Errors: INVALID_ARG (NULL or misaligned pointers, sizes, intrinsics), CUDA. */
+int rgbid_covisibility(const float* I_A, const float* W_A, int pitch_A,
+                       const float* I_B, const float* W_B, int pitch_B,
+                       int width, int height, rgbid_intrinsics K,
+                       const double* T_AB, const double* sigma_W, int params_on_device,
+                       unsigned int* d_counts, float* d_ratio, void* stream);
+
+/* Keyframe decision of the tracking front-end by covisibility ("Keyframe
+ * fusion": a new keyframe is started when the covisibility ratio of the
+ * current frame with the keyframe falls below a threshold, 0.7 in the paper).
+ * Reads the counts of rgbid_covisibility (keyframe = A, frame k = B), writes
+ * *d_switch = (ratio < threshold) and, when d_ratio is not NULL, the ratio, and
+ * advances the constant-velocity model's poses (device, 16 doubles each):
+ * on a switch T2 <- T_k^-1 T1 (frame k-1 in the new keyframe) and T1 <- I,
+ * else T2 <- T1 and T1 <- T_k.  T_k, T1 and T2 must not alias.
+ * Errors: INVALID_ARG (NULL, misaligned or aliased pointers, threshold
+ * outside [0, 1]), CUDA. */
+int rgbid_keyframe_decide(const unsigned int* d_counts, double threshold, const double* T_k,
+                          double* T1, double* T2, int* d_switch, float* d_ratio, void* stream);
 
 /* ---------------------------------------------------------------- tracking helper
  * Constant-velocity initial guess of the tracking front-end ("Camera

@@ -20,6 +20,7 @@
 // A closing robust_kernel launch (finalize_only) finishes the last sweep of an
 // alignment.
 #include <cooperative_groups.h>
+#include <cuda.h>
 #include <algorithm>
 #include <atomic>
 #include <cstdio>
@@ -53,6 +54,8 @@ struct InitArgs {
 
 struct RobustArgs {
     LevelDev A, B;
+    LevelDev A0, B0;          // level 0 (the warp at full resolution)
+    int full_level;           // > 0: warp at level 0 and reduce to this level (reading R22); 0: warp here
     AlignState* st;
     int s, nsx, nsamp;
     int scale_iters, bisect_steps, estimate_nu;
@@ -71,6 +74,9 @@ struct RobustArgs {
 
 struct SweepArgs {
     LevelDev A, B;
+    LevelDev A0, B0;          // level 0 (the warp at full resolution)
+    int full_level;           // > 0: warp at level 0 and reduce to this level (reading R22); 0: warp here
+    const float2* G;          // optional plane for the reference's gradients (the covariance iteration)
     AlignState* st;
     float* partials;
     float* r_I;
@@ -255,7 +261,7 @@ struct ClusterSum {
     }
 };
 
-template <int PREC, int CL>
+template <int PREC, int CL, bool FULL>
 __global__ void __launch_bounds__(kRobustNT) robust_kernel(RobustArgs a) {
     constexpr int MAXS = (RGBID_MAX_SAMPLES + CL * kRobustNT - 1) / (CL * kRobustNT);
     cg::cluster_group cl = cg::this_cluster();
@@ -271,8 +277,8 @@ __global__ void __launch_bounds__(kRobustNT) robust_kernel(RobustArgs a) {
     __shared__ F2 fin2[kRobustNT / 32][kSlots];
     __shared__ double T_sh[16];
     __shared__ double totd[kSlots];
-    __shared__ float xi_f[6];
-    __shared__ double xi_d[6];
+    __shared__ float xi_f[6], d_f[6];
+    __shared__ double xi_d[6], rho_d[6];
     __shared__ int ok_flag;
     __shared__ RobustParams sh_rob_prev;         // rank 0: the parameters the previous sweep used
     __shared__ int sh_cnt[3];                    // rank 0: iters_done, iters_skipped, status
@@ -364,21 +370,16 @@ __global__ void __launch_bounds__(kRobustNT) robust_kernel(RobustArgs a) {
         R.next();
         if (a.finalize_only) cluster_arrive();   // the launch's only exchange is over
         if (t < 32) {
-            if (lane == 0) {
-                const int nI = (int)tot[kSlotNI], nW = (int)tot[kSlotNW];
-                bool okl = a.update && (nI + nW) >= a.min_valid;
-                if constexpr (PREC == RGBID_PLANES_BF16_F16) {
-                    // reduced-precision planes: the 6x6 solve runs in FP64
-                    double xi[6];
-                    okl = okl && cholesky_solve6_slots(tot, xi);
+            const bool ok_in = a.update && ((int)tot[kSlotNI] + (int)tot[kSlotNW]) >= a.min_valid;
+            if constexpr (PREC == RGBID_PLANES_BF16_F16) {
+                // reduced-precision planes: FP32 factorisation refined to an FP64 solution
+                const bool okl = warp_solve6_refined(tot, ok_in, xi_f, d_f, rho_d, xi_d);
+                if (lane == 0) ok_flag = okl ? 1 : 0;
+            } else if (lane == 0) {
+                float xi[6];
+                const bool okl = ok_in && cholesky_solve6_slots(tot, xi);
 #pragma unroll
-                    for (int i = 0; i < 6; ++i) xi_d[i] = okl ? xi[i] : 0.0;
-                } else {
-                    float xi[6];
-                    okl = okl && cholesky_solve6_slots(tot, xi);
-#pragma unroll
-                    for (int i = 0; i < 6; ++i) xi_f[i] = okl ? xi[i] : 0.f;
-                }
+                for (int i = 0; i < 6; ++i) xi_f[i] = okl ? xi[i] : 0.f;
                 ok_flag = okl ? 1 : 0;
             }
             __syncwarp();
@@ -471,7 +472,19 @@ __global__ void __launch_bounds__(kRobustNT) robust_kernel(RobustArgs a) {
     // ---- systematic sample residuals r(p, 0) (NaN = masked out); the samples of a
     //      thread go through each evaluation stage together so their loads overlap
     float rs[2][MAXS];
-    {
+    if constexpr (FULL) {
+#pragma unroll
+        for (int k = 0; k < MAXS; ++k) {
+            PixelTerms o;
+            o.mI = o.mW = false;
+            if (sa[k].ok) {
+                const Warped wd = warped_at_level<PREC>(a.full_level, a.A0, a.B0, wp, su[k], sv[k]);
+                finish_given<false>(a.A, sa[k], wd.I, wd.vI, wd.W, wd.vW, o);
+            }
+            rs[0][k] = o.mI ? o.rI : __int_as_float(0x7fc00000);
+            rs[1][k] = o.mW ? o.rW : __int_as_float(0x7fc00000);
+        }
+    } else {
         PxW sw[MAXS];
         PxB sb[MAXS];
 #pragma unroll
@@ -647,12 +660,34 @@ __global__ void __launch_bounds__(kRobustNT) robust_kernel(RobustArgs a) {
 }
 
 // ---------------------------------------------------------------- sweep + solve
-template <int PREC, int R>
-__global__ void __launch_bounds__(kSweepNT, 2) sweep_kernel(SweepArgs a) {
+// MODE: kSweepTma, the block's tile of A with a one-pixel halo staged in shared
+// memory by one TMA copy (every level whose size holds the tile box);
+// kSweepPlain, A's taps read straight from global memory (smaller levels);
+// kSweepFull, B warped at level 0 and reduced to this level (reading R22);
+// kSweepGrad, the reference's gradients read from the plane G (the covariance
+// iteration).
+constexpr int kSweepPlain = 0, kSweepFull = 1, kSweepGrad = 2, kSweepTma = 3;
+
+// The TMA tile of A: starts kTmaXOff pixels left of the block (a 16-byte aligned x)
+// and one row above it, kTmaW pixels wide, 8 R + 2 rows high.
+template <int PREC>
+struct TmaTile {
+    static constexpr int kXOff = 16 / Pix<PREC>::kBytes;
+    static constexpr int kW = kTileW + 2 * kXOff;
+};
+
+template <int PREC, int R, int MODE>
+__global__ void __launch_bounds__(kSweepNT, 2) sweep_kernel(SweepArgs a, const __grid_constant__ CUtensorMap tmA) {
+    constexpr bool FULL = MODE == kSweepFull;
+    constexpr bool TMA = MODE == kSweepTma;
     constexpr int kTileH = 8 * R;
+    constexpr int kTW = TmaTile<PREC>::kW, kTH = kTileH + 2;
+    constexpr int kTileBytes = TMA ? kTW * kTH * Pix<PREC>::kBytes : 16;
     __shared__ float red[kSweepNT / 32][kSlots];
     __shared__ WarpPose sh_wp;
     __shared__ RobustParams sh_rob;
+    __shared__ __align__(128) unsigned char tile[kTileBytes];
+    __shared__ __align__(8) unsigned long long tile_bar;
     if (iteration_skipped(a.level_iters, a.level, a.iter)) {
         pdl_wait();
         return;
@@ -664,11 +699,27 @@ __global__ void __launch_bounds__(kSweepNT, 2) sweep_kernel(SweepArgs a) {
     // for all rows are in flight at once
     const int v0 = blockIdx.y * kTileH + warp * R;
     PxA sa[R];
+    if constexpr (TMA) {
+        if (threadIdx.x == 0) {
+            mbar_init(&tile_bar, 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            mbar_arrive_expect_tx(&tile_bar, (uint32_t)kTileBytes);
+            tma_load_2d(tile, &tmA, (int)blockIdx.x * kTileW - TmaTile<PREC>::kXOff, (int)blockIdx.y * kTileH - 1,
+                        &tile_bar);
+        }
+    } else {
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int v = v0 + r;
-        sa[r].ok = false;
-        if (u < a.A.w && v < a.A.h) stage_a<PREC>(a.A, u, v, sa[r]);
+        for (int r = 0; r < R; ++r) {
+            const int v = v0 + r;
+            sa[r].ok = false;
+            if (u < a.A.w && v < a.A.h) {
+                if constexpr (MODE == kSweepGrad) stage_a_grad<PREC>(a.A, a.G, u, v, sa[r]);
+                else stage_a<PREC>(a.A, u, v, sa[r]);
+            }
+        }
     }
     pdl_wait();   // the robust parameters (and pose) of this iteration are complete and visible
     if (threadIdx.x < 16) {
@@ -688,16 +739,60 @@ __global__ void __launch_bounds__(kSweepNT, 2) sweep_kernel(SweepArgs a) {
     const bool wantI = rob.ok[0] != 0, wantW = rob.ok[1] != 0;
     PxW sw[R];
     PxB sb[R];
+    if constexpr (TMA) {
+        // the tile landed long ago in practice; the wait is bounded all the same
+        const long long t0 = clock64();
+        bool landed = true;
+        while (!mbar_try_wait(&tile_bar, 0)) {
+            if (clock64() - t0 > kWaitBudgetCycles) {
+                landed = false;
+                break;
+            }
+        }
+        if (!landed) {
+            if (threadIdx.x == 0) atomicAdd(&a.st->timeouts, 1);
+            // the copy may still be in flight: give it a second bounded wait before the tile is read
+            const long long t1 = clock64();
+            while (!mbar_try_wait(&tile_bar, 0) && clock64() - t1 < kWaitBudgetCycles) {
+            }
+        }
+        // A's taps come from the tile; only the warp's inputs stay live across the B gathers
 #pragma unroll
-    for (int r = 0; r < R; ++r) stage_w(a.A, a.B, wp, u, v0 + r, sa[r], sw[r]);
+        for (int r = 0; r < R; ++r) {
+            const int v = v0 + r;
+            sa[r].ok = false;
+            if (u < a.A.w && v < a.A.h)
+                stage_a_shared<PREC>(a.A, tile, kTW, (warp * R + r + 1) * kTW + lane + TmaTile<PREC>::kXOff, u, v,
+                                     sa[r]);
+            stage_w(a.A, a.B, wp, u, v, sa[r], sw[r]);
+        }
 #pragma unroll
-    for (int r = 0; r < R; ++r) stage_b<PREC>(a.B, sw[r], sb[r]);
+        for (int r = 0; r < R; ++r) stage_b<PREC>(a.B, sw[r], sb[r]);
+    } else if constexpr (!FULL) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) stage_w(a.A, a.B, wp, u, v0 + r, sa[r], sw[r]);
+#pragma unroll
+        for (int r = 0; r < R; ++r) stage_b<PREC>(a.B, sw[r], sb[r]);
+    }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int v = v0 + r;
         if (u >= a.A.w || v >= a.A.h) continue;
         PixelTerms o;
-        finish<true>(a.A, wp, sa[r], sw[r], sb[r], o);
+        if constexpr (FULL) {
+            o.mI = o.mW = false;
+            o.rI = o.rW = 0.f;
+            if (sa[r].ok) {
+                const Warped wd = warped_at_level<PREC>(a.full_level, a.A0, a.B0, wp, u, v);
+                finish_given<true>(a.A, sa[r], wd.I, wd.vI, wd.W, wd.vW, o);
+            }
+        } else if constexpr (TMA) {
+            PxA sr;   // re-read from the tile rather than kept in registers across the gathers
+            stage_a_shared<PREC>(a.A, tile, kTW, (warp * R + r + 1) * kTW + lane + TmaTile<PREC>::kXOff, u, v, sr);
+            finish<true>(a.A, wp, sr, sw[r], sb[r], o);
+        } else {
+            finish<true>(a.A, wp, sa[r], sw[r], sb[r], o);
+        }
         if (a.r_I) {
             const int oi = v * a.A.w + u;
             a.r_I[oi] = o.mI ? o.rI : 0.f;
@@ -785,16 +880,18 @@ static int sample_stride(int w, int h, int cap) {
 }
 
 static int sweep_rows(int w, int h) { return (long long)w * h >= kSweepWidePixels ? 4 : 1; }
-static int sweep_blocks(int w, int h) {
-    const int th = 8 * sweep_rows(w, h);
+// Blocks of a sweep over a w x h level; `one_row`: the sweeps of the full-resolution
+// warp and of the covariance iteration, which take one row per thread on every level.
+static int sweep_blocks(int w, int h, bool one_row) {
+    const int th = 8 * (one_row ? 1 : sweep_rows(w, h));
     return ((w + kTileW - 1) / kTileW) * ((h + th - 1) / th);
 }
 
 // The block partials of the largest sweep over the levels of `ref`.
-static size_t workspace_bytes_for(const rgbid_pyramid& ref) {
+static size_t workspace_bytes_for(const rgbid_pyramid& ref, bool one_row) {
     int nb = 1;
     for (int l = 0; l < ref.levels && l < RGBID_MAX_LEVELS; ++l)
-        nb = std::max(nb, sweep_blocks(ref.lv[l].width, ref.lv[l].height));
+        nb = std::max(nb, sweep_blocks(ref.lv[l].width, ref.lv[l].height, one_row));
     return align_up(sizeof(AlignState), 256) + align_up((size_t)nb * kSlots * sizeof(float2), 256);
 }
 
@@ -807,6 +904,7 @@ static int check_pyramids(const rgbid_pyramid* ref, const rgbid_pyramid* cur, co
     const uintptr_t px_bytes = ref->precision == RGBID_PLANES_F32 ? 8u : 4u;   // one interleaved (I, W) pixel
     if (p->level_iters && misaligned(p->level_iters, 4)) return RGBID_ERR_INVALID_ARG;
     if (p->sample_cap < 1 || p->sample_cap > RGBID_MAX_SAMPLES) return RGBID_ERR_INVALID_ARG;
+    if (p->warp_mode != RGBID_WARP_PER_LEVEL && p->warp_mode != RGBID_WARP_FULL_RESOLUTION) return RGBID_ERR_INVALID_ARG;
     if (p->scale_iters < 0 || p->bisect_steps < 0 || p->bisect_steps > 60) return RGBID_ERR_INVALID_ARG;
     if (!(p->nu_lo > 0.0) || !(p->nu_hi > p->nu_lo) || !(p->nu0 > 0.0)) return RGBID_ERR_INVALID_ARG;
     // the Chebyshev form of the robustness equation needs alpha_min = (lo + hi)/(hi - lo) >= 1.4
@@ -825,10 +923,11 @@ static int check_pyramids(const rgbid_pyramid* ref, const rgbid_pyramid* cur, co
     return RGBID_OK;
 }
 
-template <int PREC, int CL>
+template <int PREC, int CL, bool FULL>
 static cudaError_t launch_robust_cl(const RobustArgs& ra, cudaStream_t stream) {
     if (CL > 8) {
-        cudaError_t e = cudaFuncSetAttribute(robust_kernel<PREC, CL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaError_t e =
+            cudaFuncSetAttribute(robust_kernel<PREC, CL, FULL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return e;
     }
     cudaLaunchConfig_t cfg = {};
@@ -845,7 +944,7 @@ static cudaError_t launch_robust_cl(const RobustArgs& ra, cudaStream_t stream) {
     attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 2;
-    return cudaLaunchKernelEx(&cfg, robust_kernel<PREC, CL>, ra);
+    return cudaLaunchKernelEx(&cfg, robust_kernel<PREC, CL, FULL>, ra);
 }
 
 // 16-CTA clusters (non-portable) where the device can schedule them, else 8.
@@ -858,7 +957,7 @@ static cudaError_t launch_robust(const RobustArgs& ra, cudaStream_t stream) {
     int cl = (dev >= 0 && dev < 64) ? cached[dev] : 0;
     if (cl == 0) {
         cl = 8;
-        if (cudaFuncSetAttribute(robust_kernel<PREC, 16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+        if (cudaFuncSetAttribute(robust_kernel<PREC, 16, false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
             cudaSuccess) {
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(16, 1, 1);
@@ -871,19 +970,68 @@ static cudaError_t launch_robust(const RobustArgs& ra, cudaStream_t stream) {
             cfg.attrs = attr;
             cfg.numAttrs = 1;
             int nclusters = 0;
-            if (cudaOccupancyMaxActiveClusters(&nclusters, robust_kernel<PREC, 16>, &cfg) == cudaSuccess &&
+            if (cudaOccupancyMaxActiveClusters(&nclusters, robust_kernel<PREC, 16, false>, &cfg) == cudaSuccess &&
                 nclusters > 0)
                 cl = 16;
         }
         (void)cudaGetLastError();
         if (dev >= 0 && dev < 64) cached[dev] = cl;
     }
-    return cl == 16 ? launch_robust_cl<PREC, 16>(ra, stream) : launch_robust_cl<PREC, 8>(ra, stream);
+    if (ra.full_level > 0)
+        return cl == 16 ? launch_robust_cl<PREC, 16, true>(ra, stream) : launch_robust_cl<PREC, 8, true>(ra, stream);
+    return cl == 16 ? launch_robust_cl<PREC, 16, false>(ra, stream) : launch_robust_cl<PREC, 8, false>(ra, stream);
+}
+
+// cuTensorMapEncodeTiled, looked up once through the runtime (no link to the driver library).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled_fn() {
+    static std::atomic<EncodeTiledFn> fn{nullptr};
+    EncodeTiledFn f = fn.load(std::memory_order_acquire);
+    if (!f) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess && p) {
+            f = reinterpret_cast<EncodeTiledFn>(p);
+            fn.store(f, std::memory_order_release);
+        } else {
+            (void)cudaGetLastError();
+        }
+    }
+    return f;
+}
+
+// The tensor map of a level of A for the sweep's tile (rows of pitch * pixel
+// bytes, a multiple of 16; the box of TmaTile<PREC> x (8 R + 2)).  Returns false
+// when the level is smaller than the box (the sweep then reads A directly).
+template <int PREC>
+static bool encode_level_map(CUtensorMap* m, const LevelDev& A, int R, bool* failed) {
+    *failed = false;
+    const uint32_t bw = (uint32_t)TmaTile<PREC>::kW, bh = (uint32_t)(8 * R + 2);
+    if ((uint32_t)A.w < bw || (uint32_t)A.h < bh) return false;
+    EncodeTiledFn fn = encode_tiled_fn();
+    if (!fn) {
+        *failed = true;
+        return false;
+    }
+    const cuuint64_t gdim[2] = {(cuuint64_t)A.w, (cuuint64_t)A.h};
+    const cuuint64_t gstride[1] = {(cuuint64_t)A.pitch * Pix<PREC>::kBytes};
+    const cuuint32_t box[2] = {bw, bh};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = fn(m, Pix<PREC>::kBytes == 8 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32,
+                          2, const_cast<void*>(A.IW), gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    *failed = r != CUDA_SUCCESS;
+    return r == CUDA_SUCCESS;
 }
 
 template <int PREC>
 static cudaError_t launch_sweep(const SweepArgs& sa, cudaStream_t stream) {
-    const int R = sweep_rows(sa.A.w, sa.A.h);
+    const int R = (sa.full_level > 0 || sa.G) ? 1 : sweep_rows(sa.A.w, sa.A.h);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((sa.A.w + kTileW - 1) / kTileW, (sa.A.h + 8 * R - 1) / (8 * R), 1);
     cfg.blockDim = dim3(kSweepNT, 1, 1);
@@ -894,7 +1042,18 @@ static cudaError_t launch_sweep(const SweepArgs& sa, cudaStream_t stream) {
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return R == 4 ? cudaLaunchKernelEx(&cfg, sweep_kernel<PREC, 4>, sa) : cudaLaunchKernelEx(&cfg, sweep_kernel<PREC, 1>, sa);
+    CUtensorMap tm;
+    memset(&tm, 0, sizeof(tm));
+    if (sa.G) return cudaLaunchKernelEx(&cfg, sweep_kernel<PREC, 1, kSweepGrad>, sa, tm);
+    if (sa.full_level > 0) return cudaLaunchKernelEx(&cfg, sweep_kernel<PREC, 1, kSweepFull>, sa, tm);
+    bool failed = false;
+    const bool tma = encode_level_map<PREC>(&tm, sa.A, R, &failed);
+    if (failed) return cudaErrorInvalidValue;
+    if (tma)
+        return R == 4 ? cudaLaunchKernelEx(&cfg, sweep_kernel<PREC, 4, kSweepTma>, sa, tm)
+                      : cudaLaunchKernelEx(&cfg, sweep_kernel<PREC, 1, kSweepTma>, sa, tm);
+    return R == 4 ? cudaLaunchKernelEx(&cfg, sweep_kernel<PREC, 4, kSweepPlain>, sa, tm)
+                  : cudaLaunchKernelEx(&cfg, sweep_kernel<PREC, 1, kSweepPlain>, sa, tm);
 }
 
 static cudaError_t launch_robust_any(int prec, const RobustArgs& ra, cudaStream_t s) {
@@ -909,6 +1068,9 @@ static RobustArgs robust_args(const rgbid_pyramid* ref, const rgbid_pyramid* cur
     RobustArgs ra;
     ra.A = level_dev(ref->lv[l]);
     ra.B = level_dev(cur->lv[l]);
+    ra.A0 = level_dev(ref->lv[0]);
+    ra.B0 = level_dev(cur->lv[0]);
+    ra.full_level = p->warp_mode == RGBID_WARP_FULL_RESOLUTION ? l : 0;
     ra.st = st;
     ra.s = sample_stride(ra.A.w, ra.A.h, p->sample_cap);
     ra.nsx = (ra.A.w + ra.s - 1) / ra.s;
@@ -936,9 +1098,8 @@ static RobustArgs robust_args(const rgbid_pyramid* ref, const rgbid_pyramid* cur
 using namespace rgbid;
 
 extern "C" size_t rgbid_align_workspace_bytes(const rgbid_pyramid* ref, const rgbid_align_params* params) {
-    (void)params;
     if (!ref || ref->levels < 1 || ref->levels > RGBID_MAX_LEVELS) return 0;
-    return workspace_bytes_for(*ref);
+    return workspace_bytes_for(*ref, params && params->warp_mode == RGBID_WARP_FULL_RESOLUTION);
 }
 
 extern "C" int rgbid_align(const rgbid_pyramid* ref, const rgbid_pyramid* cur, const double* T_init, int T_init_on_device,
@@ -976,6 +1137,9 @@ extern "C" int rgbid_align(const rgbid_pyramid* ref, const rgbid_pyramid* cur, c
         memset(&sa, 0, sizeof(sa));
         sa.A = ra.A;
         sa.B = ra.B;
+        sa.A0 = ra.A0;
+        sa.B0 = ra.B0;
+        sa.full_level = ra.full_level;
         sa.st = st;
         sa.partials = partials;
         sa.level_iters = params->level_iters;
@@ -1013,30 +1177,25 @@ extern "C" int rgbid_align(const rgbid_pyramid* ref, const rgbid_pyramid* cur, c
     return RGBID_OK;
 }
 
-extern "C" int rgbid_eval_step(const rgbid_pyramid* ref, const rgbid_pyramid* cur, int level, const double* T,
-                               const double* robust, const rgbid_align_params* params, void* workspace,
-                               size_t workspace_bytes, float* r_I, float* r_W, uint8_t* mask_I, uint8_t* mask_W,
-                               rgbid_align_result* d_result, void* stream_) {
-    if (!params || !T || !d_result) return RGBID_ERR_INVALID_ARG;
-    rgbid_align_params p = *params;
-    if (level < 0 || level >= RGBID_MAX_LEVELS) return RGBID_ERR_INVALID_ARG;
-    if (p.levels < level + 1) p.levels = level + 1;
-    int st_chk = check_pyramids(ref, cur, &p);
-    if (st_chk != RGBID_OK) return st_chk;
-    const bool any_out = r_I || r_W || mask_I || mask_W;
-    if (any_out && !(r_I && r_W && mask_I && mask_W)) return RGBID_ERR_INVALID_ARG;
-    if (misaligned(d_result, 8) || misaligned(r_I, 4) || misaligned(r_W, 4)) return RGBID_ERR_INVALID_ARG;
-    if (!workspace || ((uintptr_t)workspace & 255u) || workspace_bytes < rgbid_align_workspace_bytes(ref, &p))
-        return RGBID_ERR_WORKSPACE;
-    cudaStream_t stream = (cudaStream_t)stream_;
+namespace rgbid {
+// One step at a fixed pose, no update: initialisation, the robust-scale kernel
+// (unless the robust parameters are given), one sweep and the closing reduction
+// into the result record.  The pose is host or device memory; `G` (optional,
+// level `level` only) supplies the reference's gradients (the covariance
+// iteration).  Arguments are checked by the callers.
+int enqueue_eval_step(const rgbid_pyramid* ref, const rgbid_pyramid* cur, int level, const double* T, int T_on_device,
+                      const double* robust, const rgbid_align_params& p, void* workspace, float* r_I, float* r_W,
+                      uint8_t* mask_I, uint8_t* mask_W, const float2* G, rgbid_align_result* d_result,
+                      cudaStream_t stream) {
     AlignState* st = (AlignState*)workspace;
     float* partials = (float*)((char*)workspace + align_up(sizeof(AlignState), 256));
-
     InitArgs ia;
     memset(&ia, 0, sizeof(ia));
     ia.st = st;
     ia.res = d_result;
-    for (int i = 0; i < 16; ++i) ia.T_val[i] = T[i];
+    if (T_on_device) ia.T_dev = T;
+    else
+        for (int i = 0; i < 16; ++i) ia.T_val[i] = T[i];
     if (robust) {
         ia.use_fixed = 1;
         for (int i = 0; i < 6; ++i) ia.fixed[i] = (float)robust[i];
@@ -1052,6 +1211,10 @@ extern "C" int rgbid_eval_step(const rgbid_pyramid* ref, const rgbid_pyramid* cu
     memset(&sa, 0, sizeof(sa));
     sa.A = ra.A;
     sa.B = ra.B;
+    sa.A0 = ra.A0;
+    sa.B0 = ra.B0;
+    sa.full_level = ra.full_level;
+    sa.G = G;
     sa.st = st;
     sa.partials = partials;
     sa.r_I = r_I;
@@ -1063,6 +1226,31 @@ extern "C" int rgbid_eval_step(const rgbid_pyramid* ref, const rgbid_pyramid* cu
     ra.finalize_only = 1;
     if (launch_robust_any(ref->precision, ra, stream) != cudaSuccess) return RGBID_ERR_CUDA;
     return RGBID_OK;
+}
+
+size_t align_workspace_bytes(const rgbid_pyramid& ref) { return workspace_bytes_for(ref, true); }
+int check_align_inputs(const rgbid_pyramid* ref, const rgbid_pyramid* cur, const rgbid_align_params* p) {
+    return check_pyramids(ref, cur, p);
+}
+}  // namespace rgbid
+
+extern "C" int rgbid_eval_step(const rgbid_pyramid* ref, const rgbid_pyramid* cur, int level, const double* T,
+                               const double* robust, const rgbid_align_params* params, void* workspace,
+                               size_t workspace_bytes, float* r_I, float* r_W, uint8_t* mask_I, uint8_t* mask_W,
+                               rgbid_align_result* d_result, void* stream_) {
+    if (!params || !T || !d_result) return RGBID_ERR_INVALID_ARG;
+    rgbid_align_params p = *params;
+    if (level < 0 || level >= RGBID_MAX_LEVELS) return RGBID_ERR_INVALID_ARG;
+    if (p.levels < level + 1) p.levels = level + 1;
+    int st_chk = check_pyramids(ref, cur, &p);
+    if (st_chk != RGBID_OK) return st_chk;
+    const bool any_out = r_I || r_W || mask_I || mask_W;
+    if (any_out && !(r_I && r_W && mask_I && mask_W)) return RGBID_ERR_INVALID_ARG;
+    if (misaligned(d_result, 8) || misaligned(r_I, 4) || misaligned(r_W, 4)) return RGBID_ERR_INVALID_ARG;
+    if (!workspace || ((uintptr_t)workspace & 255u) || workspace_bytes < rgbid_align_workspace_bytes(ref, &p))
+        return RGBID_ERR_WORKSPACE;
+    return enqueue_eval_step(ref, cur, level, T, 0, robust, p, workspace, r_I, r_W, mask_I, mask_W, nullptr, d_result,
+                             (cudaStream_t)stream_);
 }
 
 // ---------------------------------------------------------------- allocation-free alignment

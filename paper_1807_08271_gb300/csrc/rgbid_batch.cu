@@ -79,6 +79,9 @@ int check_params(const rgbid_align_params* p) {
     if (!(p->nu_lo > 0.0) || !(p->nu_hi > p->nu_lo) || !(p->nu0 > 0.0) || !(p->nu_hi < 1e6)) return RGBID_ERR_INVALID_ARG;
     // the Chebyshev form of the robustness equation needs (lo + hi)/(hi - lo) >= 1.4
     if (p->nu_lo + p->nu_hi < 1.4 * (p->nu_hi - p->nu_lo)) return RGBID_ERR_UNSUPPORTED;
+    // the batched kernel warps B at each level only
+    if (p->warp_mode == RGBID_WARP_FULL_RESOLUTION) return RGBID_ERR_UNSUPPORTED;
+    if (p->warp_mode != RGBID_WARP_PER_LEVEL) return RGBID_ERR_INVALID_ARG;
     return RGBID_OK;
 }
 

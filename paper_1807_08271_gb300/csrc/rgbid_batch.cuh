@@ -286,8 +286,8 @@ __global__ void __launch_bounds__(kBatchNT, 2) batch_align_kernel(BatchArgs a) {
     __shared__ float nuF[2][kNuSeries];
     __shared__ float sh_g[kNuGTerms];
     __shared__ float nu_out[2];
-    __shared__ float xi_f[6];
-    __shared__ double xi_d[6];
+    __shared__ float xi_f[6], d_f[6];
+    __shared__ double xi_d[6], rho_d[6];
     __shared__ int ok_flag, n_done, n_skipped, j_status;
     __shared__ int failed;
     __shared__ unsigned int job_idx[2];
@@ -652,17 +652,15 @@ __global__ void __launch_bounds__(kBatchNT, 2) batch_align_kernel(BatchArgs a) {
 
                 // ======== solve and update (warp 0 of every CTA, identical inputs)
                 if (warp == 0) {
+                    const bool ok_in = ((int)tot[kSlotNI] + (int)tot[kSlotNW]) >= a.min_valid;
+                    bool okr = false;
+                    if constexpr (PREC == RGBID_PLANES_BF16_F16)
+                        okr = warp_solve6_refined(tot, ok_in, xi_f, d_f, rho_d, xi_d);
                     if (lane == 0) {
-                        const int nI = (int)tot[kSlotNI], nW = (int)tot[kSlotNW];
-                        bool okl = (nI + nW) >= a.min_valid;
-                        if constexpr (PREC == RGBID_PLANES_BF16_F16) {
-                            double xi[6];
-                            okl = okl && cholesky_solve6_slots(tot, xi);
-#pragma unroll
-                            for (int i = 0; i < 6; ++i) xi_d[i] = okl ? xi[i] : 0.0;
-                        } else {
+                        bool okl = okr;
+                        if constexpr (PREC != RGBID_PLANES_BF16_F16) {
                             float xi[6];
-                            okl = okl && cholesky_solve6_slots(tot, xi);
+                            okl = ok_in && cholesky_solve6_slots(tot, xi);
 #pragma unroll
                             for (int i = 0; i < 6; ++i) xi_f[i] = okl ? xi[i] : 0.f;
                         }

@@ -66,18 +66,29 @@ struct Pix;
 
 template <>
 struct Pix<RGBID_PLANES_F32> {
+    static constexpr int kBytes = 8;
     static __device__ __forceinline__ float2 load(const void* base, int idx) {
         return __ldg(reinterpret_cast<const float2*>(base) + idx);
+    }
+    // a pixel of a tile staged in shared memory
+    static __device__ __forceinline__ float2 shared(const void* base, int idx) {
+        return reinterpret_cast<const float2*>(base)[idx];
     }
 };
 
 template <>
 struct Pix<RGBID_PLANES_BF16_F16> {
-    static __device__ __forceinline__ float2 load(const void* base, int idx) {
-        uint32_t raw = __ldg(reinterpret_cast<const unsigned int*>(base) + idx);
+    static constexpr int kBytes = 4;
+    static __device__ __forceinline__ float2 unpack(uint32_t raw) {
         __nv_bfloat16 i = __ushort_as_bfloat16((unsigned short)(raw & 0xffffu));
         __half w = __ushort_as_half((unsigned short)(raw >> 16));
         return make_float2(__bfloat162float(i), __half2float(w));
+    }
+    static __device__ __forceinline__ float2 load(const void* base, int idx) {
+        return unpack(__ldg(reinterpret_cast<const unsigned int*>(base) + idx));
+    }
+    static __device__ __forceinline__ float2 shared(const void* base, int idx) {
+        return unpack(reinterpret_cast<const unsigned int*>(base)[idx]);
     }
 };
 
@@ -126,6 +137,40 @@ __device__ __forceinline__ void stage_a(const LevelDev& A, int u, int v, PxA& s)
     s.b = ((float)v - A.cy) * A.ify;
 }
 
+// stage_a from a tile of A staged in shared memory: `i` is the pixel's index in the
+// tile, `tw` the tile's row length in pixels.
+template <int PREC>
+__device__ __forceinline__ void stage_a_shared(const LevelDev& A, const void* tile, int tw, int i, int u, int v,
+                                               PxA& s) {
+    s.ok = !(u < 1 || v < 1 || u > A.w - 2 || v > A.h - 2);
+    if (!s.ok) return;
+    s.c = Pix<PREC>::shared(tile, i);
+    s.nl = Pix<PREC>::shared(tile, i - 1);
+    s.nr = Pix<PREC>::shared(tile, i + 1);
+    s.nu = Pix<PREC>::shared(tile, i - tw);
+    s.nd = Pix<PREC>::shared(tile, i + tw);
+    s.a = ((float)u - A.cx) * A.ifx;
+    s.b = ((float)v - A.cy) * A.ify;
+}
+
+// stage_a with the neighbours (the central differences' taps) read from a float
+// (I, W) plane G of A's size and pitch instead of A itself: the covariance
+// iteration takes the gradients of the bilateral-filtered reference there, while
+// the centre value (the warp, the residuals) stays A's.  G keeps A's holes.
+template <int PREC>
+__device__ __forceinline__ void stage_a_grad(const LevelDev& A, const float2* G, int u, int v, PxA& s) {
+    s.ok = !(u < 1 || v < 1 || u > A.w - 2 || v > A.h - 2);
+    if (!s.ok) return;
+    const int idx = v * A.pitch + u;
+    s.c = Pix<PREC>::load(A.IW, idx);
+    s.nl = __ldg(G + idx - 1);
+    s.nr = __ldg(G + idx + 1);
+    s.nu = __ldg(G + idx - A.pitch);
+    s.nd = __ldg(G + idx + A.pitch);
+    s.a = ((float)u - A.cx) * A.ifx;
+    s.b = ((float)v - A.cy) * A.ify;
+}
+
 __device__ __forceinline__ void stage_w(const LevelDev& A, const LevelDev& B, const WarpPose& wp, int u, int v,
                                         const PxA& s, PxW& w) {
     w.ok = false;
@@ -158,6 +203,46 @@ __device__ __forceinline__ void stage_b(const LevelDev& B, const PxW& w, PxB& t)
     t.t10 = Pix<PREC>::load(B.IW, w.bi + 1);
     t.t01 = Pix<PREC>::load(B.IW, w.bi + B.pitch);
     t.t11 = Pix<PREC>::load(B.IW, w.bi + B.pitch + 1);
+}
+
+// Jacobians (eq. DeltaX with the gradient terms of eqs. res_int / res_depth) and
+// the normal weight lambda_n of a pixel of A whose masks are decided; W_B^gamma
+// enters the inverse-depth row.
+__device__ __forceinline__ void pixel_jacobians(const LevelDev& A, const PxA& s, bool okW, float WBw, PixelTerms& o) {
+    const float WA = s.c.y, a = s.a, b = s.b;
+    // g~_I = grad I_A (K - p e_z^T) = (gx fx, gy fy, -(gx fx a + gy fy b))
+    const float gIx = 0.5f * (s.nr.x - s.nl.x) * A.fx;
+    const float gIy = 0.5f * (s.nd.x - s.nu.x) * A.fy;
+    const float gIz = -fmaf(gIx, a, gIy * b);
+    // J_I = (W_A g~_I, q x g~_I), q = (a, b, 1)
+    o.JI[0] = WA * gIx;
+    o.JI[1] = WA * gIy;
+    o.JI[2] = WA * gIz;
+    o.JI[3] = fmaf(b, gIz, -gIy);
+    o.JI[4] = fmaf(-a, gIz, gIx);
+    o.JI[5] = fmaf(a, gIy, -b * gIx);
+    if (okW) {
+        const float gWx = 0.5f * (s.nr.y - s.nl.y) * A.fx;
+        const float gWy = 0.5f * (s.nd.y - s.nu.y) * A.fy;
+        const float gWz0 = -fmaf(gWx, a, gWy * b);
+        const float gWz = gWz0 + WBw;      // + W_B^gamma e_z
+        o.JW[0] = WA * gWx;
+        o.JW[1] = WA * gWy;
+        o.JW[2] = WA * gWz;
+        o.JW[3] = fmaf(b, gWz, -gWy);
+        o.JW[4] = fmaf(-a, gWz, gWx);
+        o.JW[5] = fmaf(a, gWy, -b * gWx);
+        // lambda_n = 1 / (|n_u| |q|), n_u = g~_W / W_A + e_z  (n_u . q = 1)
+        const float iW = 1.f / WA;
+        const float nx = gWx * iW, ny = gWy * iW, nz = fmaf(gWz0, iW, 1.f);
+        const float nn = fmaf(nx, nx, fmaf(ny, ny, nz * nz));
+        const float qq = fmaf(a, a, fmaf(b, b, 1.f));
+        o.lam = rsqrtf(nn * qq);
+    } else {
+        o.lam = 0.f;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) o.JW[k] = 0.f;
+    }
 }
 
 template <bool WANT_J>
@@ -194,39 +279,118 @@ __device__ __forceinline__ void finish(const LevelDev& A, const WarpPose& wp, co
     }
     o.mW = okW;
     if (!WANT_J) return;
+    pixel_jacobians(A, s, okW, WBw, o);
+}
 
-    // g~_I = grad I_A (K - p e_z^T) = (gx fx, gy fy, -(gx fx a + gy fy b))
-    const float gIx = 0.5f * (s.nr.x - s.nl.x) * A.fx;
-    const float gIy = 0.5f * (s.nd.x - s.nu.x) * A.fy;
-    const float gIz = -fmaf(gIx, a, gIy * b);
-    // J_I = (W_A g~_I, q x g~_I), q = (a, b, 1)
-    o.JI[0] = WA * gIx;
-    o.JI[1] = WA * gIy;
-    o.JI[2] = WA * gIz;
-    o.JI[3] = fmaf(b, gIz, -gIy);
-    o.JI[4] = fmaf(-a, gIz, gIx);
-    o.JI[5] = fmaf(a, gIy, -b * gIx);
-    if (okW) {
-        const float gWx = 0.5f * (s.nr.y - s.nl.y) * A.fx;
-        const float gWy = 0.5f * (s.nd.y - s.nu.y) * A.fy;
-        const float gWz0 = -fmaf(gWx, a, gWy * b);
-        const float gWz = gWz0 + WBw;      // + W_B^gamma e_z
-        o.JW[0] = WA * gWx;
-        o.JW[1] = WA * gWy;
-        o.JW[2] = WA * gWz;
-        o.JW[3] = fmaf(b, gWz, -gWy);
-        o.JW[4] = fmaf(-a, gWz, gWx);
-        o.JW[5] = fmaf(a, gWy, -b * gWx);
-        // lambda_n = 1 / (|n_u| |q|), n_u = g~_W / W_A + e_z  (n_u . q = 1)
-        const float iW = 1.f / WA;
-        const float nx = gWx * iW, ny = gWy * iW, nz = fmaf(gWz0, iW, 1.f);
-        const float nn = fmaf(nx, nx, fmaf(ny, ny, nz * nz));
-        const float qq = fmaf(a, a, fmaf(b, b, 1.f));
-        o.lam = rsqrtf(nn * qq);
+// The same residuals and Jacobians from B's warped values given directly (the
+// warp at full resolution, reading R22): mask_I needs A's measurement, the
+// interior and the warped intensity's validity; mask_W adds the warped inverse
+// depth's validity and valid neighbours for grad W.
+template <bool WANT_J>
+__device__ __forceinline__ void finish_given(const LevelDev& A, const PxA& s, float IBw, bool vI, float WBw, bool vW,
+                                             PixelTerms& o) {
+    o.mI = false;
+    o.mW = false;
+    o.rI = 0.f;
+    o.rW = 0.f;
+    const float WA = s.c.y;
+    if (!s.ok || !(WA > 0.f) || !vI) return;
+    o.mI = true;
+    o.rI = IBw - s.c.x;
+    const bool okW = vW && (s.nl.y > 0.f) && (s.nr.y > 0.f) && (s.nu.y > 0.f) && (s.nd.y > 0.f);
+    if (okW) o.rW = WBw - WA;
+    o.mW = okW;
+    if (!WANT_J) return;
+    pixel_jacobians(A, s, okW, WBw, o);
+}
+
+// ---------------------------------------------------------------- warp at full resolution (reading R22)
+// B's maps warped towards A at a level-0 pixel p0, or reduced to a coarser level.
+struct Warped {
+    float I, W;
+    bool vI, vW;
+};
+
+// One level-0 pixel: I_B(p_B) and the transferred inverse depth W_B^gamma, valid
+// when A has a measurement at p0, p_B lies in front of B and is bilinear-valid
+// (the intensity), and also has four valid W_B taps and a positive transferred
+// depth (the inverse depth).  No interior condition: gradients are not taken here.
+template <int PREC>
+__device__ __forceinline__ Warped warp_leaf(const LevelDev& A0, const LevelDev& B0, const WarpPose& wp, int u0,
+                                            int v0) {
+    Warped r{0.f, 0.f, false, false};
+    PxA s;
+    s.ok = true;
+    s.c = Pix<PREC>::load(A0.IW, v0 * A0.pitch + u0);
+    s.a = ((float)u0 - A0.cx) * A0.ifx;
+    s.b = ((float)v0 - A0.cy) * A0.ify;
+    PxW w;
+    stage_w(A0, B0, wp, u0, v0, s, w);
+    if (!w.ok) return r;
+    PxB t;
+    stage_b<PREC>(B0, w, t);
+    const float itop = fmaf(w.ax, t.t10.x - t.t00.x, t.t00.x);
+    const float ibot = fmaf(w.ax, t.t11.x - t.t01.x, t.t01.x);
+    r.I = fmaf(w.ay, ibot - itop, itop);
+    r.vI = true;
+    if ((t.t00.y > 0.f) && (t.t10.y > 0.f) && (t.t01.y > 0.f) && (t.t11.y > 0.f)) {
+        const float wtop = fmaf(w.ax, t.t10.y - t.t00.y, t.t00.y);
+        const float wbot = fmaf(w.ax, t.t11.y - t.t01.y, t.t01.y);
+        const float WBp = fmaf(w.ay, wbot - wtop, wtop);
+        const float qbx = s.a + w.du * A0.ifx;
+        const float qby = s.b + w.dv * A0.ify;
+        const float den = fmaf(wp.R2[0], qbx, fmaf(wp.R2[1], qby, wp.R2[2])) + wp.tz * WBp;
+        if (den > 0.f) {
+            r.W = WBp / den;
+            r.vW = true;
+        }
+    }
+    return r;
+}
+
+// Level-L pixel (u, v): the pyramid's rule applied to the warped maps, each with
+// its own validity: the mean of the valid children in the order
+// ((top-left + top-right) + (bottom-left + bottom-right)), valid when one child
+// is.  The children are visited in a loop, so the code grows linearly in L.
+template <int PREC, int L>
+__device__ __forceinline__ Warped warped_down(const LevelDev& A0, const LevelDev& B0, const WarpPose& wp, int u,
+                                              int v) {
+    if constexpr (L == 0) {
+        return warp_leaf<PREC>(A0, B0, wp, u, v);
     } else {
-        o.lam = 0.f;
-#pragma unroll
-        for (int k = 0; k < 6; ++k) o.JW[k] = 0.f;
+        float I0 = 0.f, I1 = 0.f, I2 = 0.f, I3 = 0.f, W0 = 0.f, W1 = 0.f, W2 = 0.f, W3 = 0.f;
+        unsigned mI = 0u, mW = 0u;
+#pragma unroll 1
+        for (int c = 0; c < 4; ++c) {
+            const Warped k = warped_down<PREC, L - 1>(A0, B0, wp, 2 * u + (c & 1), 2 * v + (c >> 1));
+            const float ki = k.vI ? k.I : 0.f, kw = k.vW ? k.W : 0.f;
+            if (c == 0) { I0 = ki; W0 = kw; }
+            else if (c == 1) { I1 = ki; W1 = kw; }
+            else if (c == 2) { I2 = ki; W2 = kw; }
+            else { I3 = ki; W3 = kw; }
+            mI |= (k.vI ? 1u : 0u) << c;
+            mW |= (k.vW ? 1u : 0u) << c;
+        }
+        const int nI = __popc(mI), nW = __popc(mW);
+        Warped r;
+        r.vI = nI > 0;
+        r.vW = nW > 0;
+        r.I = nI > 0 ? ((I0 + I1) + (I2 + I3)) / (float)nI : 0.f;
+        r.W = nW > 0 ? ((W0 + W1) + (W2 + W3)) / (float)nW : 0.f;
+        return r;
+    }
+}
+
+template <int PREC>
+__device__ __forceinline__ Warped warped_at_level(int L, const LevelDev& A0, const LevelDev& B0, const WarpPose& wp,
+                                                  int u, int v) {
+    switch (L) {
+        case 1: return warped_down<PREC, 1>(A0, B0, wp, u, v);
+        case 2: return warped_down<PREC, 2>(A0, B0, wp, u, v);
+        case 3: return warped_down<PREC, 3>(A0, B0, wp, u, v);
+        case 4: return warped_down<PREC, 4>(A0, B0, wp, u, v);
+        case 5: return warped_down<PREC, 5>(A0, B0, wp, u, v);
+        default: return warped_down<PREC, 0>(A0, B0, wp, u, v);
     }
 }
 
@@ -279,20 +443,12 @@ struct F2 {
 __device__ __forceinline__ F2 as_f2(float x) { return F2{x, 0.f}; }
 __device__ __forceinline__ F2 as_f2(const F2& x) { return x; }
 
-// FP64 reciprocal square root for the reduced-precision form's solve: an FP32
-// seed refined by two Newton steps y <- y (3 - x y^2) / 2 in FP64.
-__device__ __forceinline__ double rsqrt_d(double x) {
-    double y = (double)rsqrtf((float)x);
-    y = y * (1.5 - 0.5 * x * y * y);
-    y = y * (1.5 - 0.5 * x * y * y);
-    return y;
-}
-
 // Solve of the normal equations H xi = -g ("Iterative optimisation") for one
 // thread: H is Jacobi-scaled to unit diagonal (D = diag(H)^-1/2, solve
-// (D H D) y = -D g, xi = D y) and factorised by Cholesky, in FP32 with pivot
-// tolerance 1e-7 or in FP64 with 1e-12 for the reduced-precision form; a
-// non-positive pivot reports a degenerate step.  H and g are read straight
+// (D H D) y = -D g, xi = D y) and factorised by Cholesky in FP32 with pivot
+// tolerance 1e-7 (the reduced-precision form refines the result to FP64
+// accuracy, warp_solve6_refined below); a non-positive pivot reports a
+// degenerate step.  H and g are read straight
 // from the reduction slots `s` (H's upper triangle row by row in slots 0..20,
 // g in kSlotG..kSlotG+5).  All 27 values are loaded into registers before the
 // factorisation starts, so no shared-memory latency sits on its dependent
@@ -304,12 +460,6 @@ struct CholTraits<float> {
     static __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
     static __device__ __forceinline__ float fma3(float a, float b, float c) { return fmaf(a, b, c); }
     static constexpr float kPivotMin = 1e-7f;
-};
-template <>
-struct CholTraits<double> {
-    static __device__ __forceinline__ double rsq(double x) { return rsqrt_d(x); }
-    static __device__ __forceinline__ double fma3(double a, double b, double c) { return fma(a, b, c); }
-    static constexpr double kPivotMin = 1e-12;
 };
 
 __host__ __device__ constexpr int upper_slot(int i, int j) { return i * (11 - i) / 2 + j; }   // i <= j
@@ -373,6 +523,125 @@ __device__ __forceinline__ bool cholesky_solve6_slots(const float* s, Real xi[6]
 #pragma unroll
     for (int i = 0; i < 6; ++i) xi[i] *= D[i];
     return ok;
+}
+
+// The FP32 factorisation and the substitutions of the same Jacobi-scaled
+// Cholesky, kept apart so that one factorisation serves two right-hand sides
+// (the refinement below).  D = diag(H)^-1/2; (D H D) = L L^T; iL = 1 / diag(L).
+__device__ __forceinline__ bool chol6_factor_f(const float (&Hp)[21], float (&D)[6], float (&L)[6][6],
+                                               float (&iL)[6]) {
+    bool ok = true;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        const float hii = Hp[upper_slot(i, i)];
+        ok = ok && hii > 0.f;
+        D[i] = rsqrtf(hii);
+    }
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        float d = Hp[upper_slot(j, j)] * D[j] * D[j];
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            if (k < j) d = fmaf(-L[j][k], L[j][k], d);
+        ok = ok && d > CholTraits<float>::kPivotMin;
+        const float r = rsqrtf(d);
+        L[j][j] = d * r;
+        iL[j] = r;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            if (i > j) {
+                float t = Hp[upper_slot(j, i)] * D[i] * D[j];
+#pragma unroll
+                for (int k = 0; k < 6; ++k)
+                    if (k < j) t = fmaf(-L[i][k], L[j][k], t);
+                L[i][j] = t * r;
+            }
+        }
+    }
+    return ok;
+}
+
+// x = H^-1 b with the factors of chol6_factor_f.
+__device__ __forceinline__ void chol6_subst_f(const float (&D)[6], const float (&L)[6][6], const float (&iL)[6],
+                                              const float (&b)[6], float (&x)[6]) {
+    float y[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        float t = b[i] * D[i];
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            if (k < i) t = fmaf(-L[i][k], y[k], t);
+        y[i] = t * iL[i];
+    }
+#pragma unroll
+    for (int i = 5; i >= 0; --i) {
+        float t = y[i];
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            if (k > i) t = fmaf(-L[k][i], x[k], t);
+        x[i] = t * iL[i];
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) x[i] *= D[i];
+}
+
+// Solve of the reduced-precision form's normal equations H xi = -g, on one warp
+// (all 32 lanes call; every lane returns the same verdict).  Lane 0 factorises
+// the Jacobi-scaled H by Cholesky in FP32 and solves for x; lanes 0..5 form the
+// residual rho = -g - H x in FP64 from the reduction's values; lane 0 solves
+// H d = rho with the same factors, and xi = x + d is returned in FP64 (one step
+// of mixed-precision iterative refinement, Wilkinson 1963 / Moler 1967).  H and
+// g are sums held in FP32, and one refinement step brings x to the accuracy of
+// an FP64 factorisation of them at about the cost of the FP32 solve: the FP64
+// work is six lanes' six dependent FMAs and one add, where a factorisation in
+// FP64 chains some hundred dependent FP64 operations on one lane.
+// `x_sh` (float[6]), `d_sh` (float[6]), `rho_sh` and `xi_sh` (double[6]) are
+// shared scratch of the calling warp; xi_sh is 0 when the verdict is false.
+__device__ __forceinline__ bool warp_solve6_refined(const float* s, bool ok_in, float* x_sh, float* d_sh,
+                                                    double* rho_sh, double* xi_sh) {
+    const int lane = threadIdx.x & 31;
+    float D[6], L[6][6], iL[6];
+    int ok = 0;
+    if (lane == 0) {
+        float Hp[21], b[6], x[6];
+#pragma unroll
+        for (int k = 0; k < 21; ++k) Hp[k] = s[k];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) b[i] = -s[kSlotG + i];
+        ok = (ok_in && chol6_factor_f(Hp, D, L, iL)) ? 1 : 0;
+        chol6_subst_f(D, L, iL, b, x);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) x_sh[i] = x[i];
+    }
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    __syncwarp();
+    if (!ok) {
+        if (lane < 6) xi_sh[lane] = 0.0;
+        __syncwarp();
+        return false;
+    }
+    if (lane < 6) {
+        double acc = -(double)s[kSlotG + lane];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            const int lo = lane < j ? lane : j, hi = lane < j ? j : lane;
+            acc = fma(-(double)s[upper_slot(lo, hi)], (double)x_sh[j], acc);
+        }
+        rho_sh[lane] = acc;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        float r[6], d[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) r[i] = (float)rho_sh[i];
+        chol6_subst_f(D, L, iL, r, d);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) d_sh[i] = d[i];
+    }
+    __syncwarp();
+    if (lane < 6) xi_sh[lane] = (double)x_sh[lane] + (double)d_sh[lane];
+    __syncwarp();
+    return true;
 }
 
 // ---------------------------------------------------------------- warp-parallel pose arithmetic (double)
@@ -462,7 +731,11 @@ __device__ __forceinline__ void warp_apply_update_d(const double xi[6], double* 
     const double tx = xi[3], ty = xi[4], tz = xi[5];
     const double t2d = tx * tx + ty * ty + tz * tz;
     double Ad, Bd;
-    if (t2d < 0.25) {
+    if (t2d < 1e-4) {
+        // the same series to t^8 (|t| < 0.01: the first omitted terms are below 3e-28)
+        Ad = 1.0 - t2d * (1.0 / 6.0 - t2d * (1.0 / 120.0 - t2d * (1.0 / 5040.0 - t2d * (1.0 / 362880.0))));
+        Bd = 0.5 - t2d * (1.0 / 24.0 - t2d * (1.0 / 720.0 - t2d * (1.0 / 40320.0 - t2d * (1.0 / 3628800.0))));
+    } else if (t2d < 0.25) {
         // Taylor series of sin t / t and (1 - cos t) / t^2 to t^16 (|t| < 0.5: error < 1e-19)
         Ad = 1.0 - t2d * (1.0 / 6.0 - t2d * (1.0 / 120.0 - t2d * (1.0 / 5040.0 - t2d * (1.0 / 362880.0 -
              t2d * (1.0 / 39916800.0 - t2d * (1.0 / 6227020800.0 - t2d * (1.0 / 1307674368000.0 -

@@ -28,6 +28,8 @@ ERR_WORKSPACE = 3
 ERR_DEGENERATE = 4
 ERR_TIMEOUT = 5
 ERR_UNSUPPORTED = 6
+WARP_PER_LEVEL = 0
+WARP_FULL_RESOLUTION = 1
 
 
 class Intrinsics(Structure):
@@ -56,7 +58,7 @@ class Timing(Structure):
 class AlignParams(Structure):
     _fields_ = [("levels", c_int), ("iters", c_int * MAX_LEVELS), ("scale_iters", c_int),
                 ("bisect_steps", c_int), ("sample_cap", c_int), ("estimate_nu", c_int),
-                ("min_valid", c_int), ("pad_", c_int), ("nu0", c_double), ("nu_lo", c_double),
+                ("min_valid", c_int), ("warp_mode", c_int), ("nu0", c_double), ("nu_lo", c_double),
                 ("nu_hi", c_double), ("timing", POINTER(Timing)), ("level_iters", c_void_p)]
 
 
@@ -72,6 +74,11 @@ RESULT_BYTES = ctypes.sizeof(AlignResult)
 class BatchItem(Structure):
     _fields_ = [("ref", Pyramid), ("cur", Pyramid), ("T_init", c_double * 16), ("levels", c_int),
                 ("iters", c_int * MAX_LEVELS), ("pad_", c_int), ("result", c_void_p)]
+
+
+class Bilateral(Structure):
+    _fields_ = [("radius", c_int), ("pad_", c_int), ("sigma_s", c_double), ("sigma_r_I", c_double),
+                ("sigma_r_W", c_double)]
 
 
 class BatchConfig(Structure):
@@ -102,6 +109,17 @@ SIGNATURES = [
                                     c_int, Intrinsics, c_void_p, c_void_p, c_int, c_int, c_void_p]),
     ("rgbid_init_keyframe", c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_int, c_int,
                                     c_int, c_void_p]),
+    ("rgbid_default_bilateral", None, [POINTER(Bilateral)]),
+    ("rgbid_covariance_workspace_bytes", c_size_t, [POINTER(Pyramid)]),
+    ("rgbid_covariance", c_int, [POINTER(Pyramid), POINTER(Pyramid), c_void_p, c_int, POINTER(AlignParams),
+                                 POINTER(Bilateral), c_void_p, c_size_t, c_void_p, c_void_p, c_void_p]),
+    ("rgbid_fuse_or_switch_keyframe", c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_int,
+                                              c_int, c_int, Intrinsics, c_void_p, c_void_p, c_int, c_void_p,
+                                              c_void_p]),
+    ("rgbid_covisibility", c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_int, c_int, c_int, Intrinsics,
+                                   c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
+    ("rgbid_keyframe_decide", c_int, [c_void_p, c_double, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                      c_void_p]),
     ("rgbid_predict_pose", c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     ("rgbid_compose_pose", c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
     ("rgbid_align_batched_workspace_bytes", c_size_t, []),
@@ -272,6 +290,81 @@ def rgbid_fuse_keyframe(I_kf, W_kf, C_kf, I_k, W_k, K, T_kf_k, sigma_W, fuse_int
                                      W_k.stride(-2), w, h, Ki, tp, sp, 1 if on_dev else 0,
                                      1 if fuse_intensity else 0, _stream_ptr(stream))
     _check("rgbid_fuse_keyframe", code)
+
+
+def rgbid_default_bilateral(**overrides) -> Bilateral:
+    f = Bilateral()
+    lib().rgbid_default_bilateral(ctypes.byref(f))
+    for k, v in overrides.items():
+        setattr(f, k, v)
+    return f
+
+
+def new_covariance_workspace(ref: Pyramid, device="cuda"):
+    import torch
+    n = lib().rgbid_covariance_workspace_bytes(ctypes.byref(ref))
+    return torch.zeros(max(int(n), 256), dtype=torch.uint8, device=device)
+
+
+def rgbid_covariance(ref: Pyramid, cur: Pyramid, T, params: AlignParams, filt: Bilateral, workspace, d_result,
+                     d_sigma, stream=None):
+    """The covariance iteration at pose ``T`` (host 4x4 or a CUDA float64 tensor of 16):
+    ``d_result`` (result tensor) receives H_filt and the iteration's statistics,
+    ``d_sigma`` (CUDA float64 tensor of 36) receives H_filt^-1."""
+    keep = []
+    if hasattr(T, "is_cuda") and T.is_cuda:
+        tp, on_dev = _ptr(T), 1
+    else:
+        Ta = np.ascontiguousarray(np.asarray(T, dtype=np.float64).reshape(16))
+        keep.append(Ta)
+        tp, on_dev = c_void_p(Ta.ctypes.data), 0
+    code = lib().rgbid_covariance(ctypes.byref(ref), ctypes.byref(cur), tp, on_dev, ctypes.byref(params),
+                                  ctypes.byref(filt), _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                  _ptr(d_result), _ptr(d_sigma), _stream_ptr(stream))
+    _check("rgbid_covariance", code)
+
+
+def _pose_sigma_args(T, sigma_W, keep):
+    """(pose pointer, sigma pointer, on_device) for host values or CUDA float64 tensors."""
+    on_dev = hasattr(T, "is_cuda") and T.is_cuda
+    if on_dev:
+        return _ptr(T), _ptr(sigma_W), 1
+    Ta = np.ascontiguousarray(np.asarray(T, dtype=np.float64).reshape(16))
+    sa = np.array([float(sigma_W)], dtype=np.float64)
+    keep += [Ta, sa]
+    return c_void_p(Ta.ctypes.data), c_void_p(sa.ctypes.data), 0
+
+
+def rgbid_fuse_or_switch_keyframe(I_kf, W_kf, C_kf, I_k, W_k, K, T_kf_k, sigma_W, d_switch,
+                                  fuse_intensity: bool = True, stream=None):
+    """Fuse frame k into the keyframe, or (device int ``d_switch`` set) make it the
+    keyframe.  ``T_kf_k`` and ``sigma_W`` are CUDA float64 tensors."""
+    h, w = W_kf.shape[-2], W_kf.shape[-1]
+    code = lib().rgbid_fuse_or_switch_keyframe(_ptr(I_kf), _ptr(W_kf), _ptr(C_kf), W_kf.stride(-2), _ptr(I_k),
+                                               _ptr(W_k), W_k.stride(-2), w, h, Intrinsics(*[float(k) for k in K]),
+                                               _ptr(T_kf_k), _ptr(sigma_W), 1 if fuse_intensity else 0,
+                                               _ptr(d_switch), _stream_ptr(stream))
+    _check("rgbid_fuse_or_switch_keyframe", code)
+
+
+def rgbid_covisibility(I_A, W_A, I_B, W_B, K, T_AB, sigma_W, d_counts, d_ratio=None, stream=None):
+    """Dense covisibility counts (device uint32[4]: S_V(A->B), S_H(A), S_V(B->A), S_H(B))
+    and optionally the ratio (device float32[1]).  ``T_AB``/``sigma_W`` are host
+    values or CUDA float64 tensors."""
+    h, w = W_A.shape[-2], W_A.shape[-1]
+    keep = []
+    tp, sp, on_dev = _pose_sigma_args(T_AB, sigma_W, keep)
+    code = lib().rgbid_covisibility(_ptr(I_A), _ptr(W_A), W_A.stride(-2), _ptr(I_B), _ptr(W_B), W_B.stride(-2), w, h,
+                                    Intrinsics(*[float(k) for k in K]), tp, sp, on_dev, _ptr(d_counts),
+                                    _ptr(d_ratio) if d_ratio is not None else None, _stream_ptr(stream))
+    _check("rgbid_covisibility", code)
+
+
+def rgbid_keyframe_decide(d_counts, threshold: float, T_k, T1, T2, d_switch, d_ratio=None, stream=None):
+    code = lib().rgbid_keyframe_decide(_ptr(d_counts), float(threshold), _ptr(T_k), _ptr(T1), _ptr(T2),
+                                       _ptr(d_switch), _ptr(d_ratio) if d_ratio is not None else None,
+                                       _stream_ptr(stream))
+    _check("rgbid_keyframe_decide", code)
 
 
 def rgbid_init_keyframe(I_kf, W_kf, C_kf, I_k, W_k, stream=None):

@@ -7,9 +7,12 @@ Per frame k, entirely enqueued on one CUDA stream (no host round trip):
      kf_T_k(0) = kf_T_{k-1} (kf_T_{k-2})^-1 kf_T_{k-1};
   3. align the frame to the keyframe (coarse-to-fine IRLS);
   4. either fuse the frame into the keyframe with the estimated pose and the
-     final sigma_W of the alignment, or, every ``kf_every`` frames, make the
-     frame the new keyframe (after its own alignment, without fusing it into
-     the outgoing one) and re-express the motion model's poses in it;
+     final sigma_W of the alignment, or make the frame the new keyframe (after
+     its own alignment, without fusing it into the outgoing one) and
+     re-express the motion model's poses in it: every ``kf_every`` frames, or,
+     with ``kf_covisibility``, when the dense covisibility ratio of the aligned
+     frame with the keyframe falls below that threshold (0.7 in the paper),
+     decided on the device;
   5. rebuild the keyframe's pyramid.
 Each frame's result (pose relative to its keyframe, robust parameters, ...) is
 copied to a device array so that the host reads them once at the end.
@@ -34,11 +37,12 @@ from . import rgbid as R
 class Tracker:
     def __init__(self, width: int, height: int, K, levels: int = 4, iters=(5, 5, 5, 10), kf_every: int = 20,
                  precision: int = R.PLANES_F32, fuse_intensity: bool = True, max_frames: int = 4096,
-                 device="cuda", graphs: bool = True):
+                 device="cuda", graphs: bool = True, kf_covisibility: float | None = None):
         import torch
         self.torch = torch
         self.w, self.h, self.K = width, height, tuple(float(k) for k in K)
         self.kf_every = kf_every
+        self.kf_covisibility = kf_covisibility
         self.fuse_intensity = fuse_intensity
         self.device = device
         self.params = R.rgbid_default_params(levels=levels, iters=iters)
@@ -60,6 +64,13 @@ class Tracker:
         self.ws = None
         self.k = 0
         self.is_kf = np.zeros(max_frames, dtype=bool)
+        if kf_covisibility is not None:
+            # device-side decision: counts, flag and ratio of the current frame, and per-frame copies
+            self.counts = torch.zeros(4, dtype=torch.int32, device=device)
+            self.d_switch = torch.zeros(1, dtype=torch.int32, device=device)
+            self.d_ratio = torch.zeros(1, dtype=torch.float32, device=device)
+            self.kf_flags = torch.zeros(max_frames, dtype=torch.int32, device=device)
+            self.ratios = torch.zeros(max_frames, dtype=torch.float32, device=device)
         self.graphs = graphs
         self._graph = {}          # (frame kind (True: keyframe switch), staging slot) -> CUDA graph of steps 1-5
         # two staging pairs for the graphs (slot 0 also takes frames passed from elsewhere)
@@ -99,7 +110,8 @@ class Tracker:
             self.is_kf[0] = True
             self.k = 1
             return
-        kf = k % self.kf_every == 0
+        # with the covisibility policy every frame has the same kind: the device decides
+        kf = self.kf_covisibility is None and k % self.kf_every == 0
         s = stream if stream is not None else torch.cuda.current_stream()
         slot = 1 if self.graphs and I is self._stage[1][0] and W is self._stage[1][1] else 0
         with torch.cuda.stream(s):
@@ -115,6 +127,9 @@ class Tracker:
             else:
                 self._frame(I, W, kf, s)
             self.results[k].copy_(self.res[0], non_blocking=True)
+            if self.kf_covisibility is not None:
+                self.kf_flags[k:k + 1].copy_(self.d_switch, non_blocking=True)
+                self.ratios[k:k + 1].copy_(self.d_ratio, non_blocking=True)
         if self.graphs and not self.params.timing and (kf, slot) not in self._graph:
             self._capture(kf, slot)
         self.is_kf[k] = kf
@@ -125,7 +140,15 @@ class Tracker:
         self.cur.build(I, W, self.K, stream)
         R.rgbid_predict_pose(self.T1, self.T2, self.Tinit, stream)
         R.rgbid_align(self.kfp.desc, self.cur.desc, self.Tinit, self.params, self.ws, self.res, stream)
-        if kf:
+        if self.kf_covisibility is not None:
+            # covisibility of the aligned frame with the keyframe, the decision, and fusion or switch
+            R.rgbid_covisibility(self.I_kf, self.W_kf, I, W, self.K, self._T_view(), self._sigmaW_view(),
+                                 self.counts, None, stream)
+            R.rgbid_keyframe_decide(self.counts, self.kf_covisibility, self._T_view(), self.T1, self.T2,
+                                    self.d_switch, self.d_ratio, stream)
+            R.rgbid_fuse_or_switch_keyframe(self.I_kf, self.W_kf, self.C_kf, I, W, self.K, self._T_view(),
+                                            self._sigmaW_view(), self.d_switch, self.fuse_intensity, stream)
+        elif kf:
             # new keyframe = this frame; poses of frames k-1 and k re-expressed in it
             R.rgbid_compose_pose(self._T_view(), True, self.T1, self.Tnew, stream)   # k_T_{k-1}
             self.T2.copy_(self.Tnew)
@@ -148,16 +171,28 @@ class Tracker:
             self._frame(SI, SW, kf, torch.cuda.current_stream())
         self._graph[(kf, slot)] = g
 
+    def keyframe_flags(self) -> np.ndarray:
+        """Per processed frame: True where the frame became the keyframe (frame 0 included)."""
+        flags = self.is_kf[:self.k].copy()
+        if self.kf_covisibility is not None:
+            flags[1:] = self.kf_flags[1:self.k].cpu().numpy() != 0
+        return flags
+
+    def covisibility_ratios(self) -> np.ndarray:
+        """Per processed frame k >= 1: its covisibility ratio with the keyframe it was aligned to."""
+        return self.ratios[1:self.k].cpu().numpy().astype(np.float64)
+
     def trajectory(self):
         """World-from-camera poses of the processed frames (frame 0 = identity), on the host."""
         n = self.k
+        is_kf = self.keyframe_flags()
         T_world = [np.eye(4)]
         T_wkf = np.eye(4)
         for k in range(1, n):
             r = R.parse_result(self.results[k])
             Tk = T_wkf @ r["T"]
             T_world.append(Tk)
-            if self.is_kf[k]:
+            if is_kf[k]:
                 T_wkf = Tk
         return np.stack(T_world)
 

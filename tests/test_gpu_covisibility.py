@@ -1,0 +1,117 @@
+"""Dense covisibility ratio ("Dense frame covisibility ratio") and the
+covisibility-driven keyframe switch ("Keyframe fusion") through the C ABI,
+against the FP64 oracle.
+
+Counts are integers decided by floating-point comparisons (the nearest pixel of
+a transferred point and the 3 sigma_W test), which the kernel takes in FP32 and
+the oracle in FP64: they must agree except for pixels whose FP64 decision
+quantity lies within FP32 rounding of its threshold, and those are counted."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1807_08271_gb300 import synth
+
+from parity import POSE_TOL, pose_error
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - collected on CPU hosts too
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1807_08271_gb300 import rgbid as R  # noqa: E402
+from paper_1807_08271_gb300.tracker import Tracker  # noqa: E402
+
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "seq640_covis_oracle.json")
+KINECT = (525.0, 525.0, 319.5, 239.5)
+
+
+def _near(IA, WA, IB, WB, K, T, sigma):
+    """Source pixels of A whose nearest-pixel rounding or 3 sigma_W test sits within
+    FP32 rounding of its threshold when transferred into B (FP64 quantities)."""
+    A = O.Level(*O.measurement_planes(IA, WA), K)
+    B = O.Level(*O.measurement_planes(IB, WB), K)
+    wp = O.inverse_geometric_warp(A, B, T)
+    fu = np.abs((wp["u_B"] + 0.5) - np.round(wp["u_B"] + 0.5))
+    fv = np.abs((wp["v_B"] + 0.5) - np.round(wp["v_B"] + 0.5))
+    h, w = A.W.shape
+    xn = np.clip(np.floor(wp["u_B"] + 0.5), 0, w - 1).astype(int)
+    yn = np.clip(np.floor(wp["v_B"] + 0.5), 0, h - 1).astype(int)
+    wB = 1.0 / np.where(wp["front"], wp["Z_B"], 1.0)
+    gate = np.abs(np.abs(B.W[yn, xn] - wB) - 3 * sigma)
+    return int((wp["validA"] & ((np.minimum(fu, fv) < 1e-4) | (gate < 1e-6))).sum())
+
+
+@pytest.mark.parametrize("seed", [3, 8])
+def test_covisibility_counts_match_the_oracle(seed):
+    p = synth.make_pair(seed, 640, 480, K=KINECT, max_angle_deg=6.0, max_trans=0.12)
+    rng = np.random.default_rng(seed)
+    for key in ("W_A", "I_B"):                       # non-finite values are holes on both sides
+        idx = rng.integers(0, 640 * 480, 300)
+        p[key].reshape(-1)[idx] = np.nan
+    planes = [torch.from_numpy(p[k]).cuda() for k in ("I_A", "W_A", "I_B", "W_B")]
+    counts = torch.zeros(4, dtype=torch.int32, device="cuda")
+    ratio = torch.zeros(1, dtype=torch.float32, device="cuda")
+    sigma = 1.5e-3
+    for T in (p["T_gt"], O.se3_exp([0.01, -0.005, 0.0, 0.0, 0.004, 0.0]) @ p["T_gt"]):
+        R.rgbid_covisibility(*planes, p["K"], T, sigma, counts, ratio)
+        torch.cuda.synchronize()
+        g = counts.cpu().numpy().astype(np.int64)
+        o = O.covisibility_ratio(p["I_A"], p["W_A"], p["I_B"], p["W_B"], p["K"], T, sigma)
+        (vab, hab), (vba, hba) = o["counts"]
+        assert g[1] == hab and g[3] == hba                       # S_H: exact
+        near_ab = _near(p["I_A"], p["W_A"], p["I_B"], p["W_B"], p["K"], T, sigma)
+        near_ba = _near(p["I_B"], p["W_B"], p["I_A"], p["W_A"], p["K"], O.se3_inv(T), sigma)
+        assert abs(int(g[0]) - vab) <= near_ab and abs(int(g[2]) - vba) <= near_ba, (g, o["counts"])
+        assert 0.3 < o["vr"] < 1.0
+        expect = min(g[0] / g[1], g[2] / g[3])
+        assert abs(float(ratio.item()) - expect) <= 1e-6
+        assert abs(float(ratio.item()) - o["vr"]) <= (near_ab + near_ba) / min(hab, hba) + 1e-6
+
+
+def test_identical_frames_are_fully_covisible():
+    p = synth.make_pair(5, 320, 240)
+    I = torch.from_numpy(p["I_A"]).cuda()
+    W = torch.from_numpy(p["W_A"]).cuda()
+    counts = torch.zeros(4, dtype=torch.int32, device="cuda")
+    R.rgbid_covisibility(I, W, I, W, p["K"], np.eye(4), 1e-3, counts)
+    torch.cuda.synchronize()
+    g = counts.cpu().numpy()
+    n = int((p["W_A"] > 0).sum())
+    assert list(g) == [n, n, n, n]
+
+
+def test_tracker_switches_keyframes_on_covisibility_like_the_oracle():
+    gold = json.load(open(GOLD))
+    thr = gold["threshold"]
+    fr = gold["fp32_planes"]["frames"]
+    n = len(fr) + 1
+    vr_o = np.array([f["covisibility"] for f in fr])
+    sw_o = np.array([f["switch"] for f in fr])
+    # the decisions of this sequence are not within FP32 counting noise of the threshold
+    assert np.min(np.abs(vr_o - thr)) > 5e-4
+    assert 2 <= sw_o.sum() <= n // 4
+    seq = synth.render_sequence(0, n_frames=n)
+    I_all = torch.from_numpy(seq["I"]).cuda()
+    W_all = torch.from_numpy(seq["W"]).cuda()
+    trk = Tracker(640, 480, seq["K"], levels=4, iters=(5, 5, 5, 10), max_frames=n, kf_covisibility=thr)
+    for k in range(n):
+        trk.step(I_all[k], W_all[k])
+    torch.cuda.synchronize()
+    flags = trk.keyframe_flags()
+    ratios = trk.covisibility_ratios()
+    assert np.array_equal(flags[1:], sw_o), (np.argwhere(flags[1:] != sw_o).ravel() + 1).tolist()
+    assert np.abs(ratios - vr_o).max() <= 5e-4, np.abs(ratios - vr_o).max()
+    res = trk.frame_results()
+    world = trk.trajectory()
+    for r, o in zip(res, fr):
+        er, et = pose_error(r["T"], np.array(o["T"]).reshape(4, 4))
+        assert er <= POSE_TOL and et <= POSE_TOL, (o["k"], er, et)
+        ew, tw = pose_error(world[o["k"]], np.array(o["T_world"]).reshape(4, 4))
+        assert ew <= POSE_TOL and tw <= POSE_TOL, (o["k"], ew, tw)
+    # one graph per staging slot: the frame kind is decided on the device
+    assert set(trk._graph) == {(False, 0)}
