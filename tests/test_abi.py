@@ -46,6 +46,8 @@ int main(void) {{
          offsetof(rgbid_align_result, cost), offsetof(rgbid_align_result, status), sizeof(rgbid_timing),
          offsetof(rgbid_timing, units), offsetof(rgbid_align_params, timing),
          offsetof(rgbid_align_params, level_iters));
+  printf("%zu %zu %zu %zu\\n", sizeof(rgbid_bilateral), offsetof(rgbid_bilateral, sigma_s),
+         offsetof(rgbid_bilateral, sigma_r_W), offsetof(rgbid_align_params, warp_mode));
   return 0;
 }}''')
     exe = tmp_path / "abi"
@@ -55,9 +57,11 @@ int main(void) {{
     b = binding
     assert sizes[:5] == [ctypes.sizeof(b.Intrinsics), ctypes.sizeof(b.Level), ctypes.sizeof(b.Pyramid),
                          ctypes.sizeof(b.AlignParams), ctypes.sizeof(b.AlignResult)]
-    assert sizes[5:] == [b.Level.IW.offset, b.AlignParams.nu0.offset, b.AlignResult.cost.offset,
-                         b.AlignResult.status.offset, ctypes.sizeof(b.Timing), b.Timing.units.offset,
-                         b.AlignParams.timing.offset, b.AlignParams.level_iters.offset]
+    assert sizes[5:13] == [b.Level.IW.offset, b.AlignParams.nu0.offset, b.AlignResult.cost.offset,
+                           b.AlignResult.status.offset, ctypes.sizeof(b.Timing), b.Timing.units.offset,
+                           b.AlignParams.timing.offset, b.AlignParams.level_iters.offset]
+    assert sizes[13:] == [ctypes.sizeof(b.Bilateral), b.Bilateral.sigma_s.offset, b.Bilateral.sigma_r_W.offset,
+                          b.AlignParams.warp_mode.offset]
 
 
 def test_host_side_calls_without_a_gpu(binding):
@@ -236,6 +240,37 @@ def test_misaligned_and_nonfinite_arguments_are_rejected_on_the_host(binding):
     assert L.rgbid_net_inputs(V(base + 4), 1, 0, f[1], None) == b.ERR_INVALID_ARG
     assert L.rgbid_net_init(V(base + 2), 1, None) == b.ERR_INVALID_ARG
     assert L.rgbid_net_plan(f[0], 1, None, 0, V(base + 0x100004), f[2], None, None) == b.ERR_INVALID_ARG
+    # covisibility, the keyframe decision and fusion-or-switch
+    cnt, flag = V(base + 0x900000), V(base + 0xA00000)
+    assert L.rgbid_covisibility(V(base + 2), *f[1:2], 160, *f[2:4], 160, 160, 120, K, T, s, 1, cnt, None,
+                                None) == b.ERR_INVALID_ARG
+    assert L.rgbid_covisibility(*f[:2], 160, *f[2:4], 160, 160, 120, K, T, s, 1, V(base + 0x900002), None,
+                                None) == b.ERR_INVALID_ARG
+    assert L.rgbid_covisibility(*f[:2], 160, *f[2:4], 160, 160, 120, b.Intrinsics(131.25, -1.0, 79.5, 59.5), T, s,
+                                1, cnt, None, None) == b.ERR_INVALID_ARG
+    assert L.rgbid_keyframe_decide(cnt, 1.5, T, f[0], f[1], flag, None, None) == b.ERR_INVALID_ARG
+    assert L.rgbid_keyframe_decide(cnt, 0.7, T, f[0], f[0], flag, None, None) == b.ERR_INVALID_ARG
+    assert L.rgbid_keyframe_decide(cnt, 0.7, T, f[0], f[1], V(base + 0xA00002), None, None) == b.ERR_INVALID_ARG
+    assert L.rgbid_fuse_or_switch_keyframe(*f[:3], 160, *f[3:5], 160, 160, 120, K, T, s, 1, None, None) == \
+        b.ERR_INVALID_ARG
+    # the covariance iteration: filter values and workspace
+    filt = b.rgbid_default_bilateral()
+    d_sig = V(base + 0xB00000)
+
+    def cov(A, B, F=filt, wsz=wsb, sigma=d_sig):
+        return L.rgbid_covariance(ctypes.byref(A), ctypes.byref(B), T, 1, ctypes.byref(p), ctypes.byref(F), ws,
+                                  wsz, res, sigma, None)
+    assert cov(good, good, F=b.rgbid_default_bilateral(radius=6)) == b.ERR_INVALID_ARG
+    assert cov(good, good, F=b.rgbid_default_bilateral(sigma_r_W=0.0)) == b.ERR_INVALID_ARG
+    assert cov(good, good, F=b.rgbid_default_bilateral(sigma_s=np.inf)) == b.ERR_INVALID_ARG
+    assert cov(good, good, sigma=V(base + 0xB00004)) == b.ERR_INVALID_ARG
+    assert cov(good, good, wsz=b.lib().rgbid_covariance_workspace_bytes(ctypes.byref(good)) - 1) == b.ERR_WORKSPACE
+    # the warp mode: unknown values are rejected, and the batched form takes the per-level warp only
+    pw = b.rgbid_default_params(levels=1, iters=[3])
+    pw.warp_mode = 2
+    assert align(good, good, params=pw) == b.ERR_INVALID_ARG
+    pw.warp_mode = b.WARP_FULL_RESOLUTION
+    assert L.rgbid_align_batched(V(base), 1, 0, ctypes.byref(pw), None, ws, wsb, None) == b.ERR_UNSUPPORTED
     # the wait-timeout probe's own arguments
     assert L.rgbid_probe_wait_timeout(-1, f[0], None) == b.ERR_INVALID_ARG
     assert L.rgbid_probe_wait_timeout(1000, None, None) == b.ERR_INVALID_ARG
