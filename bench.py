@@ -530,7 +530,7 @@ EXTENSION_RUNS = {
     # name: (arguments, summary keys taken from the form's own line)
     "batched": (["--workload", "batch", "--steps", "120"], ("per_pair_form",)),
     "precision_bf16": (["--precision", "bf16", "--steps", "120"], ()),
-    "learned": (["--workload", "learned", "--steps", "256"], ("per_pair", "batched")),
+    "learned": (["--workload", "learned", "--steps", "256"], ("per_pair", "batched", "equal_accuracy")),
 }
 
 
@@ -867,6 +867,7 @@ def native_learned(args):
     import torch
 
     from paper_1807_08271_gb300 import rgbid as R
+    from paper_1807_08271_gb300 import synth
     from paper_1807_08271_gb300 import learned as Lm
     from paper_1807_08271_gb300.learned_train import EvalSet, pose_diff, _sized
     from paper_1807_08271_gb300.synth import gpu as G
@@ -897,6 +898,7 @@ def native_learned(args):
 
     out = {}
     clk = None
+    kept = {}
     for kind in ("plain", "learned"):
         for k in range(max(3, args.warmup)):
             run(kind, k)
@@ -916,6 +918,7 @@ def native_learned(args):
         if kind == "learned":
             clk = clocks.stop()
         rr = [R.parse_result(res[k]) for k in range(n_steps)]
+        kept[kind] = rr
         ok = ev.converged(rr)
         out[kind] = dict(ms=e0.elapsed_time(e1), converged=float(np.mean(ok)),
                          iters=float(np.mean([r["iters_done"] for r in rr])),
@@ -956,6 +959,50 @@ def native_learned(args):
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
 
+    # the metric's own criterion: the learned start's final pose within 1e-5 rad and
+    # 1e-5 m of the plain form's (identity start, all levels), pair by pair
+    def agreement(a, b):
+        d = np.array([pose_err(x["T"], y["T"]) for x, y in zip(a, b)])
+        return {"pairs": int(d.shape[0]), "within_1e-5_rad_and_m": float(np.mean((d[:, 0] <= 1e-5) & (d[:, 1] <= 1e-5))),
+                "median_rad": float(np.median(d[:, 0])), "median_m": float(np.median(d[:, 1]))}
+
+    agree_10deg = agreement(kept["learned"], kept["plain"])
+
+    # held-out pairs shaped like the tracking workload: frames 20 j + d of another
+    # seeded room sequence aligned to frame 20 j (d = 1..19), identity start
+    seq1 = synth.render_sequence(seed=1 + rank, n_frames=81)
+    c1_pairs = [(20 * j, 20 * j + d) for j in range(4) for d in range(1, 20)]
+    pyr_c1 = {}
+    for f in sorted({i for pr in c1_pairs for i in pr}):
+        pyr_c1[f] = R.DevicePyramid(640, 480, 4).build(torch.from_numpy(seq1["I"][f]).cuda(),
+                                                        torch.from_numpy(seq1["W"][f]).cuda(), seq1["K"])
+    la_c1 = Lm.LearnedAligner(_sized(net, 1), thr, levels=4, iters=[5, 5, 5, 10])
+    la_c1.set_pairs([(pyr_c1[a].desc, pyr_c1[b].desc) for a, b in c1_pairs])
+    res_c1 = {k: R.result_tensor(len(c1_pairs)) for k in ("plain", "learned")}
+    c1 = {}
+    for kind in ("plain", "learned", "plain", "learned"):      # the second round is timed
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i, (a_, b_) in enumerate(c1_pairs):
+            if kind == "plain":
+                R.rgbid_align(pyr_c1[a_].desc, pyr_c1[b_].desc, None, params, ws, res_c1[kind][i])
+            else:
+                la_c1.align(i, ws, res_c1[kind][i])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        rr = [R.parse_result(res_c1[kind][i]) for i in range(len(c1_pairs))]
+        c1[kind] = {"alignments_per_s": len(c1_pairs) / (e0.elapsed_time(e1) / 1000.0),
+                    "mean_iterations": float(np.mean([r["iters_done"] for r in rr])), "results": rr}
+    gt = [np.linalg.inv(seq1["T_wc"][a_]) @ seq1["T_wc"][b_] for a_, b_ in c1_pairs]
+    c1_summary = {kind: {"alignments_per_s": v["alignments_per_s"], "mean_iterations": v["mean_iterations"],
+                         "median_rot_err_vs_truth_rad": float(np.median([pose_err(r["T"], g)[0]
+                                                                         for r, g in zip(v["results"], gt)]))}
+                  for kind, v in c1.items()}
+    c1_summary["learned_vs_plain"] = agreement(c1["learned"]["results"], c1["plain"]["results"])
+    c1_summary["pairs"] = ("frame 20 j + d of the seeded 640x480 room sequence (seed 1) aligned to frame 20 j, "
+                           "j = 0..3, d = 1..19, identity start")
+
     # the batched forms on the whole held-out set (one persistent launch each)
     res_p, ms_p, _ = ev.run(None, reps=5)
     from paper_1807_08271_gb300.learned import LearnedPlanner
@@ -988,6 +1035,8 @@ def native_learned(args):
         "per_pair": {kind: {"alignments_per_s": n_steps / (v["ms"] / 1000.0), "converged_fraction": v["converged"],
                             "mean_iterations": v["iters"], "median_rot_err_vs_truth_rad": v["median_err"]}
                      for kind, v in out.items()},
+        "equal_accuracy": {"criterion": "learned-start pose within 1e-5 rad and 1e-5 m of the plain form's",
+                           "held_out_10deg": agree_10deg, "tracking_like_pairs": c1_summary},
         "batched": {"plain_alignments_per_s": LEARNED_N / (ms_p / 1000.0),
                     "learned_alignments_per_s": LEARNED_N / (ms_l / 1000.0),
                     "plain_converged": float(np.mean(ev.converged(res_p))),
