@@ -70,7 +70,7 @@ def alu_roofline(kernel: str, units_per_launch: float, ms_per_launch: float) -> 
 # the robust-scale kernel) from the ncu captures summarised in
 # profiles/robust_kernel_seq640_level0.md and profiles/sweep_kernel_seq640_level0.md
 # (level-0 launches, cold caches); set to None whenever those kernels change.
-TRAFFIC_PER_UNIT = {"robust_kernel": 3166208 / 19200, "sweep_kernel": 6767616 / 307200}
+TRAFFIC_PER_UNIT = {"robust_kernel": 3240192 / 19200, "sweep_kernel": 4847616 / 307200}
 
 
 # ----------------------------------------------------------------------------- ranks
