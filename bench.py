@@ -529,6 +529,7 @@ def native(args):
 EXTENSION_RUNS = {
     # name: (arguments, summary keys taken from the form's own line)
     "batched": (["--workload", "batch", "--steps", "120"], ("per_pair_form",)),
+    "batched_bf16": (["--workload", "batch", "--precision", "bf16", "--steps", "120"], ("per_pair_form",)),
     "precision_bf16": (["--precision", "bf16", "--steps", "120"], ()),
     "learned": (["--workload", "learned", "--steps", "256"], ("per_pair", "batched", "equal_accuracy")),
 }
