@@ -67,6 +67,10 @@ __device__ __forceinline__ bf16 bz() { return __float2bfloat16_rn(0.f); }
 
 // ---------------------------------------------------------------- GEMM core
 constexpr int BM = 64, BN = 64, BK = 32, LDS = BK + 8, GEMM_NT = 128;
+constexpr int kVecBNone = 0, kVecBk = 1, kVecBn = 2;   // how B may be loaded 8 elements at a time
+constexpr int kVecANone = 0, kVecAk = 1, kVecAm = 2;   // how A may be loaded 8 elements at a time
+
+__device__ __forceinline__ uint4 ld16(const bf16* p) { return *reinterpret_cast<const uint4*>(p); }
 
 __device__ __forceinline__ uint32_t ld_pair(const bf16* p) { return *reinterpret_cast<const uint32_t*>(p); }
 
@@ -98,16 +102,58 @@ __global__ void __launch_bounds__(GEMM_NT) gemm_bf16(P p, int M, int N, int K, i
 #pragma unroll
             for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
 
+    // Vector loaders: 8 bf16 (16 bytes) per load where the operand is contiguous along
+    // k (A; B with kVecBk) or along n (B with kVecBn); the problem type says when its
+    // layout allows it (channel counts that are multiples of 8, so that every vector
+    // stays inside one tap and is 16-byte aligned, and K a multiple of 8, so that a
+    // vector that starts before the end of the K range ends before it too).
+    const bool vecAk = p.vecA() == kVecAk, vecAm = p.vecA() == kVecAm;
+    const bool vecBk = p.vecB() == kVecBk, vecBn = p.vecB() == kVecBn;
     for (int k0 = kb0; k0 < kb1; k0 += BK) {
-        for (int i = tid; i < BM * BK; i += GEMM_NT) {
-            const int r = i >> 5, c = i & 31;
-            const int m = m0 + r, k = k0 + c;
-            As[r][c] = (m < M && k < kb1) ? p.loadA(m, k) : bz();
+        if (vecAk) {
+            for (int i = tid; i < BM * BK / 8; i += GEMM_NT) {
+                const int r = i >> 2, c8 = (i & 3) * 8;
+                const int m = m0 + r, k = k0 + c8;
+                *reinterpret_cast<uint4*>(&As[r][c8]) = (m < M && k < kb1) ? p.loadA8(m, k) : make_uint4(0u, 0u, 0u, 0u);
+            }
+        } else if (vecAm) {
+            // 8 consecutive rows m of one column k (the problem zero-fills rows from M on)
+            for (int i = tid; i < BK * BM / 8; i += GEMM_NT) {
+                const int c = i >> 3, m8 = (i & 7) * 8;
+                const int k = k0 + c, m = m0 + m8;
+                const uint4 v = (k < kb1 && m < M) ? p.loadA8(m, k) : make_uint4(0u, 0u, 0u, 0u);
+                const bf16* e = reinterpret_cast<const bf16*>(&v);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) As[m8 + j][c] = e[j];
+            }
+        } else {
+            for (int i = tid; i < BM * BK; i += GEMM_NT) {
+                const int r = i >> 5, c = i & 31;
+                const int m = m0 + r, k = k0 + c;
+                As[r][c] = (m < M && k < kb1) ? p.loadA(m, k) : bz();
+            }
         }
-        for (int i = tid; i < BN * BK; i += GEMM_NT) {
-            const int r = i >> 5, c = i & 31;
-            const int n = n0 + r, k = k0 + c;
-            Bs[r][c] = (n < N && k < kb1) ? p.loadB(k, n) : bz();
+        if (vecBk) {
+            for (int i = tid; i < BN * BK / 8; i += GEMM_NT) {
+                const int r = i >> 2, c8 = (i & 3) * 8;
+                const int n = n0 + r, k = k0 + c8;
+                *reinterpret_cast<uint4*>(&Bs[r][c8]) = (n < N && k < kb1) ? p.loadB8(k, n) : make_uint4(0u, 0u, 0u, 0u);
+            }
+        } else if (vecBn) {
+            for (int i = tid; i < BK * BN / 8; i += GEMM_NT) {
+                const int c = i >> 3, n8 = (i & 7) * 8;
+                const int k = k0 + c, n = n0 + n8;
+                const uint4 v = (k < kb1 && n < N) ? p.loadB8(k, n) : make_uint4(0u, 0u, 0u, 0u);
+                const bf16* e = reinterpret_cast<const bf16*>(&v);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) Bs[n8 + j][c] = e[j];
+            }
+        } else {
+            for (int i = tid; i < BN * BK; i += GEMM_NT) {
+                const int r = i >> 5, c = i & 31;
+                const int n = n0 + r, k = k0 + c;
+                Bs[r][c] = (n < N && k < kb1) ? p.loadB(k, n) : bz();
+            }
         }
         __syncthreads();
 #pragma unroll
@@ -167,6 +213,17 @@ struct ConvGeo {
         if (y < 0 || y >= H || x < 0 || x >= W) return bz();
         return in[((size_t)(b * H + y) * W + x) * C + ci];
     }
+    // patch elements k .. k+7 (C a multiple of 8, k a multiple of 8: one tap)
+    __device__ __forceinline__ uint4 patch8(const bf16* in, int m, int k) const {
+        const int hw = Ho * Wo;
+        const int b = m / hw, r = m - b * hw;
+        const int i = r / Wo, j = r - i * Wo;
+        const int tap = k / C, ci = k - tap * C;
+        const int kh = tap / 3, kw = tap - kh * 3;
+        const int y = 2 * i + kh - 1, x = 2 * j + kw - 1;
+        if (y < 0 || y >= H || x < 0 || x >= W) return make_uint4(0u, 0u, 0u, 0u);
+        return ld16(in + ((size_t)(b * H + y) * W + x) * C + ci);
+    }
 };
 
 struct ConvFwd {
@@ -177,6 +234,10 @@ struct ConvFwd {
     bf16* out;
     __device__ __forceinline__ bf16 loadA(int m, int k) const { return geo.patch(in, m, k); }
     __device__ __forceinline__ bf16 loadB(int k, int n) const { return W[(size_t)k * geo.Co + n]; }
+    __device__ __forceinline__ int vecA() const { return geo.C % 8 == 0 ? kVecAk : kVecANone; }
+    __device__ __forceinline__ uint4 loadA8(int m, int k) const { return geo.patch8(in, m, k); }
+    __device__ __forceinline__ int vecB() const { return geo.Co % 8 == 0 ? kVecBn : kVecBNone; }
+    __device__ __forceinline__ uint4 loadB8(int k, int n) const { return ld16(W + (size_t)k * geo.Co + n); }
     __device__ __forceinline__ void store(int m, int n, float v) const {
         out[(size_t)m * geo.Co + n] = __float2bfloat16_rn(fmaxf(v + bias[n], 0.f));
     }
@@ -191,6 +252,10 @@ struct FcFwd {
     int Kin, Nout;
     __device__ __forceinline__ bf16 loadA(int m, int k) const { return in[(size_t)m * Kin + k]; }
     __device__ __forceinline__ bf16 loadB(int k, int n) const { return W[(size_t)k * Nout + n]; }
+    __device__ __forceinline__ int vecA() const { return Kin % 8 == 0 ? kVecAk : kVecANone; }
+    __device__ __forceinline__ uint4 loadA8(int m, int k) const { return ld16(in + (size_t)m * Kin + k); }
+    __device__ __forceinline__ int vecB() const { return Nout % 8 == 0 ? kVecBn : kVecBNone; }
+    __device__ __forceinline__ uint4 loadB8(int k, int n) const { return ld16(W + (size_t)k * Nout + n); }
     __device__ __forceinline__ void store(int m, int n, float v) const {
         const float z = v + bias[n];
         if (outf) outf[(size_t)m * Nout + n] = z;
@@ -221,6 +286,25 @@ struct ConvDgrad {
         const int tap = k / geo.Co, co = k - tap * geo.Co;
         return W[((size_t)tap * geo.C + n) * geo.Co + co];
     }
+    // the upstream gradient and the weights are contiguous along co for a fixed tap
+    __device__ __forceinline__ int vecA() const { return geo.Co % 8 == 0 ? kVecAk : kVecANone; }
+    __device__ __forceinline__ uint4 loadA8(int m, int k) const {
+        const int hw = geo.H * geo.W;
+        const int b = m / hw, r = m - b * hw;
+        const int y = r / geo.W, x = r - y * geo.W;
+        const int tap = k / geo.Co, co = k - tap * geo.Co;
+        const int kh = tap / 3, kw = tap - kh * 3;
+        const int i2 = y + 1 - kh, j2 = x + 1 - kw;
+        if (i2 < 0 || j2 < 0 || (i2 & 1) || (j2 & 1)) return make_uint4(0u, 0u, 0u, 0u);
+        const int i = i2 >> 1, j = j2 >> 1;
+        if (i >= geo.Ho || j >= geo.Wo) return make_uint4(0u, 0u, 0u, 0u);
+        return ld16(gout + ((size_t)(b * geo.Ho + i) * geo.Wo + j) * geo.Co + co);
+    }
+    __device__ __forceinline__ int vecB() const { return geo.Co % 8 == 0 ? kVecBk : kVecBNone; }
+    __device__ __forceinline__ uint4 loadB8(int k, int n) const {
+        const int tap = k / geo.Co, co = k - tap * geo.Co;
+        return ld16(W + ((size_t)tap * geo.C + n) * geo.Co + co);
+    }
     __device__ __forceinline__ void store(int m, int n, float v) const {
         const size_t o = (size_t)m * geo.C + n;
         gin[o] = __bfloat162float(act_in[o]) > 0.f ? __float2bfloat16_rn(v) : bz();
@@ -239,6 +323,10 @@ struct FcDgrad {
         return goutf ? __float2bfloat16_rn(goutf[o]) : gout[o];
     }
     __device__ __forceinline__ bf16 loadB(int k, int n) const { return W[(size_t)n * Nout + k]; }
+    __device__ __forceinline__ int vecA() const { return goutf == nullptr && Nout % 8 == 0 ? kVecAk : kVecANone; }
+    __device__ __forceinline__ uint4 loadA8(int m, int k) const { return ld16(gout + (size_t)m * Nout + k); }
+    __device__ __forceinline__ int vecB() const { return Nout % 8 == 0 ? kVecBk : kVecBNone; }
+    __device__ __forceinline__ uint4 loadB8(int k, int n) const { return ld16(W + (size_t)n * Nout + k); }
     __device__ __forceinline__ void store(int m, int n, float v) const {
         const size_t o = (size_t)m * Kin + n;
         gin[o] = __bfloat162float(act_in[o]) > 0.f ? __float2bfloat16_rn(v) : bz();
@@ -257,6 +345,14 @@ struct ConvWgrad {
         return geo.patch(in, k, m);
     }
     __device__ __forceinline__ bf16 loadB(int k, int n) const { return gout[(size_t)k * geo.Co + n]; }
+    // rows m .. m+7 of pixel k: channels of one tap, or the bias row of ones (m = 9 C, the last)
+    __device__ __forceinline__ int vecA() const { return geo.C % 8 == 0 ? kVecAm : kVecANone; }
+    __device__ __forceinline__ uint4 loadA8(int m, int k) const {
+        if (m == 9 * geo.C) return make_uint4((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(1.f)), 0u, 0u, 0u);
+        return geo.patch8(in, k, m);
+    }
+    __device__ __forceinline__ int vecB() const { return geo.Co % 8 == 0 ? kVecBn : kVecBNone; }
+    __device__ __forceinline__ uint4 loadB8(int k, int n) const { return ld16(gout + (size_t)k * geo.Co + n); }
     __device__ __forceinline__ void store(int m, int n, float v) const {
         if (m == 9 * geo.C) atomicAdd(&db[n], v);
         else atomicAdd(&dW[(size_t)m * geo.Co + n], v);
@@ -277,6 +373,13 @@ struct FcWgrad {
         const size_t o = (size_t)k * Nout + n;
         return goutf ? __float2bfloat16_rn(goutf[o]) : gout[o];
     }
+    __device__ __forceinline__ int vecA() const { return Kin % 8 == 0 ? kVecAm : kVecANone; }
+    __device__ __forceinline__ uint4 loadA8(int m, int k) const {
+        if (m == Kin) return make_uint4((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(1.f)), 0u, 0u, 0u);
+        return ld16(in + (size_t)k * Kin + m);
+    }
+    __device__ __forceinline__ int vecB() const { return goutf == nullptr && Nout % 8 == 0 ? kVecBn : kVecBNone; }
+    __device__ __forceinline__ uint4 loadB8(int k, int n) const { return ld16(gout + (size_t)k * Nout + n); }
     __device__ __forceinline__ void store(int m, int n, float v) const {
         if (m == Kin) atomicAdd(&db[n], v);
         else atomicAdd(&dW[(size_t)m * Nout + n], v);

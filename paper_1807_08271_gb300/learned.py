@@ -125,10 +125,14 @@ class LearnedAligner:
 
     The pairs' descriptors live in a device table uploaded once by
     ``set_pairs`` (a copy from pageable memory would stall the stream if it
-    were made per alignment); ``align(slot, ...)`` aligns the pair in a slot."""
+    were made per alignment); ``align(slot, ...)`` copies the pair's item into a
+    fixed device slot and, with ``graphs=True`` (the default), replays one CUDA
+    graph of the network's launches (input packing, the forward GEMMs and their
+    split-K reductions, the plan) on it: a dozen small launches whose enqueue
+    would otherwise cost more than their work."""
 
     def __init__(self, net: InitNet, thresholds, precision: int = R.PLANES_F32, levels: int = 4,
-                 iters=(5, 5, 5, 10), params: R.AlignParams | None = None):
+                 iters=(5, 5, 5, 10), params: R.AlignParams | None = None, graphs: bool = True):
         import torch
         self.net, self.precision = net, precision
         self.thresholds = [float(t) for t in thresholds]
@@ -137,8 +141,15 @@ class LearnedAligner:
         dev = net.device
         self.x = torch.zeros((1, R.NET_IN_H, R.NET_IN_W, R.NET_IN_C), dtype=torch.bfloat16, device=dev)
         self.skipped = torch.zeros(1, dtype=torch.int32, device=dev)
-        self.d_src = self.d_dst = None
+        self.d_src = None
         self.n = 0
+        self.graphs = graphs
+        self._graph = None
+        import ctypes
+        size = ctypes.sizeof(R.BatchItem)
+        # the current pair's item (input of the network and of the plan) and its plan
+        self.d_one = torch.zeros(size, dtype=torch.uint8, device=dev)
+        self.d_plan = torch.zeros(size, dtype=torch.uint8, device=dev)
 
     def set_pairs(self, pairs):
         """pairs: list of (ref, cur) pyramid descriptors; uploads their items."""
@@ -156,23 +167,38 @@ class LearnedAligner:
                 it.iters[l] = self.iters[l] if l < len(self.iters) else 0
         raw = np.frombuffer(bytes(table), dtype=np.uint8)[: n * ctypes.sizeof(R.BatchItem)].copy()
         self.d_src = torch.from_numpy(raw).to(self.net.device)
-        self.d_dst = torch.zeros_like(self.d_src)
         self.pairs = list(pairs)
         self.n = n
+
+    def _plan(self, stream=None):
+        """The network on the item in d_one and the plan into d_plan (no host state)."""
+        R.rgbid_net_inputs(self.d_one, 1, self.precision, self.x, stream)
+        R.rgbid_net_forward(self.net.params, self.x, 1, self.net.y, self.net.ws, stream)
+        R.rgbid_net_plan(self.net.y, 1, self.thresholds, self.d_one, self.d_plan, self.skipped, stream)
 
     def align(self, slot: int, workspace, result, stream=None):
         """Enqueue the learned-start alignment of pair ``slot`` into ``result``."""
         import ctypes
+        import torch
         assert 0 <= slot < self.n
         size = ctypes.sizeof(R.BatchItem)
-        src = _DevicePtr(self.d_src.data_ptr() + slot * size)
-        dst = self.d_dst.data_ptr() + slot * size
-        R.rgbid_net_inputs(src, 1, self.precision, self.x, stream)
-        R.rgbid_net_forward(self.net.params, self.x, 1, self.net.y, self.net.ws, stream)
-        R.rgbid_net_plan(self.net.y, 1, self.thresholds, src, _DevicePtr(dst), self.skipped, stream)
-        self.params.level_iters = dst + R.BatchItem.iters.offset
+        s = stream if stream is not None else torch.cuda.current_stream()
+        with torch.cuda.stream(s):
+            self.d_one.copy_(self.d_src[slot * size:(slot + 1) * size], non_blocking=True)
+            if self.graphs:
+                if self._graph is None:
+                    torch.cuda.synchronize()
+                    g = torch.cuda.CUDAGraph()
+                    with torch.cuda.graph(g):
+                        self._plan()
+                    self._graph = g
+                self._graph.replay()
+            else:
+                self._plan(s)
+        self.params.level_iters = self.d_plan.data_ptr() + R.BatchItem.iters.offset
         ref, cur = self.pairs[slot]
-        R.rgbid_align(ref, cur, _DevicePtr(dst + R.BatchItem.T_init.offset), self.params, workspace, result, stream)
+        R.rgbid_align(ref, cur, _DevicePtr(self.d_plan.data_ptr() + R.BatchItem.T_init.offset), self.params,
+                      workspace, result, stream)
 
 
 class _DevicePtr:

@@ -315,15 +315,17 @@ def evaluate_per_pair(net: InitNet, ev: EvalSet, thresholds, n: int) -> dict:
                          converged_fraction=float(np.mean(ok)),
                          median_rot_err_vs_truth_rad=float(np.median([pose_diff(r["T"], T)[0]
                                                                       for r, T in zip(rr, ev.T_gt)])))
-    # the network's share: inputs, forward pass and plan of every pair alone
+    # the network's share: the pair's item copied into place, then the inputs, forward
+    # pass and plan (one graph replay in the aligner) of every pair alone
+    size = ctypes.sizeof(R.BatchItem)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for i in range(n):
-        src = la.d_src.data_ptr() + i * ctypes.sizeof(R.BatchItem)
-        R.rgbid_net_inputs(_Ptr(src), 1, R.PLANES_F32, la.x)
-        R.rgbid_net_forward(la.net.params, la.x, 1, la.net.y, la.net.ws)
-        R.rgbid_net_plan(la.net.y, 1, la.thresholds, _Ptr(src), _Ptr(la.d_dst.data_ptr() + i * ctypes.sizeof(R.BatchItem)),
-                         la.skipped)
+        la.d_one.copy_(la.d_src[i * size:(i + 1) * size], non_blocking=True)
+        if la._graph is not None:
+            la._graph.replay()
+        else:
+            la._plan()
     e1.record()
     torch.cuda.synchronize()
     out["network_ms_per_pair"] = e0.elapsed_time(e1) / n
