@@ -171,6 +171,43 @@ class Tracker:
             self._frame(SI, SW, kf, torch.cuda.current_stream())
         self._graph[(kf, slot)] = g
 
+    def save_state(self, path: str):
+        """Write what the next frame depends on to an .npz file: the frame count, the
+        keyframe planes, the motion model's poses and the per-frame results so far.
+        A tracker built with the same arguments continues after ``load_state`` with
+        the bits an uninterrupted run would give."""
+        torch = self.torch
+        torch.cuda.synchronize(self.device)
+        arrays = dict(k=np.array(self.k), I_kf=self.I_kf.cpu().numpy(), W_kf=self.W_kf.cpu().numpy(),
+                      C_kf=self.C_kf.cpu().numpy(), T1=self.T1.cpu().numpy(), T2=self.T2.cpu().numpy(),
+                      is_kf=self.is_kf[:self.k].copy(), results=self.results[:self.k].cpu().numpy())
+        if self.kf_covisibility is not None:
+            arrays.update(kf_flags=self.kf_flags[:self.k].cpu().numpy(), ratios=self.ratios[:self.k].cpu().numpy())
+        np.savez(path, **arrays)
+
+    def load_state(self, path: str, stream=None):
+        """Restore a state written by ``save_state`` and rebuild the keyframe pyramid."""
+        torch = self.torch
+        d = np.load(path)
+        k = int(d["k"])
+        if k > self.results.shape[0] or d["I_kf"].shape != tuple(self.I_kf.shape):
+            raise ValueError("saved state does not fit this tracker")
+        if ("kf_flags" in d) != (self.kf_covisibility is not None):
+            raise ValueError("saved state and tracker differ in the keyframe policy")
+        for name in ("I_kf", "W_kf", "C_kf", "T1", "T2"):
+            getattr(self, name).copy_(torch.from_numpy(d[name]))
+        self.results[:k].copy_(torch.from_numpy(d["results"]))
+        if self.kf_covisibility is not None:
+            self.kf_flags[:k].copy_(torch.from_numpy(d["kf_flags"]))
+            self.ratios[:k].copy_(torch.from_numpy(d["ratios"]))
+        self.is_kf[:] = False
+        self.is_kf[:k] = d["is_kf"]
+        if k > 0:
+            self.kfp.build(self.I_kf, self.W_kf, self.K, stream)
+            if self.ws is None:
+                self.ws = R.new_workspace(self.kfp.desc, self.params, self.device)
+        self.k = k
+
     def keyframe_flags(self) -> np.ndarray:
         """Per processed frame: True where the frame became the keyframe (frame 0 included)."""
         flags = self.is_kf[:self.k].copy()

@@ -1,4 +1,4 @@
-"""The tracker's two staging slots: frames uploaded from pinned host memory on
+"""The tracker's two staging slots, and its saved state.  Frames uploaded from pinned host memory on
 a copy stream into the slot the next frame will read, while the current frame
 runs (the end-to-end form of the benchmark), give the same bits as enqueueing
 every launch of every frame eagerly, and every (frame kind, slot) graph is
@@ -64,3 +64,32 @@ def test_side_stream_uploads_into_alternating_slots_equal_the_eager_run():
     assert np.array_equal(trk.results.cpu().numpy(), eager.results.cpu().numpy())
     for a, b in ((trk.I_kf, eager.I_kf), (trk.W_kf, eager.W_kf), (trk.C_kf, eager.C_kf)):
         assert torch.equal(a, b)
+
+
+def test_saved_state_resumes_with_the_bits_of_an_uninterrupted_run(tmp_path):
+    """Tracking 40 frames straight through, and tracking 23, saving the state,
+    loading it into a new tracker and tracking the remaining 17 (across the switch
+    at frame 30 of a 15-frame keyframe period), give the same bits."""
+    n, cut = 40, 23
+    seq = synth.render_sequence(3, n_frames=n)
+    I = torch.from_numpy(seq["I"]).cuda()
+    W = torch.from_numpy(seq["W"]).cuda()
+    args = dict(levels=4, iters=(5, 5, 5, 10), kf_every=KF, max_frames=n)
+    full = Tracker(640, 480, seq["K"], **args)
+    for k in range(n):
+        full.step(I[k], W[k])
+    first = Tracker(640, 480, seq["K"], **args)
+    for k in range(cut):
+        first.step(I[k], W[k])
+    path = str(tmp_path / "state.npz")
+    first.save_state(path)
+    second = Tracker(640, 480, seq["K"], **args)
+    second.load_state(path)
+    for k in range(cut, n):
+        second.step(I[k], W[k])
+    torch.cuda.synchronize()
+    assert second.k == full.k == n
+    assert np.array_equal(second.results.cpu().numpy(), full.results.cpu().numpy())
+    for a, b in ((second.I_kf, full.I_kf), (second.W_kf, full.W_kf), (second.C_kf, full.C_kf)):
+        assert torch.equal(a, b)
+    assert np.array_equal(second.trajectory(), full.trajectory())
