@@ -154,6 +154,9 @@ def parse():
                          "start against the plain start")
     ap.add_argument("--precision", choices=["f32", "bf16"], default="f32",
                     help="plane storage: f32, or the reduced-precision form (bf16 I, fp16 W)")
+    ap.add_argument("--keyframes", choices=["every20", "covisibility"], default="every20",
+                    help="sequence workload: a new keyframe every 20 frames (default), or when the dense covisibility "
+                         "ratio of the aligned frame with the keyframe falls below 0.7 (decided on the device)")
     return ap.parse_args()
 
 
@@ -272,14 +275,19 @@ def reference(args):
     print(json.dumps(line))
 
 
-def config_dict(extra=None, precision="f32"):
+KF_COVISIBILITY = 0.7
+
+
+def config_dict(extra=None, precision="f32", keyframes="every20"):
+    kf = ("keyframe every 20 frames" if keyframes == "every20" else
+          f"new keyframe when the covisibility ratio with it falls below {KF_COVISIBILITY}")
     d = {"workload": "synthetic 640x480 room sequence, 300 frames at 30 Hz; frame-to-keyframe alignment on a "
-                     "4-level pyramid [10,5,5,5] iterations, fusion of every frame, keyframe every 20 frames",
+                     f"4-level pyramid [10,5,5,5] iterations, fusion of every frame, {kf}",
          "width": W, "height": H, "levels": LEVELS, "iters_fine_to_coarse": list(ITERS),
-         "frames": N_FRAMES, "keyframe_every": KF_EVERY,
+         "frames": N_FRAMES, "keyframes": kf,
          "precision": ("plain FP32 planes" if precision == "f32" else
                        "bf16 intensity / fp16 inverse-depth planes, FP32 residuals, compensated FP32 sums, "
-                       "FP64 6x6 solve and update"),
+                       "FP32 Cholesky refined by one FP64 step, FP64 pose update"),
          "l2": "flushed between steps (512 MiB write), outside the timed intervals",
          "e2e": "each frame copied from pinned host memory into one of the tracker's two staging slots; frame k+1's "
                 "copy runs on a copy stream during frame k, inside frame k's timed interval (gated on its start)"}
@@ -318,15 +326,19 @@ def native(args):
     timer_sweep = R.KernelTimer(R.KERNEL_SWEEP, per_step_launches * max(1, min(args.steps, 60)) + 8)
     prec = R.PLANES_BF16_F16 if args.precision == "bf16" else R.PLANES_F32
     bytes_per_unit = BYTES_PER_UNIT[args.precision]
+    covis = KF_COVISIBILITY if args.keyframes == "covisibility" else None
     trk = Tracker(W, H, K, levels=LEVELS, iters=ITERS, kf_every=KF_EVERY, max_frames=N_FRAMES + 1, device=dev,
-                  precision=prec)
+                  precision=prec, kf_covisibility=covis)
 
     launches = {"n": 0}
 
     def kernels_in_step(k):
         # frame pyramid (one launch, every level) + predict + init + 2 per iteration
-        # + the closing reduction + fuse, or switch (compose + init_kf) + kf pyramid
+        # + the closing reduction + kf pyramid, and then fuse, or switch (compose +
+        # init_kf), or with the covisibility policy: covisibility + decision + fuse-or-switch
         n = 1 + 1 + 1 + 2 * per_step_launches + 1 + 1
+        if covis is not None:
+            return n + 3
         n += 2 if k % KF_EVERY == 0 else 1
         return n
 
@@ -485,31 +497,42 @@ def native(args):
     # every frame of a fresh GPU pass over the whole sequence against the FP64 oracle's
     # tracking of it (stored; seed 0): alignment poses kf_T_k and world poses
     pose_check = None
-    gold = golden("seq640_oracle.json")
+    gold = golden("seq640_oracle.json" if covis is None else "seq640_covis_oracle.json")
     if gold is not None and rank == 0:
-        chk = Tracker(W, H, K, levels=LEVELS, iters=ITERS, kf_every=KF_EVERY, max_frames=N_FRAMES, device=dev,
-                      precision=prec)
-        for k in range(N_FRAMES):
+        n_chk = N_FRAMES if covis is None else len(gold["fp32_planes"]["frames"]) + 1
+        chk = Tracker(W, H, K, levels=LEVELS, iters=ITERS, kf_every=KF_EVERY, max_frames=n_chk, device=dev,
+                      precision=prec, kf_covisibility=covis)
+        for k in range(n_chk):
             chk.step(I_all[k], W_all[k])
         torch.cuda.synchronize()
         gT, gr = chk.trajectory(), chk.frame_results()
-        pose_check = {"frames": f"1..{N_FRAMES - 1}",
+        pose_check = {"frames": f"1..{n_chk - 1}",
                       "status": sorted(set(int(x["status"]) for x in gr)),
                       "max_rot_err_vs_truth_rad": max(pose_err(seq["T_wc"][0] @ gT[k], seq["T_wc"][k])[0]
-                                                      for k in range(N_FRAMES))}
+                                                      for k in range(n_chk))}
+        if covis is not None:
+            fr = gold["fp32_planes"]["frames"]
+            flags = chk.keyframe_flags()[1:]
+            pose_check["keyframe_switches"] = [int(k) + 1 for k in np.argwhere(flags).ravel()]
+            pose_check["switches_equal_oracle"] = bool(np.array_equal(flags, [f["switch"] for f in fr]))
+            pose_check["max_covisibility_diff"] = float(np.max(np.abs(chk.covisibility_ratios()
+                                                                      - [f["covisibility"] for f in fr])))
         planes = (("reduced_planes", "fp32_planes") if args.precision == "bf16" else ("fp32_planes",))
+        if covis is not None:
+            planes = ("fp32_planes",) if args.precision == "f32" else ()
         for name in planes:
             fr = gold[name]["frames"]
             pose_check[f"alignment_vs_oracle_{name}"] = err_stats(
                 [pose_err(np.array(o["T"]).reshape(4, 4), x["T"]) for o, x in zip(fr, gr)])
             pose_check[f"world_vs_oracle_{name}"] = err_stats(
                 [pose_err(np.array(o["T_world"]).reshape(4, 4), gT[o["k"]]) for o in fr])
-        pose_check["oracle"] = "stored FP64 oracle tracking of this sequence (tests/golden/seq640_oracle.json)"
+        pose_check["oracle"] = ("stored FP64 oracle tracking of this sequence (tests/golden/"
+                                + ("seq640_oracle.json)" if covis is None else "seq640_covis_oracle.json)"))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": config_dict(precision=args.precision),
+        "config": config_dict(precision=args.precision, keyframes=args.keyframes),
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 2 * W * H * 4,
                 "d2h_bytes_per_step": R.RESULT_BYTES},
         "roofline": roofline, "roofline_other_kernels": others,
@@ -518,7 +541,7 @@ def native(args):
         "cpu_baseline": cpu, "clocks": clk, "gpu_launches": gpu_launches,
         "wall_s_timed": t_wall, "max_rot_err_vs_truth_rad": rot, "pose_check": pose_check,
     }
-    if world == 1 and args.precision == "f32" and not args.no_extensions:
+    if world == 1 and args.precision == "f32" and args.keyframes == "every20" and not args.no_extensions:
         line["extensions"] = run_extensions(args)
     print(json.dumps(line))
     if dist:
@@ -531,6 +554,7 @@ EXTENSION_RUNS = {
     "batched": (["--workload", "batch", "--steps", "120"], ("per_pair_form",)),
     "batched_bf16": (["--workload", "batch", "--precision", "bf16", "--steps", "120"], ("per_pair_form",)),
     "precision_bf16": (["--precision", "bf16", "--steps", "120"], ()),
+    "keyframes_by_covisibility": (["--keyframes", "covisibility", "--steps", "120"], ()),
     "learned": (["--workload", "learned", "--steps", "256"], ("per_pair", "batched", "equal_accuracy")),
 }
 

@@ -9,9 +9,10 @@ the plane sums over the pixels fused at least once.  Calls only oracle/ and the
 seeded input generator; the two plane sets run in two spawned processes.
 
 With --covisibility THR it writes tests/golden/seq640_covis_oracle.json
-instead: the float32 planes tracked with the keyframe switched whenever the
-covisibility ratio of the aligned frame with its keyframe falls below THR,
-with each frame's ratio and switch decision.
+instead: the first --frames frames of the same sequence on the float32 planes,
+tracked with the keyframe switched whenever the covisibility ratio of the
+aligned frame with its keyframe falls below THR, with each frame's ratio and
+switch decision.
 
     python tests/golden/make_seq_oracle_poses.py [--frames N] [--covisibility THR]
 """
@@ -27,15 +28,18 @@ sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 import numpy as np  # noqa: E402
 
 GRID = (slice(3, None, 16), slice(3, None, 16))
+SEQ_FRAMES = 300
 
 
 def _track(args):
     import oracle as O
     from paper_1807_08271_gb300 import synth
     reduced, n, covis = args
-    seq = synth.render_sequence(0, n_frames=n)
+    # the benchmark's 300-frame sequence (its trajectory depends on its length), first n frames tracked
+    seq = synth.render_sequence(0, n_frames=SEQ_FRAMES)
     o = O.track_sequence(seq["I"], seq["W"], seq["K"], levels=4, iters=(5, 5, 5, 10),
-                         kf_every=None if covis is not None else 20, reduced=reduced, kf_covisibility=covis)
+                         kf_every=None if covis is not None else 20, reduced=reduced, kf_covisibility=covis,
+                         n_frames=n)
     frames = []
     for k, r in enumerate(o["results"], start=1):
         frames.append({"k": k, "T": r["T"].reshape(-1).tolist(), "T_world": o["T_world"][k].reshape(-1).tolist(),
@@ -61,7 +65,7 @@ def main():
     a = ap.parse_args()
     if a.covisibility is not None:
         _, res = _track((False, a.frames, a.covisibility))
-        out = {"config": f"640x480 room sequence, seed 0, {a.frames} frames, 4 levels, iterations [5, 5, 5, 10] "
+        out = {"config": f"640x480 room sequence, seed 0, first {a.frames} of its 300 frames, 4 levels, iterations [5, 5, 5, 10] "
                          f"finest first, keyframe switch when the covisibility ratio falls below {a.covisibility}, "
                          "FP64 oracle (oracle.track_sequence)", "threshold": a.covisibility, "fp32_planes": res}
         with open(os.path.join(HERE, "seq640_covis_oracle.json"), "w") as f:

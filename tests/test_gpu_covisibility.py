@@ -92,12 +92,14 @@ def test_tracker_switches_keyframes_on_covisibility_like_the_oracle():
     n = len(fr) + 1
     vr_o = np.array([f["covisibility"] for f in fr])
     sw_o = np.array([f["switch"] for f in fr])
-    # the decisions of this sequence are not within FP32 counting noise of the threshold
-    assert np.min(np.abs(vr_o - thr)) > 5e-4
+    # the decisions of this sequence are not within FP32 counting noise of the threshold:
+    # a ratio moves by (pixels whose FP64 decision sits at an FP32 rounding boundary) / |S_H|,
+    # a few pixels in ~250,000, far below the 2e-4 margin asked of every frame here
+    assert np.min(np.abs(vr_o - thr)) > 2e-4
     assert 2 <= sw_o.sum() <= n // 4
-    seq = synth.render_sequence(0, n_frames=n)
-    I_all = torch.from_numpy(seq["I"]).cuda()
-    W_all = torch.from_numpy(seq["W"]).cuda()
+    seq = synth.render_sequence(0, n_frames=300)      # the benchmark's sequence, its first n frames tracked
+    I_all = torch.from_numpy(seq["I"][:n]).cuda()
+    W_all = torch.from_numpy(seq["W"][:n]).cuda()
     trk = Tracker(640, 480, seq["K"], levels=4, iters=(5, 5, 5, 10), max_frames=n, kf_covisibility=thr)
     for k in range(n):
         trk.step(I_all[k], W_all[k])
@@ -105,7 +107,7 @@ def test_tracker_switches_keyframes_on_covisibility_like_the_oracle():
     flags = trk.keyframe_flags()
     ratios = trk.covisibility_ratios()
     assert np.array_equal(flags[1:], sw_o), (np.argwhere(flags[1:] != sw_o).ravel() + 1).tolist()
-    assert np.abs(ratios - vr_o).max() <= 5e-4, np.abs(ratios - vr_o).max()
+    assert np.abs(ratios - vr_o).max() <= 2e-4, np.abs(ratios - vr_o).max()
     res = trk.frame_results()
     world = trk.trajectory()
     for r, o in zip(res, fr):
