@@ -154,6 +154,8 @@ def parse():
                          "start against the plain start")
     ap.add_argument("--precision", choices=["f32", "bf16"], default="f32",
                     help="plane storage: f32, or the reduced-precision form (bf16 I, fp16 W)")
+    ap.add_argument("--no-level-kernel", action="store_true",
+                    help="run every level by the per-iteration kernels (no persistent level kernel)")
     ap.add_argument("--keyframes", choices=["every20", "covisibility"], default="every20",
                     help="sequence workload: a new keyframe every 20 frames (default), or when the dense covisibility "
                          "ratio of the aligned frame with the keyframe falls below 0.7 (decided on the device)")
@@ -324,19 +326,22 @@ def native(args):
     # sweep kernel over the end-to-end steps (one kernel per timed region)
     timer_robust = R.KernelTimer(R.KERNEL_ROBUST, (per_step_launches + 1) * max(1, min(args.steps, 60)) + 8)
     timer_sweep = R.KernelTimer(R.KERNEL_SWEEP, per_step_launches * max(1, min(args.steps, 60)) + 8)
+    timer_level = R.KernelTimer(R.KERNEL_LEVEL, LEVELS * max(1, min(args.steps, 60)) + 8)
     prec = R.PLANES_BF16_F16 if args.precision == "bf16" else R.PLANES_F32
     bytes_per_unit = BYTES_PER_UNIT[args.precision]
     covis = KF_COVISIBILITY if args.keyframes == "covisibility" else None
     trk = Tracker(W, H, K, levels=LEVELS, iters=ITERS, kf_every=KF_EVERY, max_frames=N_FRAMES + 1, device=dev,
-                  precision=prec, kf_covisibility=covis)
+                  precision=prec, kf_covisibility=covis, level_kernel=not args.no_level_kernel)
+    align_launches = None      # known once the first frame has built the pyramids
 
     launches = {"n": 0}
 
     def kernels_in_step(k):
-        # frame pyramid (one launch, every level) + predict + init + 2 per iteration
-        # + the closing reduction + kf pyramid, and then fuse, or switch (compose +
-        # init_kf), or with the covisibility policy: covisibility + decision + fuse-or-switch
-        n = 1 + 1 + 1 + 2 * per_step_launches + 1 + 1
+        # frame pyramid (one launch, every level) + predict + the alignment (init, two
+        # per iteration or one level kernel per level, the closing reduction) + kf
+        # pyramid, and then fuse, or switch (compose + init_kf), or with the
+        # covisibility policy: covisibility + decision + fuse-or-switch
+        n = 1 + 1 + align_launches + 1
         if covis is not None:
             return n + 3
         n += 2 if k % KF_EVERY == 0 else 1
@@ -414,6 +419,8 @@ def native(args):
     # warm-up (also builds the library on first use and captures the frame graphs)
     run_steps(args.warmup, timed=False)
     torch.cuda.synchronize()
+    align_launches = trk.align_launches()
+    level_kernels = align_launches < 2 * per_step_launches + 2
     pipe["ready"] = None      # the first timed frame uploads inside its own interval
 
     # ---- device-resident timed region (no per-launch events: they would break the
@@ -449,7 +456,10 @@ def native(args):
     #      steps (CUDA events around every launch of that kernel on the tracker's stream)
     kern = {}
     n_kern = max(1, min(args.steps, 60))
-    for name, timer in (("robust_kernel", timer_robust), ("sweep_kernel", timer_sweep)):
+    timed_kernels = [("robust_kernel", timer_robust), ("sweep_kernel", timer_sweep)]
+    if level_kernels:
+        timed_kernels.append(("level_kernel", timer_level))
+    for name, timer in timed_kernels:
         timer.reset()
         timer.attach(trk.params)
         evk = run_steps(n_kern, timed=True)
@@ -501,7 +511,7 @@ def native(args):
     if gold is not None and rank == 0:
         n_chk = N_FRAMES if covis is None else len(gold["fp32_planes"]["frames"]) + 1
         chk = Tracker(W, H, K, levels=LEVELS, iters=ITERS, kf_every=KF_EVERY, max_frames=n_chk, device=dev,
-                      precision=prec, kf_covisibility=covis)
+                      precision=prec, kf_covisibility=covis, level_kernel=not args.no_level_kernel)
         for k in range(n_chk):
             chk.step(I_all[k], W_all[k])
         torch.cuda.synchronize()
@@ -533,6 +543,7 @@ def native(args):
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": config_dict(precision=args.precision, keyframes=args.keyframes),
+        "level_kernel": level_kernels, "align_launches_per_frame": align_launches,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 2 * W * H * 4,
                 "d2h_bytes_per_step": R.RESULT_BYTES},
         "roofline": roofline, "roofline_other_kernels": others,

@@ -93,7 +93,8 @@ typedef struct {
 typedef enum {
     RGBID_KERNEL_SWEEP = 0,      /* fused warp + residual + Jacobian + weight + reduce (+ solve) */
     RGBID_KERNEL_ROBUST = 1,     /* systematic sample + (mu, sigma, nu) */
-    RGBID_KERNEL_BATCH = 2       /* the persistent kernel of rgbid_align_batched (units are not counted) */
+    RGBID_KERNEL_BATCH = 2,      /* the persistent kernel of rgbid_align_batched (units are not counted) */
+    RGBID_KERNEL_LEVEL = 3       /* the persistent level kernel of rgbid_align (units: level pixels x iterations) */
 } rgbid_kernel_id;
 
 typedef struct {
@@ -135,6 +136,13 @@ typedef struct {
     const int* level_iters;      /* optional DEVICE array of RGBID_MAX_LEVELS ints read by the kernels
                                     (rgbid_align only): level l runs min(iters[l], level_iters[l])
                                     iterations; the launches of the others exit at once.  NULL: iters. */
+    int no_level_kernel;         /* 0 (default): rgbid_align runs a level whose systematic sample is every
+                                    pixel (w h <= sample_cap, and <= 20480 pixels) in one persistent
+                                    16-CTA cluster launch: each iteration warps the level once, takes its
+                                    residuals as the sample, and solves inside the cluster.  1: every
+                                    level by the per-iteration robust-scale and sweep kernels.  Both
+                                    compute the same steps (sums in another order). */
+    int pad2_;
 } rgbid_align_params;
 
 /* Result of an alignment (or of one evaluated step).  Lives in device memory
@@ -195,6 +203,12 @@ int rgbid_build_pyramid(const float* I0, const float* W0, int pitch0, int width,
  * (more with RGBID_WARP_FULL_RESOLUTION, whose sweeps take one row per thread
  * on every level). */
 size_t rgbid_align_workspace_bytes(const rgbid_pyramid* ref, const rgbid_align_params* params);
+
+/* Kernel launches one rgbid_align call with these arguments enqueues on the
+ * current device (the initialisation, the per-iteration robust-scale and sweep
+ * kernels or one level kernel per level, and the closing launch), or -1 when
+ * the arguments are invalid.  Host only. */
+int rgbid_align_launches(const rgbid_pyramid* ref, const rgbid_align_params* params);
 
 /* Align `cur` (B) to `ref` (A).  Both pyramids must have the same size,
  * precision and intrinsics.  `T_init` is 16 doubles (row-major A_T_B): a host

@@ -28,14 +28,13 @@
 
 #include "rgbid_cluster.cuh"
 #include "rgbid_device.cuh"
+#include "rgbid_level.h"
 #include "rgbid_util.h"
 
 namespace cg = cooperative_groups;
 
 namespace rgbid {
 
-constexpr int kRobustNT = 256;      // threads per CTA of the robust-scale cluster
-constexpr int kRobustMaxNV = 96;    // widest cluster reduction (the Chebyshev sums of both channels)
 constexpr int kSweepNT = 256;       // 8 warps
 constexpr int kTileW = 32;
 // Rows per thread of the sweep: 4 on a level of at least kSweepWidePixels (its blocks
@@ -69,6 +68,7 @@ struct RobustArgs {
     int update;               // 0: results only (one evaluated step), 1: also update the pose
     int min_valid;
     int finalize_only;        // 1: finish the previous sweep and stop (no robust estimation)
+    int state_after_wait;     // 1: the preceding launch writes the state (a level kernel): read it after the wait
     float nu_g[kNuGTerms];    // Chebyshev series of the nu equation's constant part on [nu_lo, nu_hi]
 };
 
@@ -132,135 +132,6 @@ __global__ void init_kernel(InitArgs a) {
 }
 
 // ---------------------------------------------------------------- robust scale (cluster)
-// All cluster-wide sums use the same fixed combine tree (warp butterfly, then
-// a shuffle tree over the 8 warps of a CTA, then a shuffle tree over the CTAs
-// of the cluster with compensated (TwoSum) pairs), so every thread of every
-// CTA sees bit-identical totals and takes identical branches.
-
-template <int CL>
-struct ClusterSum {
-    float (*red_w)[kRobustMaxNV];             // per-warp partials [8][NV]
-    float2 (*recv)[CL][kRobustMaxNV];         // receive buffers [2][CL][NV]
-    float* out;                               // [NV] cluster totals
-    unsigned long long* mbar;                 // [2]
-    int* timeouts;                            // device counter of expired waits
-    uint32_t rank;
-    int round;
-    long long budget = kWaitBudgetCycles;     // clock64 cycles a wait may take before it gives up
-
-    // One all-to-all round in three parts.  arm<NV>(): thread 0 announces the round's
-    // bytes (CL sources x NV values) on this CTA's barrier.  send(t, r, s): the calling
-    // thread pushes this CTA's compensated partial of value t into CTA r (st.async
-    // completes the bytes on r's barrier).  receive<NV>(t): threads t < NV wait for
-    // value t from every CTA and return the total, summed over the ranks in the same
-    // pairwise tree in every CTA, so every CTA holds bit-identical totals.  Spreading
-    // the CL x NV sends over the threads keeps the issue of the round's stores short.
-    // The caller separates rounds with __syncthreads and next().
-    template <int NV>
-    __device__ __forceinline__ void arm() {
-        if (threadIdx.x == 0) mbar_arrive_expect_tx(&mbar[round & 1], (uint32_t)(CL * NV * sizeof(float2)));
-    }
-    __device__ __forceinline__ void send(int t, int r, F2 s) {
-        const int par = round & 1;
-        st_async_f2(map_to_rank(smem_addr(&recv[par][rank][t]), (uint32_t)r), s.hi, s.lo,
-                    map_to_rank(smem_addr(&mbar[par]), (uint32_t)r));
-    }
-    template <int NV>
-    __device__ __forceinline__ F2 receive(int t) {
-        const int par = round & 1;
-        const uint32_t phase = (uint32_t)(round >> 1) & 1u;
-        const long long t0 = clock64();
-        while (!mbar_try_wait(&mbar[par], phase)) {
-            if (clock64() - t0 > budget) {
-                atomicAdd(timeouts, 1);
-                break;
-            }
-        }
-        // fixed pairwise tree over the CL source CTAs
-        F2 acc[CL];
-#pragma unroll
-        for (int r = 0; r < CL; ++r) {
-            const float2 p = recv[par][r][t];
-            acc[r] = F2{p.x, p.y};
-        }
-#pragma unroll
-        for (int step = 1; step < CL; step <<= 1)
-#pragma unroll
-            for (int r = 0; r < CL; ++r)      // constant trip count: acc stays in registers
-                if (r % (2 * step) == 0 && r + step < CL) acc[r].add(acc[r + step]);
-        return acc[0];
-    }
-    // All CL x NV sends of a round, value t's partial given by part(t).
-    template <int NV, typename Part>
-    __device__ __forceinline__ void send_all(Part part) {
-        for (int p = (int)threadIdx.x; p < NV * CL; p += kRobustNT) {
-            const int t = p / CL, r = p - t * CL;
-            send(t, r, part(t));
-        }
-    }
-    // A round by one thread per value t < NV, which sends to every CTA itself
-    // (`do_send` = false withholds this CTA's partials: the wait-timeout probe).
-    template <int NV>
-    __device__ __forceinline__ F2 exchange(int t, F2 s, bool do_send = true) {
-        if (t == 0) mbar_arrive_expect_tx(&mbar[round & 1], (uint32_t)(CL * NV * sizeof(float2)));
-        if (do_send) {
-#pragma unroll
-            for (int r = 0; r < CL; ++r) send(t, r, s);
-        }
-        return receive<NV>(t);
-    }
-    __device__ __forceinline__ void next() { ++round; }
-
-    // The same round towards CTA 0 alone: every CTA pushes its partial of value t
-    // into CTA 0, which waits and returns the total (the same tree over the ranks);
-    // the other CTAs return at once.  For sums only CTA 0 consumes.
-    template <int NV>
-    __device__ __forceinline__ F2 gather(int t, F2 s) {
-        if (rank == 0 && t == 0) mbar_arrive_expect_tx(&mbar[round & 1], (uint32_t)(CL * NV * sizeof(float2)));
-        send(t, 0, s);
-        if (rank != 0) return F2{0.f, 0.f};
-        return receive<NV>(t);
-    }
-
-    // Block reduction of per-thread partials v[0..NV) (NV <= 8: one warp sum each;
-    // a multiple of 32: reduce-scatter chunks) into per-warp partials, summed over the
-    // warps in a fixed pairwise tree; then values t < NSEND go through the cluster: to
-    // every CTA (ROOT = false; out[] bit-identical in all CTAs) or to CTA 0 alone
-    // (ROOT = true; out[] valid in CTA 0 only).
-    template <int NV, int NSEND = NV, bool ROOT = false>
-    __device__ __forceinline__ void run(float (&v)[NV]) {
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        if constexpr (NV <= 8) {
-#pragma unroll
-            for (int j = 0; j < NV; ++j) {
-                const float x = warp_sum(v[j]);
-                if (lane == 0) red_w[warp][j] = x;
-            }
-        } else {
-            static_assert(NV % 32 == 0, "chunks of 32");
-#pragma unroll
-            for (int c = 0; c < NV / 32; ++c) {
-                float chunk[32];
-#pragma unroll
-                for (int i = 0; i < 32; ++i) chunk[i] = v[c * 32 + i];
-                red_w[warp][c * 32 + lane] = warp_reduce_scatter32(chunk);
-            }
-        }
-        __syncthreads();
-        const auto part = [&](int t) { return warp_tree<kRobustNT / 32>(red_w, t); };
-        const int t = threadIdx.x;
-        if constexpr (ROOT) {
-            if (t < NSEND) out[t] = gather<NSEND>(t, part(t)).value();
-        } else {
-            arm<NSEND>();
-            send_all<NSEND>(part);
-            if (t < NSEND) out[t] = receive<NSEND>(t).value();
-        }
-        __syncthreads();
-        next();
-    }
-};
-
 template <int PREC, int CL, bool FULL>
 __global__ void __launch_bounds__(kRobustNT) robust_kernel(RobustArgs a) {
     constexpr int MAXS = (RGBID_MAX_SAMPLES + CL * kRobustNT - 1) / (CL * kRobustNT);
@@ -302,20 +173,25 @@ __global__ void __launch_bounds__(kRobustNT) robust_kernel(RobustArgs a) {
     // the pose and its FP32 warp form, and the keyframe-side loads of the systematic
     // sample (A's planes do not change during an alignment).  Only the sweep's
     // partials and their count need the wait.
-    if (rank == 0) {
-        constexpr int kRobWords = (int)(sizeof(RobustParams) / 4);
-        if (threadIdx.x < kRobWords)
-            reinterpret_cast<int*>(&sh_rob_prev)[threadIdx.x] =
-                __ldcg(reinterpret_cast<const int*>(&a.st->rob) + threadIdx.x);
-        else if (threadIdx.x == 32) sh_cnt[0] = __ldcg(&a.st->iters_done);
-        else if (threadIdx.x == 33) sh_cnt[1] = __ldcg(&a.st->iters_skipped);
-        else if (threadIdx.x == 34) sh_cnt[2] = __ldcg(&a.st->status);
-    }
-    static_assert(sizeof(WarpPose) == 16 * sizeof(float), "the warp pose is 16 floats");
-    if (threadIdx.x >= 64 && threadIdx.x < 80) T_sh[threadIdx.x - 64] = __ldcg(a.st->T + (threadIdx.x - 64));
-    else if (threadIdx.x >= 96 && threadIdx.x < 112)
-        reinterpret_cast<float*>(&sh_wp)[threadIdx.x - 96] =
-            __ldcg(reinterpret_cast<const float*>(&a.st->wp) + (threadIdx.x - 96));
+    // A level kernel writes the state itself, so after one of them the state is read
+    // only once the wait is over.
+    const auto load_state = [&]() {
+        if (rank == 0) {
+            constexpr int kRobWords = (int)(sizeof(RobustParams) / 4);
+            if (threadIdx.x < kRobWords)
+                reinterpret_cast<int*>(&sh_rob_prev)[threadIdx.x] =
+                    __ldcg(reinterpret_cast<const int*>(&a.st->rob) + threadIdx.x);
+            else if (threadIdx.x == 32) sh_cnt[0] = __ldcg(&a.st->iters_done);
+            else if (threadIdx.x == 33) sh_cnt[1] = __ldcg(&a.st->iters_skipped);
+            else if (threadIdx.x == 34) sh_cnt[2] = __ldcg(&a.st->status);
+        }
+        static_assert(sizeof(WarpPose) == 16 * sizeof(float), "the warp pose is 16 floats");
+        if (threadIdx.x >= 64 && threadIdx.x < 80) T_sh[threadIdx.x - 64] = __ldcg(a.st->T + (threadIdx.x - 64));
+        else if (threadIdx.x >= 96 && threadIdx.x < 112)
+            reinterpret_cast<float*>(&sh_wp)[threadIdx.x - 96] =
+                __ldcg(reinterpret_cast<const float*>(&a.st->wp) + (threadIdx.x - 96));
+    };
+    if (!a.state_after_wait) load_state();
     PxA sa[MAXS];
     int su[MAXS], sv[MAXS];
     {
@@ -335,6 +211,7 @@ __global__ void __launch_bounds__(kRobustNT) robust_kernel(RobustArgs a) {
         }
     }
     pdl_wait();  // the previous sweep's partials (and the state) are complete and visible
+    if (a.state_after_wait) load_state();
     cluster_wait();
     pdl_trigger();
     ClusterSum<CL> R{red_w, recv, tot, mbar, &a.st->timeouts, (uint32_t)rank, 0};
@@ -905,6 +782,7 @@ static int check_pyramids(const rgbid_pyramid* ref, const rgbid_pyramid* cur, co
     if (p->level_iters && misaligned(p->level_iters, 4)) return RGBID_ERR_INVALID_ARG;
     if (p->sample_cap < 1 || p->sample_cap > RGBID_MAX_SAMPLES) return RGBID_ERR_INVALID_ARG;
     if (p->warp_mode != RGBID_WARP_PER_LEVEL && p->warp_mode != RGBID_WARP_FULL_RESOLUTION) return RGBID_ERR_INVALID_ARG;
+    if (p->no_level_kernel != 0 && p->no_level_kernel != 1) return RGBID_ERR_INVALID_ARG;
     if (p->scale_iters < 0 || p->bisect_steps < 0 || p->bisect_steps > 60) return RGBID_ERR_INVALID_ARG;
     if (!(p->nu_lo > 0.0) || !(p->nu_hi > p->nu_lo) || !(p->nu0 > 0.0)) return RGBID_ERR_INVALID_ARG;
     // the Chebyshev form of the robustness equation needs alpha_min = (lo + hi)/(hi - lo) >= 1.4
@@ -1057,6 +935,8 @@ static cudaError_t launch_sweep(const SweepArgs& sa, cudaStream_t stream) {
 }
 
 static cudaError_t launch_robust_any(int prec, const RobustArgs& ra, cudaStream_t s) {
+    // every launch may read the pending partials and writes the state (and the record)
+    if (!ra.st || !ra.partials || !ra.res) return cudaErrorInvalidValue;
     return prec == RGBID_PLANES_F32 ? launch_robust<RGBID_PLANES_F32>(ra, s) : launch_robust<RGBID_PLANES_BF16_F16>(ra, s);
 }
 static cudaError_t launch_sweep_any(int prec, const SweepArgs& sa, cudaStream_t s) {
@@ -1090,7 +970,37 @@ static RobustArgs robust_args(const rgbid_pyramid* ref, const rgbid_pyramid* cur
     ra.update = 1;
     ra.min_valid = p->min_valid;
     ra.finalize_only = 0;
+    ra.state_after_wait = 0;
     return ra;
+}
+
+// A level whose systematic sample is every pixel runs in the persistent level kernel.
+static bool use_level_kernel(const rgbid_pyramid* ref, const rgbid_align_params* p, int l) {
+    if (p->no_level_kernel || p->warp_mode != RGBID_WARP_PER_LEVEL) return false;
+    const rgbid_level& L = ref->lv[l];
+    return level_kernel_takes(ref->precision, L.width, L.height, p->sample_cap);
+}
+
+static LevelArgs level_args(const rgbid_pyramid* ref, const rgbid_pyramid* cur, int l, const rgbid_align_params* p,
+                            AlignState* st, float* partials) {
+    LevelArgs la;
+    memset(&la, 0, sizeof(la));
+    la.A = level_dev(ref->lv[l]);
+    la.B = level_dev(cur->lv[l]);
+    la.st = st;
+    la.partials = reinterpret_cast<float2*>(partials);
+    la.iters = p->iters[l];
+    la.level_iters = p->level_iters;
+    la.level = l;
+    la.scale_iters = p->scale_iters;
+    la.bisect_steps = p->bisect_steps;
+    la.estimate_nu = p->estimate_nu;
+    la.min_valid = p->min_valid;
+    la.nu0 = (float)p->nu0;
+    la.nu_lo = p->nu_lo;
+    la.nu_hi = p->nu_hi;
+    nu_device_series(p->nu_lo, p->nu_hi, la.nu_g);
+    return la;
 }
 
 }  // namespace rgbid
@@ -1100,6 +1010,16 @@ using namespace rgbid;
 extern "C" size_t rgbid_align_workspace_bytes(const rgbid_pyramid* ref, const rgbid_align_params* params) {
     if (!ref || ref->levels < 1 || ref->levels > RGBID_MAX_LEVELS) return 0;
     return workspace_bytes_for(*ref, params && params->warp_mode == RGBID_WARP_FULL_RESOLUTION);
+}
+
+extern "C" int rgbid_align_launches(const rgbid_pyramid* ref, const rgbid_align_params* params) {
+    if (check_pyramids(ref, ref, params) != RGBID_OK) return -1;
+    int n = 2;   // the initialisation and the closing launch
+    for (int l = params->levels - 1; l >= 0; --l) {
+        if (params->iters[l] <= 0) continue;
+        n += use_level_kernel(ref, params, l) ? 1 : 2 * params->iters[l];
+    }
+    return n;
 }
 
 extern "C" int rgbid_align(const rgbid_pyramid* ref, const rgbid_pyramid* cur, const double* T_init, int T_init_on_device,
@@ -1128,11 +1048,26 @@ extern "C" int rgbid_align(const rgbid_pyramid* ref, const rgbid_pyramid* cur, c
 
     rgbid_timing* tm = params->timing;
     RobustArgs ra{};
+    bool after_level_kernel = false;   // the next robust-scale launch follows a level kernel
     for (int l = params->levels - 1; l >= 0; --l) {
         ra = robust_args(ref, cur, l, params, st);
+        // set before any level kernel: the closing launch takes `ra` of the finest level
         ra.partials = reinterpret_cast<const float2*>(partials);
         ra.res = d_result;
         ra.level_iters = params->level_iters;
+        if (params->iters[l] > 0 && use_level_kernel(ref, params, l)) {
+            const LevelArgs la = level_args(ref, cur, l, params, st, partials);
+            const bool tl = tm && tm->kernel == RGBID_KERNEL_LEVEL && tm->count < tm->capacity;
+            if (tl && cudaEventRecord((cudaEvent_t)tm->ev_start[tm->count], stream) != cudaSuccess) return RGBID_ERR_CUDA;
+            if (launch_level(ref->precision, la, stream) != cudaSuccess) return RGBID_ERR_CUDA;
+            if (tl) {
+                if (cudaEventRecord((cudaEvent_t)tm->ev_end[tm->count], stream) != cudaSuccess) return RGBID_ERR_CUDA;
+                tm->count += 1;
+                tm->units += (long long)la.A.w * la.A.h * params->iters[l];
+            }
+            after_level_kernel = true;
+            continue;
+        }
         SweepArgs sa;
         memset(&sa, 0, sizeof(sa));
         sa.A = ra.A;
@@ -1147,6 +1082,8 @@ extern "C" int rgbid_align(const rgbid_pyramid* ref, const rgbid_pyramid* cur, c
         for (int it = 0; it < params->iters[l]; ++it) {
             ra.iter = it;
             sa.iter = it;
+            ra.state_after_wait = after_level_kernel ? 1 : 0;
+            after_level_kernel = false;
             const bool tr = tm && tm->kernel == RGBID_KERNEL_ROBUST && tm->count < tm->capacity;
             if (tr && cudaEventRecord((cudaEvent_t)tm->ev_start[tm->count], stream) != cudaSuccess) return RGBID_ERR_CUDA;
             if (launch_robust_any(ref->precision, ra, stream) != cudaSuccess) return RGBID_ERR_CUDA;
@@ -1165,8 +1102,9 @@ extern "C" int rgbid_align(const rgbid_pyramid* ref, const rgbid_pyramid* cur, c
             }
         }
     }
-    // the last sweep's reduction, solve and update (no robust estimation)
+    // the last sweep's (or level kernel's) pending step: reduction, solve and update
     ra.finalize_only = 1;
+    ra.state_after_wait = after_level_kernel ? 1 : 0;
     const bool tr = tm && tm->kernel == RGBID_KERNEL_ROBUST && tm->count < tm->capacity;
     if (tr && cudaEventRecord((cudaEvent_t)tm->ev_start[tm->count], stream) != cudaSuccess) return RGBID_ERR_CUDA;
     if (launch_robust_any(ref->precision, ra, stream) != cudaSuccess) return RGBID_ERR_CUDA;

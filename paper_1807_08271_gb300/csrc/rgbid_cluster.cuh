@@ -236,4 +236,142 @@ __device__ __forceinline__ void accumulate(float (&acc)[kSlots], const float (&J
     acc[kSlotCost] = fmaf(w * r, r, acc[kSlotCost]);
 }
 
+// ---- cluster-wide sums of the per-pair alignment kernels
+constexpr int kRobustNT = 256;      // threads per CTA of the robust-scale cluster
+constexpr int kRobustMaxNV = 96;    // widest cluster reduction (the Chebyshev sums of both channels)
+
+// All cluster-wide sums use the same fixed combine tree (warp butterfly, then
+// a shuffle tree over the 8 warps of a CTA, then a shuffle tree over the CTAs
+// of the cluster with compensated (TwoSum) pairs), so every thread of every
+// CTA sees bit-identical totals and takes identical branches.
+
+template <int CL>
+struct ClusterSum {
+    float (*red_w)[kRobustMaxNV];             // per-warp partials [8][NV]
+    float2 (*recv)[CL][kRobustMaxNV];         // receive buffers [2][CL][NV]
+    float* out;                               // [NV] cluster totals
+    unsigned long long* mbar;                 // [2]
+    int* timeouts;                            // device counter of expired waits
+    uint32_t rank;
+    int round;
+    long long budget = kWaitBudgetCycles;     // clock64 cycles a wait may take before it gives up
+
+    // One all-to-all round in three parts.  arm<NV>(): thread 0 announces the round's
+    // bytes (CL sources x NV values) on this CTA's barrier.  send(t, r, s): the calling
+    // thread pushes this CTA's compensated partial of value t into CTA r (st.async
+    // completes the bytes on r's barrier).  receive<NV>(t): threads t < NV wait for
+    // value t from every CTA and return the total, summed over the ranks in the same
+    // pairwise tree in every CTA, so every CTA holds bit-identical totals.  Spreading
+    // the CL x NV sends over the threads keeps the issue of the round's stores short.
+    // The caller separates rounds with __syncthreads and next().
+    template <int NV>
+    __device__ __forceinline__ void arm() {
+        if (threadIdx.x == 0) mbar_arrive_expect_tx(&mbar[round & 1], (uint32_t)(CL * NV * sizeof(float2)));
+    }
+    __device__ __forceinline__ void send(int t, int r, F2 s) {
+        const int par = round & 1;
+        st_async_f2(map_to_rank(smem_addr(&recv[par][rank][t]), (uint32_t)r), s.hi, s.lo,
+                    map_to_rank(smem_addr(&mbar[par]), (uint32_t)r));
+    }
+    template <int NV>
+    __device__ __forceinline__ F2 receive(int t) {
+        const int par = round & 1;
+        const uint32_t phase = (uint32_t)(round >> 1) & 1u;
+        const long long t0 = clock64();
+        while (!mbar_try_wait(&mbar[par], phase)) {
+            if (clock64() - t0 > budget) {
+                atomicAdd(timeouts, 1);
+                budget = 0;       // the cluster's exchanges are broken: later waits give up at once
+                break;
+            }
+        }
+        // fixed pairwise tree over the CL source CTAs
+        F2 acc[CL];
+#pragma unroll
+        for (int r = 0; r < CL; ++r) {
+            const float2 p = recv[par][r][t];
+            acc[r] = F2{p.x, p.y};
+        }
+#pragma unroll
+        for (int step = 1; step < CL; step <<= 1)
+#pragma unroll
+            for (int r = 0; r < CL; ++r)      // constant trip count: acc stays in registers
+                if (r % (2 * step) == 0 && r + step < CL) acc[r].add(acc[r + step]);
+        return acc[0];
+    }
+    // All CL x NV sends of a round, value t's partial given by part(t).
+    template <int NV, typename Part>
+    __device__ __forceinline__ void send_all(Part part) {
+        for (int p = (int)threadIdx.x; p < NV * CL; p += kRobustNT) {
+            const int t = p / CL, r = p - t * CL;
+            send(t, r, part(t));
+        }
+    }
+    // A round by one thread per value t < NV, which sends to every CTA itself
+    // (`do_send` = false withholds this CTA's partials: the wait-timeout probe).
+    template <int NV>
+    __device__ __forceinline__ F2 exchange(int t, F2 s, bool do_send = true) {
+        if (t == 0) mbar_arrive_expect_tx(&mbar[round & 1], (uint32_t)(CL * NV * sizeof(float2)));
+        if (do_send) {
+#pragma unroll
+            for (int r = 0; r < CL; ++r) send(t, r, s);
+        }
+        return receive<NV>(t);
+    }
+    __device__ __forceinline__ void next() { ++round; }
+
+    // The same round towards CTA 0 alone: every CTA pushes its partial of value t
+    // into CTA 0, which waits and returns the total (the same tree over the ranks);
+    // the other CTAs return at once.  For sums only CTA 0 consumes.
+    template <int NV>
+    __device__ __forceinline__ F2 gather(int t, F2 s) {
+        if (rank == 0 && t == 0) mbar_arrive_expect_tx(&mbar[round & 1], (uint32_t)(CL * NV * sizeof(float2)));
+        send(t, 0, s);
+        if (rank != 0) return F2{0.f, 0.f};
+        return receive<NV>(t);
+    }
+
+    // Block reduction of per-thread partials v[0..NV) (NV <= 8: one warp sum each;
+    // a multiple of 32: reduce-scatter chunks) into per-warp partials, summed over the
+    // warps in a fixed pairwise tree; then values t < NSEND go through the cluster: to
+    // every CTA (ROOT = false; out[] bit-identical in all CTAs) or to CTA 0 alone
+    // (ROOT = true; out[] valid in CTA 0 only).
+    template <int NV, int NSEND = NV, bool ROOT = false>
+    __device__ __forceinline__ void run(float (&v)[NV]) {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        if constexpr (NV <= 8) {
+#pragma unroll
+            for (int j = 0; j < NV; ++j) {
+                const float x = warp_sum(v[j]);
+                if (lane == 0) red_w[warp][j] = x;
+            }
+        } else {
+            static_assert(NV % 32 == 0, "chunks of 32");
+#pragma unroll
+            for (int c = 0; c < NV / 32; ++c) {
+                float chunk[32];
+#pragma unroll
+                for (int i = 0; i < 32; ++i) chunk[i] = v[c * 32 + i];
+                red_w[warp][c * 32 + lane] = warp_reduce_scatter32(chunk);
+            }
+        }
+        __syncthreads();
+        const auto part = [&](int t) { return warp_tree<kRobustNT / 32>(red_w, t); };
+        const int t = threadIdx.x;
+        if constexpr (ROOT) {
+            if (t < NSEND) out[t] = gather<NSEND>(t, part(t)).value();
+        } else if constexpr (NSEND <= 8) {
+            // a few values: each is sent to every CTA by its own thread (shorter than
+            // spreading the sends, which makes every sender rebuild its warp tree)
+            if (t < NSEND) out[t] = exchange<NSEND>(t, part(t)).value();
+        } else {
+            arm<NSEND>();
+            send_all<NSEND>(part);
+            if (t < NSEND) out[t] = receive<NSEND>(t).value();
+        }
+        __syncthreads();
+        next();
+    }
+};
+
 }  // namespace rgbid

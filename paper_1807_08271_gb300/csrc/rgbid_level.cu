@@ -1,0 +1,517 @@
+// Persistent per-level alignment kernel (sm_103a).
+//
+// On a level whose systematic sample is every pixel (sample stride 1, "Error
+// distribution and robust optimisation"), the sample residuals of an iteration
+// are the residuals the level's sweep evaluates at the same pose.  One 16-CTA
+// cluster then runs all of the level's Gauss-Newton iterations ("Iterative
+// optimisation") in one launch, and each pixel is warped once per iteration:
+//   terms    every thread warps its <= MAXP pixels with the current pose; it keeps
+//            r_I and r_W (NaN where masked out) in registers and the Jacobians
+//            and lambda_n in shared memory;
+//   robust   Student-t (mu, sigma) at nu0 by the lagged-weight fixed point, then
+//            nu by bisection on the robustness equation, from those residuals;
+//            every sum goes through the cluster's distributed shared memory, and
+//            every CTA bisects the same totals, so all hold the same parameters;
+//   normal   the weighted 27 normal-equation terms, cost and counts of the CTA's
+//            pixels; one exchange gives every CTA the cluster totals;
+//   update   every CTA solves H xi = -g and applies T <- exp(xi)^-1 T to its copy
+//            of the FP64 pose; the copies stay bit-identical.
+// The level's last step is not solved here.  Its totals stay in the workspace as
+// one pending block partial, next to the robust parameters that weighted them,
+// exactly as a sweep leaves its partials; the next level's robust-scale kernel,
+// or the alignment's closing launch, solves from them and updates the pose.
+#include <cooperative_groups.h>
+#include <algorithm>
+#include <atomic>
+
+#include "rgbid_cluster.cuh"
+#include "rgbid_device.cuh"
+#include "rgbid_level.h"
+
+namespace cg = cooperative_groups;
+
+namespace rgbid {
+
+constexpr int kJTerms = 13;     // per pixel in shared memory: J_I (6), J_W (6), lambda_n
+
+template <int MAXP>
+constexpr size_t level_dyn_smem() {
+    return (size_t)MAXP * kJTerms * kRobustNT * sizeof(float);
+}
+
+// H xi = -g from the cluster totals (warp 0 of every CTA, identical inputs); a
+// solved step updates the CTA's FP64 pose and its FP32 warp form.  cnt holds
+// the alignment's iterations done and skipped and its status.
+template <int PREC>
+__device__ __forceinline__ void level_solve_update(const float* tot, int min_valid, double* T_sh, WarpPose* wp_sh,
+                                                   float* xi_f, float* d_f, double* rho_d, double* xi_d,
+                                                   int* ok_flag, int* cnt) {
+    const int lane = threadIdx.x & 31;
+    const bool ok_in = ((int)tot[kSlotNI] + (int)tot[kSlotNW]) >= min_valid;
+    if constexpr (PREC == RGBID_PLANES_BF16_F16) {
+        // reduced-precision planes: FP32 factorisation refined to an FP64 solution
+        const bool okl = warp_solve6_refined(tot, ok_in, xi_f, d_f, rho_d, xi_d);
+        if (lane == 0) *ok_flag = okl ? 1 : 0;
+    } else if (lane == 0) {
+        float xi[6];
+        const bool okl = ok_in && cholesky_solve6_slots(tot, xi);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) xi_f[i] = okl ? xi[i] : 0.f;
+        *ok_flag = okl ? 1 : 0;
+    }
+    __syncwarp();
+    const bool ok = *ok_flag != 0;
+    if (ok) {
+        if constexpr (PREC == RGBID_PLANES_BF16_F16) {
+            double xi[6];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) xi[i] = xi_d[i];
+            warp_apply_update_d(xi, T_sh);
+        } else {
+            float xi[6];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) xi[i] = xi_f[i];
+            warp_apply_update(xi, T_sh);
+        }
+        warp_make_pose(T_sh, wp_sh);
+    }   // else the pose is kept (a degenerate step)
+    if (lane == 0) {
+        cnt[0] += 1;
+        if (!ok) {
+            cnt[1] += 1;
+            cnt[2] = RGBID_ERR_DEGENERATE;
+        }
+    }
+    __syncwarp();
+}
+
+template <int PREC, int MAXP>
+__global__ void __launch_bounds__(kRobustNT, 1) level_kernel(LevelArgs a) {
+    constexpr int CL = kLevelCL, NT = kRobustNT, NW = NT / 32;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int tid = (int)threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    extern __shared__ __align__(16) float Jsm[];     // [MAXP][kJTerms][NT]
+    __shared__ float red_w[NW][kRobustMaxNV];
+    __shared__ float2 recv[2][CL][kRobustMaxNV];
+    __shared__ float tot[kRobustMaxNV];
+    __shared__ float2 tot2[kSlots];                 // the last step's totals as compensated pairs
+    __shared__ __align__(8) unsigned long long mbar[2];
+    __shared__ WarpPose sh_wp;
+    __shared__ double T_sh[16];
+    __shared__ float nu_out[2];
+    __shared__ float nuF[2][kNuSeries];
+    __shared__ float sh_g[kNuGTerms];
+    __shared__ F2 fin2[NW][kSlots];
+    __shared__ float xi_f[6], d_f[6];
+    __shared__ double xi_d[6], rho_d[6];
+    __shared__ int ok_flag;
+    __shared__ int sh_cnt[3];                       // iterations done, skipped, status
+
+    // the device count of the level, written before the alignment's first kernel
+    const int n_it = a.level_iters ? min(a.iters, __ldg(a.level_iters + a.level)) : a.iters;
+    if (n_it <= 0) {
+        pdl_wait();   // keeps the chain of dependent launches ordered; never triggers
+        return;
+    }
+    if (tid == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+#pragma unroll
+        for (int k = 0; k < kNuGTerms; ++k) sh_g[k] = a.nu_g[k];
+    }
+    // no CTA stores into another before every barrier of the cluster is initialised
+    cluster_arrive();
+    pdl_wait();   // the state and any pending partials of the preceding launches are visible
+    if (tid < 16) {
+        T_sh[tid] = __ldcg(a.st->T + tid);
+    } else if (tid < 32) {
+        reinterpret_cast<float*>(&sh_wp)[tid - 16] =
+            __ldcg(reinterpret_cast<const float*>(&a.st->wp) + (tid - 16));
+    } else if (tid == 32) {
+        sh_cnt[0] = __ldcg(&a.st->iters_done);
+    } else if (tid == 33) {
+        sh_cnt[1] = __ldcg(&a.st->iters_skipped);
+    } else if (tid == 34) {
+        sh_cnt[2] = __ldcg(&a.st->status);
+    }
+    const unsigned int nb = __ldcg(&a.st->pending);   // the same value in every CTA
+    cluster_wait();
+    ClusterSum<CL> R{red_w, recv, tot, mbar, &a.st->timeouts, (uint32_t)rank, 0};
+
+    // ---- a pending step of the previous level: the CTAs sum disjoint subsets of its
+    //      block partials, one exchange gives every CTA the totals, and every CTA
+    //      solves and updates its copy of the pose
+    if (nb) {
+        F2 acc{0.f, 0.f};
+        constexpr unsigned kStride = (unsigned)CL * NW;
+        for (unsigned int b0 = (unsigned)rank + (unsigned)CL * (unsigned)warp; b0 < nb; b0 += 4u * kStride) {
+            float2 v[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const unsigned int b = b0 + (unsigned)q * kStride;
+                v[q] = b < nb ? __ldcg(a.partials + (size_t)b * kSlots + lane) : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc.add(F2{v[q].x, v[q].y});
+        }
+        fin2[warp][lane] = acc;
+        __syncthreads();
+        if (tid < kSlots) tot[tid] = R.template exchange<kSlots>(tid, warp_tree<NW>(fin2, tid)).value();
+        __syncthreads();
+        R.next();
+        if (warp == 0) level_solve_update<PREC>(tot, a.min_valid, T_sh, &sh_wp, xi_f, d_f, rho_d, xi_d, &ok_flag, sh_cnt);
+    }
+    __syncthreads();
+
+    const int w = a.A.w, npix = a.A.w * a.A.h;
+    const int gt = rank * NT + tid;
+    const float nu0 = a.nu0;
+    const float lo0 = (float)a.nu_lo, hi0 = (float)a.nu_hi;
+    const float m = 0.5f * (lo0 + hi0), h = 0.5f * (hi0 - lo0);
+    float* const Jt = Jsm + tid;                     // this thread's column of the Jacobian store
+    for (int it = 0; it < n_it; ++it) {
+        const bool last = it + 1 == n_it;
+        const WarpPose wp = sh_wp;
+        // the next launch may be scheduled while the last step runs; it reads the
+        // state only after this grid has completed
+        if (last) pdl_trigger();
+
+        // ---- per-pixel terms at the current pose; the pixels of a thread go through
+        //      each stage together so their loads overlap
+        float rs[2][MAXP];
+        {
+            PxA sa[MAXP];
+            PxW sw[MAXP];
+            PxB sb[MAXP];
+            int pu[MAXP], pv[MAXP];
+#pragma unroll
+            for (int k = 0; k < MAXP; ++k) {
+                const int i = gt + k * (CL * NT);
+                sa[k].ok = false;
+                pu[k] = 0;
+                pv[k] = 0;
+                if (i < npix) {
+                    pv[k] = i / w;
+                    pu[k] = i - pv[k] * w;
+                    stage_a<PREC>(a.A, pu[k], pv[k], sa[k]);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < MAXP; ++k) stage_w(a.A, a.B, wp, pu[k], pv[k], sa[k], sw[k]);
+#pragma unroll
+            for (int k = 0; k < MAXP; ++k) stage_b<PREC>(a.B, sw[k], sb[k]);
+#pragma unroll
+            for (int k = 0; k < MAXP; ++k) {
+                PixelTerms o;
+                finish<true>(a.A, wp, sa[k], sw[k], sb[k], o);
+                rs[0][k] = o.mI ? o.rI : __int_as_float(0x7fc00000);
+                rs[1][k] = o.mW ? o.rW : __int_as_float(0x7fc00000);
+                float* const J = Jt + k * (kJTerms * NT);
+                if (o.mI) {
+#pragma unroll
+                    for (int j = 0; j < 6; ++j) J[j * NT] = o.JI[j];
+                }
+                if (o.mW) {
+#pragma unroll
+                    for (int j = 0; j < 6; ++j) J[(6 + j) * NT] = o.JW[j];
+                    J[12 * NT] = o.lam;
+                }
+            }
+        }
+
+        // ---- counts and mean square -> sigma0 (mu0 = 0)
+        {
+            float v4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int k = 0; k < MAXP; ++k) {
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    // masked pixels (NaN) add exact zeros: selects, not branches
+                    const float r = rs[c][k];
+                    const bool use = r == r;
+                    const float rv = use ? r : 0.f;
+                    v4[2 * c] += use ? 1.f : 0.f;
+                    v4[2 * c + 1] = fmaf(rv, rv, v4[2 * c + 1]);
+                }
+            }
+            R.run(v4);
+        }
+        const float n[2] = {tot[0], tot[2]};
+        float mu[2] = {0.f, 0.f};
+        float sig[2];
+        bool live[2];
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const float ms = n[c] > 0.f ? __fdividef(tot[2 * c + 1], n[c]) : 0.f;
+            sig[c] = ms > 0.f ? ms * rsqrtf(ms) : 0.f;
+            live[c] = n[c] > 0.f && sig[c] >= 1e-12f;
+        }
+
+        // ---- (mu, sigma) fixed point at nu0 with lagged weights:
+        //      mu <- sum w r / sum w ; sigma^2 <- sum w (r - mu_new)^2 / n, with d = r - mu_old
+        //      sum w (r - mu_new)^2 = S2 - S1^2 / S0.
+        for (int si = 0; si < a.scale_iters; ++si) {
+            if (!live[0] && !live[1]) break;
+            float v6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const float mc = mu[c];
+                const float s2 = sig[c] * sig[c];
+                const float s2nu = s2 * nu0;
+                const float num = (nu0 + 1.f) * s2;
+#pragma unroll
+                for (int k = 0; k < MAXP; ++k) {
+                    const float r = rs[c][k];
+                    const bool use = r == r;
+                    const float dr = r - mc;
+                    const float wr = __fdividef(num, fmaf(dr, dr, s2nu));   // omega((r - mu)/sigma, nu0)
+                    const float wv = use ? wr : 0.f, d = use ? dr : 0.f;
+                    v6[3 * c] += wv;
+                    v6[3 * c + 1] = fmaf(wv, d, v6[3 * c + 1]);
+                    v6[3 * c + 2] = fmaf(wv * d, d, v6[3 * c + 2]);
+                }
+            }
+            R.run(v6);
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                if (!live[c]) continue;
+                const float S0 = tot[3 * c], S1 = tot[3 * c + 1], S2 = tot[3 * c + 2];
+                const float delta = __fdividef(S1, S0);
+                mu[c] += delta;
+                const float var = __fdividef(fmaf(-S1, delta, S2), n[c]);
+                sig[c] = var > 0.f ? var * rsqrtf(var) : 0.f;
+                if (!(sig[c] >= 1e-12f)) live[c] = false;
+            }
+        }
+        bool ok[2];
+#pragma unroll
+        for (int c = 0; c < 2; ++c) ok[c] = n[c] > 0.f && sig[c] >= 1e-12f;
+
+        // ---- nu by bisection on eq. robustnessValue: the Chebyshev power sums of both
+        //      channels in packed pairs (low half I, high half W), exchanged to every CTA
+        float nu[2] = {nu0, nu0};
+        const bool do_nu = a.estimate_nu && (ok[0] || ok[1]);
+        if (do_nu) {
+            unsigned long long V[kChebVals];
+#pragma unroll
+            for (int i = 0; i < kChebVals; ++i) V[i] = 0ull;
+            const float is0 = ok[0] ? __fdividef(1.f, sig[0]) : 0.f;
+            const float is1 = ok[1] ? __fdividef(1.f, sig[1]) : 0.f;
+#pragma unroll 1
+            for (int k = 0; k < MAXP; ++k) {
+                float r0 = rs[0][0], r1 = rs[1][0];
+#pragma unroll
+                for (int q = 1; q < MAXP; ++q)
+                    if (k == q) {
+                        r0 = rs[0][q];
+                        r1 = rs[1][q];
+                    }
+                float q2[2], g2[2], l2[2];
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const float x = ((c ? r1 : r0) - mu[c]) * (c ? is1 : is0);
+                    const bool use = ok[c] && x == x;
+                    const float al = __fdividef(fmaf(x, x, m), h);
+                    const float s2 = fmaf(al, al, -1.f);
+                    const float gam = rsqrtf(s2);
+                    const float be = fmaf(s2, gam, al);
+                    q2[c] = use ? __fdividef(1.f, be) : 0.f;
+                    g2[c] = use ? gam : 0.f;
+                    l2[c] = use ? __logf(0.5f * be) : 0.f;
+                }
+                const unsigned long long Q = f2_pack(q2[0], q2[1]), G = f2_pack(g2[0], g2[1]);
+                V[0] = f2_add(V[0], f2_pack(l2[0], l2[1]));
+                V[1 + kChebK] = f2_add(V[1 + kChebK], G);          // G_0
+                unsigned long long qk = Q;
+#pragma unroll
+                for (int kk = 1; kk <= kChebK; ++kk) {
+                    V[kk] = f2_add(V[kk], qk);                       // P_k
+                    V[1 + kChebK + kk] = f2_fma(G, qk, V[1 + kChebK + kk]);   // G_k
+                    qk = f2_mul(qk, Q);
+                }
+            }
+            float v[96];
+#pragma unroll
+            for (int i = 0; i < kChebVals; ++i) {
+                v[i] = f2_lo(V[i]);
+                v[kChebVals + i] = f2_hi(V[i]);
+            }
+#pragma unroll
+            for (int i = 2 * kChebVals; i < 96; ++i) v[i] = 0.f;
+            R.template run<96, 2 * kChebVals, false>(v);
+            if (tid < 64) {
+                // warp c solves channel c, in every CTA on the same totals
+                const int c = tid >> 5;
+                float nuc = nu0;
+                if (ok[c]) nuc = bisect_nu_warp(tot + c * kChebVals, n[c], sh_g, lo0, hi0, a.bisect_steps, nuF[c]);
+                if (lane == 0) nu_out[c] = nuc;
+            }
+            __syncthreads();
+            nu[0] = nu_out[0];
+            nu[1] = nu_out[1];
+            if (ok[0] && ok[1]) nu[0] = fmaxf(nu[0], nu[1]);
+        }
+
+        // ---- normal equations of the CTA's pixels with these weights
+        {
+            float acc[kSlots];
+#pragma unroll
+            for (int i = 0; i < kSlots; ++i) acc[i] = 0.f;
+#pragma unroll
+            for (int k = 0; k < MAXP; ++k) {
+                const float* const J = Jt + k * (kJTerms * NT);
+                const float rI = rs[0][k], rW = rs[1][k];
+                if (rI == rI) {
+                    acc[kSlotNI] += 1.f;
+                    if (ok[0]) {
+                        float Jl[6];
+#pragma unroll
+                        for (int j = 0; j < 6; ++j) Jl[j] = J[j * NT];
+                        accumulate(acc, Jl, robust_weight(rI, mu[0], sig[0], nu[0]), rI);
+                    }
+                }
+                if (rW == rW) {
+                    acc[kSlotNW] += 1.f;
+                    if (ok[1]) {
+                        float Jl[6];
+#pragma unroll
+                        for (int j = 0; j < 6; ++j) Jl[j] = J[(6 + j) * NT];
+                        accumulate(acc, Jl, J[12 * NT] * robust_weight(rW, mu[1], sig[1], nu[1]), rW);
+                    }
+                }
+            }
+            red_w[warp][lane] = warp_reduce_scatter32(acc);
+            __syncthreads();
+            if (tid < kSlots) {
+                const F2 T2 = R.template exchange<kSlots>(tid, warp_tree<NW>(red_w, tid));
+                tot[tid] = T2.value();
+                tot2[tid] = make_float2(T2.hi, T2.lo);
+            }
+            __syncthreads();
+            R.next();
+        }
+
+        if (!last) {
+            if (warp == 0)
+                level_solve_update<PREC>(tot, a.min_valid, T_sh, &sh_wp, xi_f, d_f, rho_d, xi_d, &ok_flag, sh_cnt);
+            __syncthreads();
+        } else if (rank == 0) {
+            // the level's last step is left pending, as a sweep leaves its partials
+            AlignState* const st = a.st;
+            if (tid < kSlots) {
+                a.partials[tid] = tot2[tid];
+            } else if (tid < kSlots + 16) {
+                const int q = tid - kSlots;
+                st->T[q] = T_sh[q];
+                reinterpret_cast<float*>(&st->wp)[q] = reinterpret_cast<const float*>(&sh_wp)[q];
+            } else if (tid == kSlots + 16) {
+                RobustParams& rp = st->rob;
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    rp.mu[c] = mu[c];
+                    rp.sigma[c] = sig[c];
+                    rp.nu[c] = nu[c];
+                    rp.ok[c] = ok[c] ? 1 : 0;
+                }
+            } else if (tid == kSlots + 17) {
+                st->iters_done = sh_cnt[0];
+                st->iters_skipped = sh_cnt[1];
+                st->status = sh_cnt[2];
+                st->pending = 1u;
+            }
+        }
+    }
+    // no CTA leaves before every CTA is past its last exchange
+    cluster_arrive();
+    cluster_wait();
+}
+
+// ---------------------------------------------------------------- host side
+template <int PREC, int MAXP>
+static cudaError_t level_attributes() {
+    cudaError_t e = cudaFuncSetAttribute(level_kernel<PREC, MAXP>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(level_kernel<PREC, MAXP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)level_dyn_smem<MAXP>());
+}
+
+template <int PREC, int MAXP>
+static void level_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, cudaStream_t stream) {
+    cfg = cudaLaunchConfig_t{};
+    cfg.gridDim = dim3(kLevelCL, 1, 1);
+    cfg.blockDim = dim3(kRobustNT, 1, 1);
+    cfg.dynamicSmemBytes = level_dyn_smem<MAXP>();
+    cfg.stream = stream;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kLevelCL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 2;
+}
+
+// Whether the device schedules the 16-CTA cluster of both pixel capacities with
+// their shared memory; a fixed property of the device, cached per ordinal.
+template <int PREC>
+static bool level_kernel_schedulable() {
+    static std::atomic<int> cached[64];   // 0 unknown, 1 yes, 2 no
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    int c = cached[dev].load(std::memory_order_relaxed);
+    if (c == 0) {
+        bool ok = level_attributes<PREC, 2>() == cudaSuccess && level_attributes<PREC, 5>() == cudaSuccess;
+        if (ok) {
+            cudaLaunchConfig_t cfg;
+            cudaLaunchAttribute attr[2];
+            level_config<PREC, 5>(cfg, attr, 0);
+            cfg.numAttrs = 1;   // the cluster shape alone
+            int nclusters = 0;
+            ok = cudaOccupancyMaxActiveClusters(&nclusters, level_kernel<PREC, 5>, &cfg) == cudaSuccess &&
+                 nclusters > 0;
+        }
+        (void)cudaGetLastError();
+        c = ok ? 1 : 2;
+        cached[dev].store(c, std::memory_order_relaxed);
+    }
+    return c == 1;
+}
+
+bool level_kernel_takes(int precision, int w, int h, int cap) {
+    const long long n = (long long)w * h;
+    if (n > cap || n > kLevelMaxPixels) return false;   // the sample must be every pixel
+    return precision == RGBID_PLANES_F32 ? level_kernel_schedulable<RGBID_PLANES_F32>()
+                                         : level_kernel_schedulable<RGBID_PLANES_BF16_F16>();
+}
+
+template <int PREC>
+static cudaError_t launch_level_t(const LevelArgs& la, cudaStream_t stream) {
+    const long long n = (long long)la.A.w * la.A.h;
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[2];
+    if (n <= (long long)kLevelCL * kRobustNT * 2) {
+        cudaError_t e = level_attributes<PREC, 2>();
+        if (e != cudaSuccess) return e;
+        level_config<PREC, 2>(cfg, attr, stream);
+        return cudaLaunchKernelEx(&cfg, level_kernel<PREC, 2>, la);
+    }
+    cudaError_t e = level_attributes<PREC, 5>();
+    if (e != cudaSuccess) return e;
+    level_config<PREC, 5>(cfg, attr, stream);
+    return cudaLaunchKernelEx(&cfg, level_kernel<PREC, 5>, la);
+}
+
+cudaError_t launch_level(int precision, const LevelArgs& la, cudaStream_t stream) {
+    const long long n = (long long)la.A.w * la.A.h;
+    if (n < 1 || n > kLevelMaxPixels) return cudaErrorInvalidValue;
+    return precision == RGBID_PLANES_F32 ? launch_level_t<RGBID_PLANES_F32>(la, stream)
+                                         : launch_level_t<RGBID_PLANES_BF16_F16>(la, stream);
+}
+
+}  // namespace rgbid

@@ -48,6 +48,7 @@ class Pyramid(Structure):
 KERNEL_SWEEP = 0
 KERNEL_ROBUST = 1
 KERNEL_BATCH = 2
+KERNEL_LEVEL = 3
 
 
 class Timing(Structure):
@@ -59,7 +60,8 @@ class AlignParams(Structure):
     _fields_ = [("levels", c_int), ("iters", c_int * MAX_LEVELS), ("scale_iters", c_int),
                 ("bisect_steps", c_int), ("sample_cap", c_int), ("estimate_nu", c_int),
                 ("min_valid", c_int), ("warp_mode", c_int), ("nu0", c_double), ("nu_lo", c_double),
-                ("nu_hi", c_double), ("timing", POINTER(Timing)), ("level_iters", c_void_p)]
+                ("nu_hi", c_double), ("timing", POINTER(Timing)), ("level_iters", c_void_p),
+                ("no_level_kernel", c_int), ("pad2_", c_int)]
 
 
 class AlignResult(Structure):
@@ -98,6 +100,7 @@ SIGNATURES = [
     ("rgbid_build_pyramid", c_int, [c_void_p, c_void_p, c_int, c_int, c_int, Intrinsics, c_int, c_int,
                                     c_void_p, c_size_t, POINTER(Pyramid), c_void_p]),
     ("rgbid_align_workspace_bytes", c_size_t, [POINTER(Pyramid), POINTER(AlignParams)]),
+    ("rgbid_align_launches", c_int, [POINTER(Pyramid), POINTER(AlignParams)]),
     ("rgbid_align", c_int, [POINTER(Pyramid), POINTER(Pyramid), c_void_p, c_int, POINTER(AlignParams),
                             c_void_p, c_size_t, c_void_p, c_void_p]),
     ("rgbid_align_noalloc", c_int, [POINTER(Pyramid), POINTER(Pyramid), c_void_p, c_int, POINTER(AlignParams),
@@ -225,6 +228,11 @@ def rgbid_build_pyramid(I0, W0, K0, levels: int, precision: int, storage, stream
 
 def rgbid_align_workspace_bytes(ref: Pyramid, params: AlignParams) -> int:
     return int(lib().rgbid_align_workspace_bytes(ctypes.byref(ref), ctypes.byref(params)))
+
+
+def rgbid_align_launches(ref: Pyramid, params: AlignParams) -> int:
+    """Kernel launches one rgbid_align call enqueues with these arguments (-1: invalid)."""
+    return int(lib().rgbid_align_launches(ctypes.byref(ref), ctypes.byref(params)))
 
 
 def rgbid_align(ref: Pyramid, cur: Pyramid, T_init, params: AlignParams, workspace, result, stream=None):

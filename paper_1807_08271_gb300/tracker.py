@@ -25,7 +25,9 @@ into staging (or finds it there), replays the graph and copies the frame's
 result into the result array, instead of enqueueing some fifty launches.  Two
 slots let a caller upload frame k+1 (``staging(slot)``) while frame k runs.  The per-launch timing hook of the
 alignment (``params.timing``) needs the eager path, which step() takes while
-it is attached.
+it is attached.  With ``level_kernel=False`` every level of the alignment runs by
+the per-iteration kernels (the library's default runs a level whose systematic
+sample is every pixel in one persistent cluster launch).
 """
 from __future__ import annotations
 
@@ -37,7 +39,8 @@ from . import rgbid as R
 class Tracker:
     def __init__(self, width: int, height: int, K, levels: int = 4, iters=(5, 5, 5, 10), kf_every: int = 20,
                  precision: int = R.PLANES_F32, fuse_intensity: bool = True, max_frames: int = 4096,
-                 device="cuda", graphs: bool = True, kf_covisibility: float | None = None):
+                 device="cuda", graphs: bool = True, kf_covisibility: float | None = None,
+                 level_kernel: bool = True):
         import torch
         self.torch = torch
         self.w, self.h, self.K = width, height, tuple(float(k) for k in K)
@@ -46,6 +49,7 @@ class Tracker:
         self.fuse_intensity = fuse_intensity
         self.device = device
         self.params = R.rgbid_default_params(levels=levels, iters=iters)
+        self.params.no_level_kernel = 0 if level_kernel else 1
         self.cur = R.DevicePyramid(width, height, levels, precision, device)
         self.kfp = R.DevicePyramid(width, height, levels, precision, device)
         f32 = dict(dtype=torch.float32, device=device)
@@ -84,6 +88,11 @@ class Tracker:
     def _sigmaW_view(self):
         off = 8 * (16 + 36 + 6 + 2 + 1)
         return self.res[0, off:off + 8].view(self.torch.float64)
+
+    def align_launches(self) -> int:
+        """Kernel launches of one frame's alignment (initialisation to closing launch);
+        available once the first frame has been stepped."""
+        return R.rgbid_align_launches(self.kfp.desc, self.params)
 
     def staging(self, slot: int):
         """The (I, W) staging pair of ``slot`` (0 or 1): a frame copied there may be

@@ -46,8 +46,9 @@ int main(void) {{
          offsetof(rgbid_align_result, cost), offsetof(rgbid_align_result, status), sizeof(rgbid_timing),
          offsetof(rgbid_timing, units), offsetof(rgbid_align_params, timing),
          offsetof(rgbid_align_params, level_iters));
-  printf("%zu %zu %zu %zu\\n", sizeof(rgbid_bilateral), offsetof(rgbid_bilateral, sigma_s),
-         offsetof(rgbid_bilateral, sigma_r_W), offsetof(rgbid_align_params, warp_mode));
+  printf("%zu %zu %zu %zu %zu\\n", sizeof(rgbid_bilateral), offsetof(rgbid_bilateral, sigma_s),
+         offsetof(rgbid_bilateral, sigma_r_W), offsetof(rgbid_align_params, warp_mode),
+         offsetof(rgbid_align_params, no_level_kernel));
   return 0;
 }}''')
     exe = tmp_path / "abi"
@@ -61,7 +62,7 @@ int main(void) {{
                            b.AlignResult.status.offset, ctypes.sizeof(b.Timing), b.Timing.units.offset,
                            b.AlignParams.timing.offset, b.AlignParams.level_iters.offset]
     assert sizes[13:] == [ctypes.sizeof(b.Bilateral), b.Bilateral.sigma_s.offset, b.Bilateral.sigma_r_W.offset,
-                          b.AlignParams.warp_mode.offset]
+                          b.AlignParams.warp_mode.offset, b.AlignParams.no_level_kernel.offset]
 
 
 def test_host_side_calls_without_a_gpu(binding):
@@ -271,6 +272,11 @@ def test_misaligned_and_nonfinite_arguments_are_rejected_on_the_host(binding):
     assert align(good, good, params=pw) == b.ERR_INVALID_ARG
     pw.warp_mode = b.WARP_FULL_RESOLUTION
     assert L.rgbid_align_batched(V(base), 1, 0, ctypes.byref(pw), None, ws, wsb, None) == b.ERR_UNSUPPORTED
+    # the level-kernel switch takes 0 or 1
+    pk = b.rgbid_default_params(levels=1, iters=[3])
+    assert pk.no_level_kernel == 0
+    pk.no_level_kernel = 2
+    assert align(good, good, params=pk) == b.ERR_INVALID_ARG
     # the wait-timeout probe's own arguments
     assert L.rgbid_probe_wait_timeout(-1, f[0], None) == b.ERR_INVALID_ARG
     assert L.rgbid_probe_wait_timeout(1000, None, None) == b.ERR_INVALID_ARG
