@@ -67,10 +67,12 @@ def alu_roofline(kernel: str, units_per_launch: float, ms_per_launch: float) -> 
 
 
 # DRAM bytes (read + write) per unit (level pixel for the sweep, sample pixel for
-# the robust-scale kernel) from the ncu captures summarised in
-# profiles/robust_kernel_seq640_level0.md and profiles/sweep_kernel_seq640_level0.md
-# (level-0 launches, cold caches); set to None whenever those kernels change.
-TRAFFIC_PER_UNIT = {"robust_kernel": 3240192 / 19200, "sweep_kernel": 4847616 / 307200}
+# the robust-scale kernel, level pixel x iteration for the level kernel) from one ncu
+# capture of each kernel on this workload (the sweep and robust-scale kernels at
+# level 0, the level kernel's two launches of a frame; cold caches); set to None
+# whenever those kernels change.
+TRAFFIC_PER_UNIT = {"robust_kernel": 3240192 / 19200, "sweep_kernel": 4847616 / 307200,
+                    "level_kernel": (166912 + 511232) / (4800 * 10 + 19200 * 5)}
 
 
 # ----------------------------------------------------------------------------- ranks
