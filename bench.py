@@ -71,8 +71,8 @@ def alu_roofline(kernel: str, units_per_launch: float, ms_per_launch: float) -> 
 # capture of each kernel on this workload (the sweep and robust-scale kernels at
 # level 0, the level kernel's two launches of a frame; cold caches); set to None
 # whenever those kernels change.
-TRAFFIC_PER_UNIT = {"robust_kernel": 3240192 / 19200, "sweep_kernel": 4847616 / 307200,
-                    "level_kernel": (166912 + 511232) / (4800 * 10 + 19200 * 5)}
+TRAFFIC_PER_UNIT = {"robust_kernel": None, "sweep_kernel": 4847616 / 307200,
+                    "level_kernel": (166912 + 511232) / (4800 * 10 + 19200 * 5), "split_kernel": None}
 
 
 # ----------------------------------------------------------------------------- ranks
@@ -329,6 +329,7 @@ def native(args):
     timer_robust = R.KernelTimer(R.KERNEL_ROBUST, (per_step_launches + 1) * max(1, min(args.steps, 60)) + 8)
     timer_sweep = R.KernelTimer(R.KERNEL_SWEEP, per_step_launches * max(1, min(args.steps, 60)) + 8)
     timer_level = R.KernelTimer(R.KERNEL_LEVEL, LEVELS * max(1, min(args.steps, 60)) + 8)
+    timer_split = R.KernelTimer(R.KERNEL_SPLIT, LEVELS * max(1, min(args.steps, 60)) + 8)
     prec = R.PLANES_BF16_F16 if args.precision == "bf16" else R.PLANES_F32
     bytes_per_unit = BYTES_PER_UNIT[args.precision]
     covis = KF_COVISIBILITY if args.keyframes == "covisibility" else None
@@ -460,7 +461,7 @@ def native(args):
     n_kern = max(1, min(args.steps, 60))
     timed_kernels = [("robust_kernel", timer_robust), ("sweep_kernel", timer_sweep)]
     if level_kernels:
-        timed_kernels.append(("level_kernel", timer_level))
+        timed_kernels += [("level_kernel", timer_level), ("split_kernel", timer_split)]
     for name, timer in timed_kernels:
         timer.reset()
         timer.attach(trk.params)
@@ -485,6 +486,8 @@ def native(args):
     peak, peak_kind = measured_peaks()
     rooflines = {}
     for name, (k_ms, k_units, k_count, region_ms) in kern.items():
+        if k_count == 0:
+            continue                                     # a kernel this configuration does not launch
         alg_bytes = bytes_per_unit * k_units             # 16 B (FP32 planes) or 8 B (bf16/fp16) per unit
         achieved = alg_bytes / (k_ms / 1000.0) / 1e9 if k_ms > 0 else 0.0
         rooflines[name] = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
@@ -496,6 +499,8 @@ def native(args):
                            "avg_launch_us": 1000.0 * k_ms / max(k_count, 1),
                            "share_of_step": k_ms / region_ms if region_ms else None}
     dominant = max(rooflines, key=lambda n: rooflines[n]["share_of_step"] or 0.0)
+    # the kernel that evaluates every pixel of the finest level (the ALU roofline's)
+    pixel_kernel = "sweep_kernel" if "sweep_kernel" in rooflines else "split_kernel"
     roofline = rooflines[dominant]
     others = {n: r for n, r in rooflines.items() if n != dominant}
     cpu = None
@@ -549,8 +554,8 @@ def native(args):
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 2 * W * H * 4,
                 "d2h_bytes_per_step": R.RESULT_BYTES},
         "roofline": roofline, "roofline_other_kernels": others,
-        "alu_roofline": alu_roofline("sweep_kernel", rooflines["sweep_kernel"]["units_per_launch"],
-                                     rooflines["sweep_kernel"]["avg_launch_us"] / 1000.0),
+        "alu_roofline": alu_roofline(pixel_kernel, rooflines[pixel_kernel]["units_per_launch"],
+                                     rooflines[pixel_kernel]["avg_launch_us"] / 1000.0),
         "cpu_baseline": cpu, "clocks": clk, "gpu_launches": gpu_launches,
         "wall_s_timed": t_wall, "max_rot_err_vs_truth_rad": rot, "pose_check": pose_check,
     }

@@ -94,7 +94,8 @@ typedef enum {
     RGBID_KERNEL_SWEEP = 0,      /* fused warp + residual + Jacobian + weight + reduce (+ solve) */
     RGBID_KERNEL_ROBUST = 1,     /* systematic sample + (mu, sigma, nu) */
     RGBID_KERNEL_BATCH = 2,      /* the persistent kernel of rgbid_align_batched (units are not counted) */
-    RGBID_KERNEL_LEVEL = 3       /* the persistent level kernel of rgbid_align (units: level pixels x iterations) */
+    RGBID_KERNEL_LEVEL = 3,      /* the persistent level kernel of rgbid_align (units: level pixels x iterations) */
+    RGBID_KERNEL_SPLIT = 4       /* the split level kernel of rgbid_align (units: level pixels x iterations) */
 } rgbid_kernel_id;
 
 typedef struct {
@@ -136,12 +137,16 @@ typedef struct {
     const int* level_iters;      /* optional DEVICE array of RGBID_MAX_LEVELS ints read by the kernels
                                     (rgbid_align only): level l runs min(iters[l], level_iters[l])
                                     iterations; the launches of the others exit at once.  NULL: iters. */
-    int no_level_kernel;         /* 0 (default): rgbid_align runs a level whose systematic sample is every
-                                    pixel (w h <= sample_cap, and <= 20480 pixels) in one persistent
-                                    16-CTA cluster launch: each iteration warps the level once, takes its
-                                    residuals as the sample, and solves inside the cluster.  1: every
-                                    level by the per-iteration robust-scale and sweep kernels.  Both
-                                    compute the same steps (sums in another order). */
+    int no_level_kernel;         /* 0 (default): rgbid_align runs each level in one launch where it can.
+                                    A level whose systematic sample is every pixel (w h <= sample_cap,
+                                    and <= 20480 pixels) runs in one persistent 16-CTA cluster: each
+                                    iteration warps the level once, takes its residuals as the sample,
+                                    and solves inside the cluster.  A larger level runs in the split
+                                    kernel, a cooperative launch of one such cluster (solve, sample,
+                                    robust parameters) and helper CTAs that evaluate every pixel's
+                                    terms while the cluster estimates the parameters.  1: every level
+                                    by the per-iteration robust-scale and sweep kernels.  All compute
+                                    the same steps (sums in another order). */
     int pad2_;
 } rgbid_align_params;
 

@@ -113,6 +113,11 @@ __global__ void init_kernel(InitArgs a) {
     st->iters_done = 0;
     st->iters_skipped = 0;
     st->timeouts = 0;
+    st->mb.pose_flag = 0u;
+    st->mb.rob_flag = 0u;
+    st->mb.arrived = 0u;
+    st->mb.exited = 0u;
+    st->mb.error = 0;
     if (a.use_fixed) {
         for (int c = 0; c < 2; ++c) {
             st->rob.mu[c] = a.fixed[3 * c + 0];
@@ -764,9 +769,10 @@ static int sweep_blocks(int w, int h, bool one_row) {
     return ((w + kTileW - 1) / kTileW) * ((h + th - 1) / th);
 }
 
-// The block partials of the largest sweep over the levels of `ref`.
+// The block partials of the largest sweep over the levels of `ref`, and at least one
+// per helper CTA the split kernel may launch.
 static size_t workspace_bytes_for(const rgbid_pyramid& ref, bool one_row) {
-    int nb = 1;
+    int nb = kSplitMaxHelpers;
     for (int l = 0; l < ref.levels && l < RGBID_MAX_LEVELS; ++l)
         nb = std::max(nb, sweep_blocks(ref.lv[l].width, ref.lv[l].height, one_row));
     return align_up(sizeof(AlignState), 256) + align_up((size_t)nb * kSlots * sizeof(float2), 256);
@@ -981,6 +987,41 @@ static bool use_level_kernel(const rgbid_pyramid* ref, const rgbid_align_params*
     return level_kernel_takes(ref->precision, L.width, L.height, p->sample_cap);
 }
 
+// A level whose sample is a strict subset of its pixels runs in the split kernel when
+// its tiles fit the helper CTAs.
+static bool use_split_kernel(const rgbid_pyramid* ref, const rgbid_align_params* p, int l) {
+    if (p->no_level_kernel || p->warp_mode != RGBID_WARP_PER_LEVEL) return false;
+    const rgbid_level& L = ref->lv[l];
+    return split_kernel_takes(ref->precision, L.width, L.height);
+}
+
+static SplitArgs split_args(const RobustArgs& ra, const rgbid_align_params* p, float* partials) {
+    SplitArgs sp;
+    memset(&sp, 0, sizeof(sp));
+    sp.A = ra.A;
+    sp.B = ra.B;
+    sp.st = ra.st;
+    sp.partials = reinterpret_cast<float2*>(partials);
+    sp.iters = p->iters[ra.level];
+    sp.level_iters = p->level_iters;
+    sp.level = ra.level;
+    sp.s = ra.s;
+    sp.nsx = ra.nsx;
+    sp.nsamp = ra.nsamp;
+    sp.scale_iters = p->scale_iters;
+    sp.bisect_steps = p->bisect_steps;
+    sp.estimate_nu = p->estimate_nu;
+    sp.min_valid = p->min_valid;
+    sp.nu0 = (float)p->nu0;
+    sp.nu_lo = p->nu_lo;
+    sp.nu_hi = p->nu_hi;
+    memcpy(sp.nu_g, ra.nu_g, sizeof(sp.nu_g));
+    sp.n_helpers = 0;         // set by the caller for the device
+    sp.tiles_x = (ra.A.w + kSplitTileW - 1) / kSplitTileW;
+    sp.tiles_y = (ra.A.h + kSplitTileH - 1) / kSplitTileH;
+    return sp;
+}
+
 static LevelArgs level_args(const rgbid_pyramid* ref, const rgbid_pyramid* cur, int l, const rgbid_align_params* p,
                             AlignState* st, float* partials) {
     LevelArgs la;
@@ -1017,7 +1058,7 @@ extern "C" int rgbid_align_launches(const rgbid_pyramid* ref, const rgbid_align_
     int n = 2;   // the initialisation and the closing launch
     for (int l = params->levels - 1; l >= 0; --l) {
         if (params->iters[l] <= 0) continue;
-        n += use_level_kernel(ref, params, l) ? 1 : 2 * params->iters[l];
+        n += (use_level_kernel(ref, params, l) || use_split_kernel(ref, params, l)) ? 1 : 2 * params->iters[l];
     }
     return n;
 }
@@ -1064,6 +1105,21 @@ extern "C" int rgbid_align(const rgbid_pyramid* ref, const rgbid_pyramid* cur, c
                 if (cudaEventRecord((cudaEvent_t)tm->ev_end[tm->count], stream) != cudaSuccess) return RGBID_ERR_CUDA;
                 tm->count += 1;
                 tm->units += (long long)la.A.w * la.A.h * params->iters[l];
+            }
+            after_level_kernel = true;
+            continue;
+        }
+        if (params->iters[l] > 0 && use_split_kernel(ref, params, l)) {
+            SplitArgs sp = split_args(ra, params, partials);
+            sp.n_helpers = split_kernel_helpers(ref->precision);
+            sp.max_tiles = (sp.tiles_x * sp.tiles_y + sp.n_helpers - 1) / sp.n_helpers;
+            const bool tl = tm && tm->kernel == RGBID_KERNEL_SPLIT && tm->count < tm->capacity;
+            if (tl && cudaEventRecord((cudaEvent_t)tm->ev_start[tm->count], stream) != cudaSuccess) return RGBID_ERR_CUDA;
+            if (launch_split(ref->precision, sp, stream) != cudaSuccess) return RGBID_ERR_CUDA;
+            if (tl) {
+                if (cudaEventRecord((cudaEvent_t)tm->ev_end[tm->count], stream) != cudaSuccess) return RGBID_ERR_CUDA;
+                tm->count += 1;
+                tm->units += (long long)sp.A.w * sp.A.h * params->iters[l];
             }
             after_level_kernel = true;
             continue;

@@ -36,6 +36,10 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, u
                  : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -322,10 +326,15 @@ struct ClusterSum {
 
     // The same round towards CTA 0 alone: every CTA pushes its partial of value t
     // into CTA 0, which waits and returns the total (the same tree over the ranks);
-    // the other CTAs return at once.  For sums only CTA 0 consumes.
+    // the other CTAs return at once.  For sums only CTA 0 consumes.  The other CTAs
+    // still complete their own barrier's phase of the round (an arrival with no
+    // bytes), so every CTA's phases keep counting the rounds when more follow.
     template <int NV>
     __device__ __forceinline__ F2 gather(int t, F2 s) {
-        if (rank == 0 && t == 0) mbar_arrive_expect_tx(&mbar[round & 1], (uint32_t)(CL * NV * sizeof(float2)));
+        if (t == 0) {
+            if (rank == 0) mbar_arrive_expect_tx(&mbar[round & 1], (uint32_t)(CL * NV * sizeof(float2)));
+            else mbar_arrive(&mbar[round & 1]);
+        }
         send(t, 0, s);
         if (rank != 0) return F2{0.f, 0.f};
         return receive<NV>(t);

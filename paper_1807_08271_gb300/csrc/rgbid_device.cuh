@@ -47,6 +47,21 @@ struct LevelDev {
     float fx, fy, cx, cy, ifx, ify;
 };
 
+// Hand-over between the roles of the split level kernel (the robust-scale cluster
+// and the helper CTAs of one launch): flags counting published iterations, the
+// helpers' arrivals and exits.  Zero between launches: the last CTA of a launch
+// to leave resets it, and the alignment's initialisation clears it.
+struct SplitMailbox {
+    unsigned int pose_flag;  // iterations whose pose is published
+    unsigned int rob_flag;   // iterations whose robust parameters are published
+    unsigned int arrived;    // helper partials posted
+    unsigned int exited;     // CTAs done with the mailbox
+    int error;               // a wait ran out: every role gives up
+    int pad[3];
+    WarpPose wp;             // the published pose (FP32 warp form)
+    RobustParams rob;        // the published robust parameters
+};
+
 // Device-resident state of one alignment (lives at the start of the workspace).
 struct AlignState {
     double T[16];           // current estimate A_T_B
@@ -58,6 +73,7 @@ struct AlignState {
     int iters_skipped;
     int timeouts;
     int pad[3];
+    SplitMailbox mb;
 };
 
 // ---------------------------------------------------------------- pixel loads

@@ -428,6 +428,510 @@ __global__ void __launch_bounds__(kRobustNT, 1) level_kernel(LevelArgs a) {
     cluster_wait();
 }
 
+// ---------------------------------------------------------------- split level kernel
+// A level whose systematic sample is a strict subset of its pixels (640x480 and
+// 320x240 of the sequence).  One launch runs all of the level's iterations:
+//   cluster 0 (16 CTAs)  reduces the previous step's partials, solves and updates the
+//                        pose in every CTA, publishes the pose, evaluates the sample
+//                        residuals at it, estimates (mu, sigma, nu) as the robust-scale
+//                        kernel does, and publishes the parameters (CTA 0);
+//   helper CTAs          evaluate every pixel's residuals, Jacobians and lambda_n as soon
+//                        as the pose is published, keep them in shared memory, weight
+//                        and accumulate them once the parameters are published, and post
+//                        one compensated partial each.
+// The pixel work of an iteration thus overlaps the robust-scale chain instead of
+// following it.  The roles hand over through the workspace's mailbox: a release store
+// of a counter after the data, an acquire load before reading it, every wait bounded.
+// The launch is cooperative, so every CTA is resident while others wait on it.  The
+// level's last step stays pending (one partial per helper), as a sweep leaves it.
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int ld_relaxed_s32(const int* p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned int* p, unsigned int v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Thread 0 waits until *word >= target; every thread of the CTA gets the verdict
+// through its own shared slot.  A wait that runs out counts a timeout and raises the
+// mailbox's error flag; a raised flag makes every later wait give up at once.
+__device__ __forceinline__ bool cta_wait(AlignState* st, const unsigned int* word, unsigned int target, int* slot) {
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const long long t0 = clock64();
+        while (ld_acquire_u32(word) < target) {
+            if (ld_relaxed_s32(&st->mb.error)) {
+                ok = 0;
+                break;
+            }
+            if (clock64() - t0 > kWaitBudgetCycles) {
+                atomicAdd(&st->timeouts, 1);
+                atomicExch(&st->mb.error, 1);
+                ok = 0;
+                break;
+            }
+        }
+        *slot = ok;
+    }
+    __syncthreads();
+    return *slot != 0;
+}
+
+constexpr int kSampleTerms = 13;   // a sample's cached keyframe-side stage: 5 taps (10), a, b, interior
+
+template <int PREC>
+__global__ void __launch_bounds__(kRobustNT, 1) split_kernel(SplitArgs a) {
+    constexpr int CL = kLevelCL, NT = kRobustNT, NW = NT / 32;
+    constexpr int MAXS = (RGBID_MAX_SAMPLES + CL * NT - 1) / (CL * NT);
+    constexpr int G = 4;                             // a helper's tiles in flight
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int tid = (int)threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    extern __shared__ __align__(16) float dyn[];     // cluster 0: cached samples; helpers: pixel terms
+    __shared__ float red_w[NW][kRobustMaxNV];
+    __shared__ float2 recv[2][CL][kRobustMaxNV];
+    __shared__ float tot[kRobustMaxNV];
+    __shared__ __align__(8) unsigned long long mbar[2];
+    __shared__ WarpPose sh_wp;
+    __shared__ RobustParams sh_rob;
+    __shared__ double T_sh[16];
+    __shared__ float nu_out[2];
+    __shared__ float nuF[2][kNuSeries];
+    __shared__ float sh_g[kNuGTerms];
+    __shared__ F2 fin2[NW][kSlots];
+    __shared__ float xi_f[6], d_f[6];
+    __shared__ double xi_d[6], rho_d[6];
+    __shared__ int ok_flag;
+    __shared__ int sh_cnt[3];                        // iterations done, skipped, status
+    __shared__ int go[3];                            // verdicts of the CTA's mailbox waits, one per site
+
+    const int n_it = a.level_iters ? min(a.iters, __ldg(a.level_iters + a.level)) : a.iters;
+    if (n_it <= 0) {
+        pdl_wait();   // keeps the chain of dependent launches ordered; never triggers
+        return;
+    }
+    AlignState* const st = a.st;
+    SplitMailbox* const mb = &st->mb;
+
+    if (blockIdx.x < CL) {
+        // ================================================================ cluster 0
+        if (tid == 0) {
+            mbar_init(&mbar[0], 1);
+            mbar_init(&mbar[1], 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+#pragma unroll
+            for (int k = 0; k < kNuGTerms; ++k) sh_g[k] = a.nu_g[k];
+        }
+        cluster_arrive();
+        // the keyframe-side stage of this thread's samples, kept for every iteration
+        // (A's planes do not change during an alignment)
+        float* const Sa = dyn + tid;                 // [MAXS][kSampleTerms][NT]
+        const int gt = rank * NT + tid;
+#pragma unroll
+        for (int k = 0; k < MAXS; ++k) {
+            const int i = gt + k * (CL * NT);
+            PxA p;
+            p.ok = false;
+            if (i < a.nsamp) {
+                const int sy = i / a.nsx, sx = i - sy * a.nsx;
+                stage_a<PREC>(a.A, sx * a.s, sy * a.s, p);
+            }
+            float* const q = Sa + k * (kSampleTerms * NT);
+            q[0] = p.c.x; q[NT] = p.c.y; q[2 * NT] = p.nl.x; q[3 * NT] = p.nl.y; q[4 * NT] = p.nr.x;
+            q[5 * NT] = p.nr.y; q[6 * NT] = p.nu.x; q[7 * NT] = p.nu.y; q[8 * NT] = p.nd.x; q[9 * NT] = p.nd.y;
+            q[10 * NT] = p.a; q[11 * NT] = p.b; q[12 * NT] = p.ok ? 1.f : 0.f;
+        }
+        pdl_wait();   // the state and the pending partials of the preceding launches are visible
+        if (tid < 16) {
+            T_sh[tid] = __ldcg(st->T + tid);
+        } else if (tid < 32) {
+            reinterpret_cast<float*>(&sh_wp)[tid - 16] = __ldcg(reinterpret_cast<const float*>(&st->wp) + (tid - 16));
+        } else if (tid == 32) {
+            sh_cnt[0] = __ldcg(&st->iters_done);
+        } else if (tid == 33) {
+            sh_cnt[1] = __ldcg(&st->iters_skipped);
+        } else if (tid == 34) {
+            sh_cnt[2] = __ldcg(&st->status);
+        } else if (tid >= 64 && tid < 64 + (int)(sizeof(RobustParams) / 4)) {
+            reinterpret_cast<int*>(&sh_rob)[tid - 64] = __ldcg(reinterpret_cast<const int*>(&st->rob) + (tid - 64));
+        }
+        const unsigned int nb0 = __ldcg(&st->pending);
+        cluster_wait();
+        // the cluster barrier's arrive came before these loads: only a CTA barrier
+        // makes warp 0's copies of the state visible to the other warps
+        __syncthreads();
+        ClusterSum<CL> R{red_w, recv, tot, mbar, &st->timeouts, (uint32_t)rank, 0};
+        const float nu0 = a.nu0;
+        const float lo0 = (float)a.nu_lo, hi0 = (float)a.nu_hi;
+        const float m = 0.5f * (lo0 + hi0), h = 0.5f * (hi0 - lo0);
+
+        for (int it = 0; it < n_it; ++it) {
+            // ---- the previous step: the pending partials of the preceding launch, or the
+            //      helpers' partials of the previous iteration
+            if (it > 0 && !cta_wait(st, &mb->arrived, (unsigned)a.n_helpers * (unsigned)it, &go[0])) break;
+            const unsigned int nb = it == 0 ? nb0 : (unsigned)a.n_helpers;
+            if (nb) {
+                F2 acc{0.f, 0.f};
+                constexpr unsigned kStride = (unsigned)CL * NW;
+                for (unsigned int b0 = (unsigned)rank + (unsigned)CL * (unsigned)warp; b0 < nb; b0 += 4u * kStride) {
+                    float2 v[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const unsigned int b = b0 + (unsigned)q * kStride;
+                        v[q] = b < nb ? __ldcg(a.partials + (size_t)b * kSlots + lane) : make_float2(0.f, 0.f);
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc.add(F2{v[q].x, v[q].y});
+                }
+                fin2[warp][lane] = acc;
+                __syncthreads();
+                if (tid < kSlots) tot[tid] = R.template exchange<kSlots>(tid, warp_tree<NW>(fin2, tid)).value();
+                __syncthreads();
+                R.next();
+                if (warp == 0)
+                    level_solve_update<PREC>(tot, a.min_valid, T_sh, &sh_wp, xi_f, d_f, rho_d, xi_d, &ok_flag, sh_cnt);
+                __syncthreads();
+            }
+            // ---- publish this iteration's pose to the helpers
+            if (rank == 0 && warp == 0) {
+                if (lane < 16) {
+                    __stcg(reinterpret_cast<float*>(&mb->wp) + lane, reinterpret_cast<const float*>(&sh_wp)[lane]);
+                    __threadfence();
+                }
+                __syncwarp();
+                if (lane == 0) st_release_u32(&mb->pose_flag, (unsigned)it + 1u);
+            }
+            const WarpPose wp = sh_wp;
+
+            // ---- systematic sample residuals at this pose (NaN = masked out)
+            float rs[2][MAXS];
+            {
+                PxA sa[MAXS];
+                PxW sw[MAXS];
+                PxB sb[MAXS];
+                int su[MAXS], sv[MAXS];
+#pragma unroll
+                for (int k = 0; k < MAXS; ++k) {
+                    const int i = gt + k * (CL * NT);
+                    const float* const q = Sa + k * (kSampleTerms * NT);
+                    sa[k].c = make_float2(q[0], q[NT]);
+                    sa[k].nl = make_float2(q[2 * NT], q[3 * NT]);
+                    sa[k].nr = make_float2(q[4 * NT], q[5 * NT]);
+                    sa[k].nu = make_float2(q[6 * NT], q[7 * NT]);
+                    sa[k].nd = make_float2(q[8 * NT], q[9 * NT]);
+                    sa[k].a = q[10 * NT];
+                    sa[k].b = q[11 * NT];
+                    sa[k].ok = q[12 * NT] != 0.f;
+                    const int sy = i < a.nsamp ? i / a.nsx : 0, sx = i < a.nsamp ? i - sy * a.nsx : 0;
+                    su[k] = sx * a.s;
+                    sv[k] = sy * a.s;
+                }
+#pragma unroll
+                for (int k = 0; k < MAXS; ++k) stage_w(a.A, a.B, wp, su[k], sv[k], sa[k], sw[k]);
+#pragma unroll
+                for (int k = 0; k < MAXS; ++k) stage_b<PREC>(a.B, sw[k], sb[k]);
+#pragma unroll
+                for (int k = 0; k < MAXS; ++k) {
+                    PixelTerms o;
+                    finish<false>(a.A, wp, sa[k], sw[k], sb[k], o);
+                    rs[0][k] = o.mI ? o.rI : __int_as_float(0x7fc00000);
+                    rs[1][k] = o.mW ? o.rW : __int_as_float(0x7fc00000);
+                }
+            }
+
+            // ---- counts and mean square -> sigma0 (mu0 = 0)
+            {
+                float v4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int k = 0; k < MAXS; ++k) {
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        const float r = rs[c][k];
+                        const bool use = r == r;
+                        const float rv = use ? r : 0.f;
+                        v4[2 * c] += use ? 1.f : 0.f;
+                        v4[2 * c + 1] = fmaf(rv, rv, v4[2 * c + 1]);
+                    }
+                }
+                R.run(v4);
+            }
+            const float n[2] = {tot[0], tot[2]};
+            float mu[2] = {0.f, 0.f};
+            float sig[2];
+            bool live[2];
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const float ms = n[c] > 0.f ? __fdividef(tot[2 * c + 1], n[c]) : 0.f;
+                sig[c] = ms > 0.f ? ms * rsqrtf(ms) : 0.f;
+                live[c] = n[c] > 0.f && sig[c] >= 1e-12f;
+            }
+            // ---- (mu, sigma) fixed point at nu0 with lagged weights
+            for (int si = 0; si < a.scale_iters; ++si) {
+                if (!live[0] && !live[1]) break;
+                float v6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const float mc = mu[c];
+                    const float s2 = sig[c] * sig[c];
+                    const float s2nu = s2 * nu0;
+                    const float num = (nu0 + 1.f) * s2;
+#pragma unroll
+                    for (int k = 0; k < MAXS; ++k) {
+                        const float r = rs[c][k];
+                        const bool use = r == r;
+                        const float dr = r - mc;
+                        const float wr = __fdividef(num, fmaf(dr, dr, s2nu));
+                        const float wv = use ? wr : 0.f, d = use ? dr : 0.f;
+                        v6[3 * c] += wv;
+                        v6[3 * c + 1] = fmaf(wv, d, v6[3 * c + 1]);
+                        v6[3 * c + 2] = fmaf(wv * d, d, v6[3 * c + 2]);
+                    }
+                }
+                R.run(v6);
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    if (!live[c]) continue;
+                    const float S0 = tot[3 * c], S1 = tot[3 * c + 1], S2 = tot[3 * c + 2];
+                    const float delta = __fdividef(S1, S0);
+                    mu[c] += delta;
+                    const float var = __fdividef(fmaf(-S1, delta, S2), n[c]);
+                    sig[c] = var > 0.f ? var * rsqrtf(var) : 0.f;
+                    if (!(sig[c] >= 1e-12f)) live[c] = false;
+                }
+            }
+            bool ok[2];
+#pragma unroll
+            for (int c = 0; c < 2; ++c) ok[c] = n[c] > 0.f && sig[c] >= 1e-12f;
+
+            // ---- nu: the Chebyshev power sums gathered to CTA 0, which bisects
+            float nu[2] = {nu0, nu0};
+            const bool do_nu = a.estimate_nu && (ok[0] || ok[1]);
+            if (do_nu) {
+                unsigned long long V[kChebVals];
+#pragma unroll
+                for (int i = 0; i < kChebVals; ++i) V[i] = 0ull;
+                const float is0 = ok[0] ? __fdividef(1.f, sig[0]) : 0.f;
+                const float is1 = ok[1] ? __fdividef(1.f, sig[1]) : 0.f;
+#pragma unroll 1
+                for (int k = 0; k < MAXS; ++k) {
+                    float r0 = rs[0][0], r1 = rs[1][0];
+#pragma unroll
+                    for (int q = 1; q < MAXS; ++q)
+                        if (k == q) {
+                            r0 = rs[0][q];
+                            r1 = rs[1][q];
+                        }
+                    float q2[2], g2[2], l2[2];
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        const float x = ((c ? r1 : r0) - mu[c]) * (c ? is1 : is0);
+                        const bool use = ok[c] && x == x;
+                        const float al = __fdividef(fmaf(x, x, m), h);
+                        const float s2 = fmaf(al, al, -1.f);
+                        const float gam = rsqrtf(s2);
+                        const float be = fmaf(s2, gam, al);
+                        q2[c] = use ? __fdividef(1.f, be) : 0.f;
+                        g2[c] = use ? gam : 0.f;
+                        l2[c] = use ? __logf(0.5f * be) : 0.f;
+                    }
+                    const unsigned long long Q = f2_pack(q2[0], q2[1]), Gp = f2_pack(g2[0], g2[1]);
+                    V[0] = f2_add(V[0], f2_pack(l2[0], l2[1]));
+                    V[1 + kChebK] = f2_add(V[1 + kChebK], Gp);
+                    unsigned long long qk = Q;
+#pragma unroll
+                    for (int kk = 1; kk <= kChebK; ++kk) {
+                        V[kk] = f2_add(V[kk], qk);
+                        V[1 + kChebK + kk] = f2_fma(Gp, qk, V[1 + kChebK + kk]);
+                        qk = f2_mul(qk, Q);
+                    }
+                }
+                float v[96];
+#pragma unroll
+                for (int i = 0; i < kChebVals; ++i) {
+                    v[i] = f2_lo(V[i]);
+                    v[kChebVals + i] = f2_hi(V[i]);
+                }
+#pragma unroll
+                for (int i = 2 * kChebVals; i < 96; ++i) v[i] = 0.f;
+                R.template run<96, 2 * kChebVals, true>(v);   // only CTA 0 bisects
+            }
+            if (rank == 0) {
+                if (do_nu && tid < 64) {
+                    const int c = tid >> 5;
+                    float nuc = nu0;
+                    if (ok[c]) nuc = bisect_nu_warp(tot + c * kChebVals, n[c], sh_g, lo0, hi0, a.bisect_steps, nuF[c]);
+                    if (lane == 0) nu_out[c] = nuc;
+                }
+                __syncthreads();
+                if (do_nu) {
+                    nu[0] = nu_out[0];
+                    nu[1] = nu_out[1];
+                    if (ok[0] && ok[1]) nu[0] = fmaxf(nu[0], nu[1]);
+                }
+                if (tid == 0) {
+                    RobustParams rp;
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        rp.mu[c] = mu[c];
+                        rp.sigma[c] = sig[c];
+                        rp.nu[c] = nu[c];
+                        rp.ok[c] = ok[c] ? 1 : 0;
+                    }
+                    sh_rob = rp;
+                    // ---- publish the parameters to the helpers
+                    const int* const src = reinterpret_cast<const int*>(&rp);
+#pragma unroll
+                    for (int q = 0; q < (int)(sizeof(RobustParams) / 4); ++q)
+                        __stcg(reinterpret_cast<int*>(&mb->rob) + q, src[q]);
+                    __threadfence();
+                    st_release_u32(&mb->rob_flag, (unsigned)it + 1u);
+                }
+            }
+        }
+        // ---- the level's last step stays pending: the helpers' partials, weighted with
+        //      the parameters published last, at the pose published last
+        __syncthreads();
+        if (rank == 0) {
+            if (tid < 16) {
+                st->T[tid] = T_sh[tid];
+                reinterpret_cast<float*>(&st->wp)[tid] = reinterpret_cast<const float*>(&sh_wp)[tid];
+            } else if (tid == 16) {
+                st->rob = sh_rob;
+            } else if (tid == 17) {
+                st->iters_done = sh_cnt[0];
+                st->iters_skipped = sh_cnt[1];
+                st->status = sh_cnt[2];
+                st->pending = (unsigned)a.n_helpers;
+            }
+        }
+        // no CTA leaves before every CTA is past its last exchange
+        cluster_arrive();
+        cluster_wait();
+    } else {
+        // ================================================================ helper CTAs
+        const int hc = (int)blockIdx.x - CL;
+        const int ntiles = a.tiles_x * a.tiles_y;
+        float* const Tm = dyn + tid;                 // [max_tiles][kSplitTerms][NT]
+        pdl_wait();
+        for (int it = 0; it < n_it; ++it) {
+            if (!cta_wait(st, &mb->pose_flag, (unsigned)it + 1u, &go[1])) break;
+            if (tid < 16) reinterpret_cast<float*>(&sh_wp)[tid] = __ldcg(reinterpret_cast<const float*>(&mb->wp) + tid);
+            __syncthreads();
+            const WarpPose wp = sh_wp;
+            // ---- the terms of every pixel of this CTA's tiles at the published pose
+#pragma unroll 1
+            for (int j0 = 0; j0 < a.max_tiles; j0 += G) {
+                PxA sa[G];
+                PxW sw[G];
+                PxB sb[G];
+                int pu[G], pv[G];
+#pragma unroll
+                for (int g = 0; g < G; ++g) {
+                    sa[g].ok = false;
+                    pu[g] = 0;
+                    pv[g] = 0;
+                    const int t = hc + (j0 + g) * a.n_helpers;
+                    if (j0 + g < a.max_tiles && t < ntiles) {
+                        const int ty = t / a.tiles_x, tx = t - ty * a.tiles_x;
+                        const int u = tx * kSplitTileW + lane, v = ty * kSplitTileH + warp;
+                        if (u < a.A.w && v < a.A.h) {
+                            pu[g] = u;
+                            pv[g] = v;
+                            stage_a<PREC>(a.A, u, v, sa[g]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int g = 0; g < G; ++g) stage_w(a.A, a.B, wp, pu[g], pv[g], sa[g], sw[g]);
+#pragma unroll
+                for (int g = 0; g < G; ++g) stage_b<PREC>(a.B, sw[g], sb[g]);
+#pragma unroll
+                for (int g = 0; g < G; ++g) {
+                    if (j0 + g >= a.max_tiles) continue;
+                    PixelTerms o;
+                    finish<true>(a.A, wp, sa[g], sw[g], sb[g], o);
+                    float* const T = Tm + (j0 + g) * (kSplitTerms * NT);
+                    T[0] = o.mI ? o.rI : __int_as_float(0x7fc00000);
+                    T[NT] = o.mW ? o.rW : __int_as_float(0x7fc00000);
+                    if (o.mI) {
+#pragma unroll
+                        for (int q = 0; q < 6; ++q) T[(2 + q) * NT] = o.JI[q];
+                    }
+                    if (o.mW) {
+#pragma unroll
+                        for (int q = 0; q < 6; ++q) T[(8 + q) * NT] = o.JW[q];
+                        T[14 * NT] = o.lam;
+                    }
+                }
+            }
+            // ---- weighted normal equations once the parameters are published
+            if (!cta_wait(st, &mb->rob_flag, (unsigned)it + 1u, &go[2])) break;
+            if (tid < (int)(sizeof(RobustParams) / 4))
+                reinterpret_cast<int*>(&sh_rob)[tid] = __ldcg(reinterpret_cast<const int*>(&mb->rob) + tid);
+            __syncthreads();
+            const RobustParams rob = sh_rob;
+            float acc[kSlots];
+#pragma unroll
+            for (int i = 0; i < kSlots; ++i) acc[i] = 0.f;
+#pragma unroll 1
+            for (int j = 0; j < a.max_tiles; ++j) {
+                const float* const T = Tm + j * (kSplitTerms * NT);
+                const float rI = T[0], rW = T[NT];
+                if (rI == rI) {
+                    acc[kSlotNI] += 1.f;
+                    if (rob.ok[0]) {
+                        float Jl[6];
+#pragma unroll
+                        for (int q = 0; q < 6; ++q) Jl[q] = T[(2 + q) * NT];
+                        accumulate(acc, Jl, robust_weight(rI, rob.mu[0], rob.sigma[0], rob.nu[0]), rI);
+                    }
+                }
+                if (rW == rW) {
+                    acc[kSlotNW] += 1.f;
+                    if (rob.ok[1]) {
+                        float Jl[6];
+#pragma unroll
+                        for (int q = 0; q < 6; ++q) Jl[q] = T[(8 + q) * NT];
+                        accumulate(acc, Jl, T[14 * NT] * robust_weight(rW, rob.mu[1], rob.sigma[1], rob.nu[1]), rW);
+                    }
+                }
+            }
+            red_w[warp][lane] = warp_reduce_scatter32(acc);
+            __syncthreads();
+            if (warp == 0) {
+                F2 sum{0.f, 0.f};
+#pragma unroll
+                for (int w = 0; w < NW; ++w) sum.add(red_w[w][lane]);
+                __stcg(a.partials + (size_t)hc * kSlots + lane, make_float2(sum.hi, sum.lo));
+                __threadfence();
+                __syncwarp();
+                if (lane == 0) atomicAdd(&mb->arrived, 1u);
+            }
+        }
+    }
+    // ---- the last CTA to leave resets the mailbox for the next launch
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        const unsigned int done = atomicAdd(&mb->exited, 1u) + 1u;
+        if (done == gridDim.x) {
+            mb->pose_flag = 0u;
+            mb->rob_flag = 0u;
+            mb->arrived = 0u;
+            mb->error = 0;
+            __threadfence();
+            mb->exited = 0u;
+        }
+    }
+}
+
 // ---------------------------------------------------------------- host side
 template <int PREC, int MAXP>
 static cudaError_t level_attributes() {
@@ -512,6 +1016,106 @@ cudaError_t launch_level(int precision, const LevelArgs& la, cudaStream_t stream
     if (n < 1 || n > kLevelMaxPixels) return cudaErrorInvalidValue;
     return precision == RGBID_PLANES_F32 ? launch_level_t<RGBID_PLANES_F32>(la, stream)
                                          : launch_level_t<RGBID_PLANES_BF16_F16>(la, stream);
+}
+
+// ---- split kernel
+constexpr size_t kSplitMaxSmem = (size_t)kSplitMaxTiles * kSplitTerms * kRobustNT * sizeof(float);
+constexpr size_t kSplitSampleSmem =
+    (size_t)((RGBID_MAX_SAMPLES + kLevelCL * kRobustNT - 1) / (kLevelCL * kRobustNT)) * kSampleTerms * kRobustNT *
+    sizeof(float);
+
+static size_t split_smem(int max_tiles) {
+    return std::max((size_t)max_tiles * kSplitTerms * kRobustNT * sizeof(float), kSplitSampleSmem);
+}
+
+template <int PREC>
+static cudaError_t split_attributes() {
+    cudaError_t e = cudaFuncSetAttribute(split_kernel<PREC>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(split_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSplitMaxSmem);
+}
+
+// Helper CTAs: every co-resident 16-CTA cluster after the first (at the largest
+// shared memory a launch takes), at most 8 clusters; a fixed property of the
+// device, cached per ordinal.
+template <int PREC>
+static int split_helpers_t() {
+    static std::atomic<int> cached[64];   // 0 unknown, -1 none, else helper CTAs
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    int c = cached[dev].load(std::memory_order_relaxed);
+    if (c == 0) {
+        int nclusters = 0;
+        if (split_attributes<PREC>() == cudaSuccess) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(kLevelCL, 1, 1);
+            cfg.blockDim = dim3(kRobustNT, 1, 1);
+            cfg.dynamicSmemBytes = kSplitMaxSmem;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = kLevelCL;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            if (cudaOccupancyMaxActiveClusters(&nclusters, split_kernel<PREC>, &cfg) != cudaSuccess) nclusters = 0;
+        }
+        (void)cudaGetLastError();
+        c = nclusters >= 2 ? std::min(kLevelCL * (nclusters - 1), kSplitMaxHelpers) : -1;
+        cached[dev].store(c, std::memory_order_relaxed);
+    }
+    return c > 0 ? c : 0;
+}
+
+int split_kernel_helpers(int precision) {
+    return precision == RGBID_PLANES_F32 ? split_helpers_t<RGBID_PLANES_F32>()
+                                         : split_helpers_t<RGBID_PLANES_BF16_F16>();
+}
+
+bool split_kernel_takes(int precision, int w, int h) {
+    const int nh = split_kernel_helpers(precision);
+    if (nh <= 0) return false;
+    const long long tiles = (long long)((w + kSplitTileW - 1) / kSplitTileW) * ((h + kSplitTileH - 1) / kSplitTileH);
+    return (tiles + nh - 1) / nh <= kSplitMaxTiles;
+}
+
+template <int PREC>
+static cudaError_t launch_split_t(const SplitArgs& sa, cudaStream_t stream) {
+    cudaError_t e = split_attributes<PREC>();
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(kLevelCL + sa.n_helpers), 1, 1);
+    cfg.blockDim = dim3(kRobustNT, 1, 1);
+    cfg.dynamicSmemBytes = split_smem(sa.max_tiles);
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[3];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kLevelCL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeCooperative;   // every CTA resident: the roles wait on one another
+    attr[1].val.cooperative = 1;
+    attr[2].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[2].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 3;
+    return cudaLaunchKernelEx(&cfg, split_kernel<PREC>, sa);
+}
+
+cudaError_t launch_split(int precision, const SplitArgs& sa, cudaStream_t stream) {
+    if (sa.n_helpers <= 0 || sa.n_helpers > kSplitMaxHelpers || sa.n_helpers % kLevelCL ||
+        sa.n_helpers != split_kernel_helpers(precision))
+        return cudaErrorInvalidValue;
+    if (sa.max_tiles < 1 || sa.max_tiles > kSplitMaxTiles ||
+        (long long)sa.max_tiles * sa.n_helpers < (long long)sa.tiles_x * sa.tiles_y)
+        return cudaErrorInvalidValue;
+    if (sa.tiles_x * kSplitTileW < sa.A.w || sa.tiles_y * kSplitTileH < sa.A.h) return cudaErrorInvalidValue;
+    if (sa.nsamp < 1 || sa.nsamp > RGBID_MAX_SAMPLES) return cudaErrorInvalidValue;
+    return precision == RGBID_PLANES_F32 ? launch_split_t<RGBID_PLANES_F32>(sa, stream)
+                                         : launch_split_t<RGBID_PLANES_BF16_F16>(sa, stream);
 }
 
 }  // namespace rgbid

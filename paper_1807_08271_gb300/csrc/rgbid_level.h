@@ -27,6 +27,38 @@ struct LevelArgs {
     float nu_g[kNuGTerms];    // Chebyshev series of the nu equation's constant part on [nu_lo, nu_hi]
 };
 
+// The split level kernel (a level whose sample is a strict subset of its pixels): one
+// 16-CTA cluster solves, samples and estimates the robust parameters; helper CTAs of
+// the same cooperative launch evaluate every pixel's terms as soon as the pose is
+// published and accumulate them once the parameters are.
+constexpr int kSplitTileW = 32, kSplitTileH = 8;   // one pixel per thread per tile
+constexpr int kSplitTerms = 15;                    // per pixel in shared memory: r_I, r_W, J_I, J_W, lambda_n
+constexpr int kSplitMaxTiles = 13;                 // tiles per helper CTA (shared memory)
+constexpr int kSplitMaxHelpers = 8 * 16;           // helper CTAs at most (8 clusters)
+
+struct SplitArgs {
+    LevelDev A, B;
+    AlignState* st;
+    float2* partials;         // pending partials of the previous launch, then one per helper CTA
+    int iters;
+    const int* level_iters;
+    int level;
+    int s, nsx, nsamp;        // the systematic sample
+    int scale_iters, bisect_steps, estimate_nu, min_valid;
+    float nu0;
+    double nu_lo, nu_hi;
+    float nu_g[kNuGTerms];
+    int n_helpers;            // helper CTAs (the grid's CTAs after the first cluster)
+    int tiles_x, tiles_y;     // kSplitTileW x kSplitTileH tiles of the level
+    int max_tiles;            // tiles per helper CTA
+};
+
+// Helper CTAs the split kernel launches on the current device (0: not available).
+int split_kernel_helpers(int precision);
+// Whether a w x h level runs in the split kernel (its tiles fit the helpers).
+bool split_kernel_takes(int precision, int w, int h);
+cudaError_t launch_split(int precision, const SplitArgs& sa, cudaStream_t stream);
+
 // Whether a w x h level with sample cap `cap` runs in the level kernel on the current
 // device (its sample is every pixel, the pixels fit one launch, and the device
 // schedules the 16-CTA cluster with the kernel's shared memory).

@@ -49,6 +49,7 @@ KERNEL_SWEEP = 0
 KERNEL_ROBUST = 1
 KERNEL_BATCH = 2
 KERNEL_LEVEL = 3
+KERNEL_SPLIT = 4
 
 
 class Timing(Structure):

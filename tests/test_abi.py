@@ -303,8 +303,9 @@ def test_nu_constant_series_matches_digamma(binding):
 def test_workspace_covers_the_largest_sweep_over_the_levels(binding):
     """The alignment workspace holds the state plus one 32-slot compensated pair per
     block of the largest sweep over the reference's levels (32-pixel-wide tiles of
-    8 rows on levels under 250K pixels, 32 rows on larger ones).  Descriptor-only
-    pyramids: nothing is read or launched."""
+    8 rows on levels under 250K pixels, 32 rows on larger ones), and at least one per
+    helper CTA the split level kernel may launch (128).  Descriptor-only pyramids:
+    nothing is read or launched."""
     b = binding
 
     def blocks(w, h):
@@ -315,7 +316,7 @@ def test_workspace_covers_the_largest_sweep_over_the_levels(binding):
         P = b.Pyramid()
         P.levels, P.precision = levels, b.PLANES_F32
         w, h = w0, h0
-        nb = 0
+        nb = 128
         for l in range(levels):
             P.lv[l].width, P.lv[l].height, P.lv[l].pitch = w, h, w
             nb = max(nb, blocks(w, h))

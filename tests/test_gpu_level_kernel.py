@@ -1,6 +1,9 @@
-"""The persistent level kernel of rgbid_align (a level whose systematic sample is
-every pixel runs all its Gauss-Newton iterations in one 16-CTA cluster launch)
-against the per-iteration robust-scale and sweep kernels and the FP64 oracle.
+"""The one-launch-per-level kernels of rgbid_align against the per-iteration
+robust-scale and sweep kernels and the FP64 oracle: the persistent level kernel (a
+level whose systematic sample is every pixel runs all its Gauss-Newton iterations in
+one 16-CTA cluster launch) and the split kernel (a larger level: the cluster solves,
+samples and estimates the robust parameters while helper CTAs of the same
+cooperative launch evaluate every pixel).
 
 Both paths evaluate the same steps ("Iterative optimisation", "Error
 distribution and robust optimisation"); their FP32 sums run in another order,
@@ -54,8 +57,9 @@ def _both_paths(pair, levels, iters, precision=R.PLANES_F32, T_init=None):
 @pytest.mark.parametrize("precision", [R.PLANES_F32, R.PLANES_BF16_F16])
 def test_level_kernel_matches_the_per_iteration_kernels_and_the_oracle(pair640, precision):
     a, b, (PA, _, pa, pb) = _both_paths(pair640, 4, (5, 5, 5, 10), precision)
-    # two level-kernel launches (80x60, 160x120) replace 2 x 15 per-iteration launches
-    assert R.rgbid_align_launches(PA.desc, pa) == 2 + 2 * 10 + 2
+    # two level-kernel launches (80x60, 160x120) and two split launches (320x240,
+    # 640x480) replace 2 x 25 per-iteration launches
+    assert R.rgbid_align_launches(PA.desc, pa) == 2 + 4
     assert R.rgbid_align_launches(PA.desc, pb) == 2 + 2 * 25
     er, et = pose_error(a["T"], b["T"])
     assert er <= PATHS_TOL and et <= PATHS_TOL, (er, et)
@@ -100,6 +104,12 @@ def test_device_iteration_counts_in_the_level_kernel(pair640):
     per_it, _ = _align(PA, PB, 4, (5, 5, 5, 10), False, level_iters=counts)
     er, et = pose_error(dev_sched["T"], per_it["T"])
     assert er <= PATHS_TOL and et <= PATHS_TOL, (er, et)
+    # device counts that cut the split levels too
+    counts2 = torch.tensor([2, 3, 5, 10], dtype=torch.int32, device="cuda")
+    dev2, _ = _align(PA, PB, 4, (5, 5, 5, 10), True, level_iters=counts2)
+    host2, _ = _align(PA, PB, 4, (2, 3, 5, 10), True)
+    assert np.array_equal(dev2["T"], host2["T"]) and np.array_equal(dev2["H"], host2["H"])
+    assert dev2["iters_done"] == 20
 
 
 def test_level_kernel_timing_counts_its_launches_and_units(pair640):
@@ -109,6 +119,33 @@ def test_level_kernel_timing_counts_its_launches_and_units(pair640):
     assert timer.t.count == 2
     assert timer.t.units == 160 * 120 * 5 + 80 * 60 * 10
     assert timer.total_ms() > 0.0
+    split = R.KernelTimer(R.KERNEL_SPLIT, 8)
+    _align(PA, PB, 4, (5, 5, 5, 10), True, timer=split)
+    assert split.t.count == 2
+    assert split.t.units == 640 * 480 * 5 + 320 * 240 * 5
+    assert split.total_ms() > 0.0
+
+
+def test_split_kernel_is_deterministic(pair640):
+    (PA, _, _), (PB, _, _) = gpu_pair(pair640, 4)
+    a, _ = _align(PA, PB, 4, (5, 5, 5, 10), True)
+    b, _ = _align(PA, PB, 4, (5, 5, 5, 10), True)
+    assert np.array_equal(a["T"], b["T"]) and np.array_equal(a["H"], b["H"]) and np.array_equal(a["g"], b["g"])
+
+
+def test_split_kernel_on_a_pyramid_with_few_sweep_blocks():
+    """A 200x100 finest level (stride 2, 91 tiles): fewer sweep blocks than helper CTAs,
+    so the workspace must hold a partial per helper."""
+    K = (200.0, 200.0, 99.5, 49.5)
+    pair = synth.make_pair(9, 200, 100, K=K, max_angle_deg=3.0, max_trans=0.05)
+    a, b, (PA, _, pa, _) = _both_paths(pair, 2, (5, 10))
+    assert R.rgbid_align_launches(PA.desc, pa) == 2 + 2
+    er, et = pose_error(a["T"], b["T"])
+    assert er <= PATHS_TOL and et <= PATHS_TOL, (er, et)
+    A, B = oracle_pair(pair, 2)
+    o = O.align(A, B, None, O.AlignParams(levels=2, iters=(5, 10)))
+    er, et = pose_error(a["T"], o["T"])
+    assert er <= POSE_TOL and et <= POSE_TOL, (er, et)
 
 
 def test_a_level_without_measurements_is_degenerate_in_the_level_kernel():
@@ -120,3 +157,13 @@ def test_a_level_without_measurements_is_degenerate_in_the_level_kernel():
     for g in (a, b):
         assert np.array_equal(g["T"], T0)
         assert g["status"] == R.ERR_DEGENERATE and g["iters_skipped"] == 20 and g["n_valid"] == [0, 0]
+
+
+def test_a_reference_without_measurements_is_degenerate_in_the_split_kernel(pair640):
+    p = dict(pair640)
+    p["W_A"] = np.zeros_like(p["W_A"])
+    T0 = O.se3_exp([0.0, 0.01, 0, 0, 0, 0.002])
+    a, b, _ = _both_paths(p, 4, (5, 5, 5, 10), T_init=T0)
+    for g in (a, b):
+        assert np.array_equal(g["T"], T0)
+        assert g["status"] == R.ERR_DEGENERATE and g["iters_skipped"] == 25 and g["n_valid"] == [0, 0]
