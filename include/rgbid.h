@@ -354,10 +354,13 @@ int rgbid_batch_autotune(const rgbid_batch_item* d_items, int n_items, int preci
  * rgbid_net_param_offset(l, 0) stored [kh][kw][c_in][c_out] (convolutions)
  * or [in][out] (fully connected), its biases at rgbid_net_param_offset(l, 1);
  * every tensor starts on a multiple of 64 floats.  The forward and backward
- * passes compute on bfloat16 tensor cores (mma.sync m16n8k16, FP32
- * accumulation): weights, inputs, hidden activations and back-propagated
- * activation gradients are rounded to bfloat16 where they are stored; the
- * output, biases and parameter gradients are float32.
+ * passes compute on the fifth-generation tensor cores (tcgen05.mma, bfloat16
+ * operands in shared memory, FP32 accumulators in tensor memory): weights,
+ * inputs, hidden activations and back-propagated activation gradients are
+ * rounded to bfloat16 where they are stored; the output, biases and parameter
+ * gradients are float32.  The first rgbid_net_workspace_bytes call on a device
+ * sets the GEMM kernels' shared-memory attribute there: make it before any
+ * stream capture of the passes.
  */
 #define RGBID_NET_IN_H 60
 #define RGBID_NET_IN_W 80
@@ -375,6 +378,12 @@ size_t rgbid_net_param_offset(int layer, int what);
 /* Workspace bytes for batches of up to `batch` inputs (bfloat16 weights,
  * activations kept for the backward pass, activation gradients). */
 size_t rgbid_net_workspace_bytes(int batch);
+
+/* Waits of the network's GEMM kernels on their tensor-core operations that ran
+ * out of their ~2 s budget on the current device since the library was loaded
+ * (0 in a healthy run; a CTA whose wait runs out still finishes, with a wrong
+ * tile).  Synchronises the device; returns (unsigned)-1 if it cannot be read. */
+unsigned int rgbid_net_wait_timeouts(void);
 
 /* Fill `params` (device, rgbid_net_param_count floats) with He-uniform weights
  * U(-sqrt(6/fan_in), sqrt(6/fan_in)) drawn from splitmix64(seed, index), biases 0. */

@@ -3,8 +3,8 @@
 // pyramid levels, and the plan that turns proposals into batch items.
 //
 // Every layer pass is one implicit GEMM C[M x N] = A[M x K] B[K x N] computed
-// by mma.sync.m16n8k16 (bf16 operands, FP32 accumulation) in 64 x 64 tiles
-// with K-steps of 32; a problem type supplies how A and B elements are
+// by tcgen05.mma (bf16 operands in shared memory, FP32 accumulator in tensor
+// memory) in 128 x 64 tiles with K-slices of 64; a problem type supplies how A and B elements are
 // gathered (convolution patches, transposed weights, upstream gradients) and
 // what the epilogue does (bias, ReLU, rounding to bf16, the ReLU mask of the
 // layer below, or FP32 atomics for split-K weight gradients):
@@ -18,6 +18,9 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
+#include <type_traits>
+#include <utility>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -66,136 +69,395 @@ constexpr size_t kMaxGradPerSample = act_per_sample(0);   // the largest activat
 __device__ __forceinline__ bf16 bz() { return __float2bfloat16_rn(0.f); }
 
 // ---------------------------------------------------------------- GEMM core
-constexpr int BM = 64, BN = 64, BK = 32, LDS = BK + 8, GEMM_NT = 128;
+// One CTA of 128 threads computes a 128 x TN tile of C (TN = 32 or 64, the
+// smallest that covers N) on the fifth-generation tensor cores: the four warps
+// gather 64-wide K slices of A (128 rows) and B (TN rows) into shared memory, one
+// thread issues tcgen05.mma (M = 128, N = TN, K = 16 per instruction, bf16
+// operands, FP32 accumulator in tensor memory) and commits them to an mbarrier.
+// Two stages alternate: while the tensor core reads one, each thread's loads of
+// the next slice are already in flight in registers and land in the other stage
+// once the MMAs that last read it have completed.  The epilogue reads the
+// accumulator back with tcgen05.ld (warp w owns rows 32w .. 32w + 31, one row per
+// lane) and hands each element to the problem's store.
+//
+// Shared-memory operand layout (both operands K-major, no swizzle): an 8-row x
+// 16-byte core matrix is 128 contiguous bytes; the 8 core matrices along K of one
+// 8-row group follow each other (128 B apart, the descriptor's leading-dimension
+// offset) and the 8-row groups are 1024 B apart (its stride-dimension offset).
+// Element (r, k) of a tile therefore sits at byte
+//     (r / 8) * 1024 + (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2,
+// and the 16-byte vector i of a tile (8 consecutive k of one row) at byte 16 i
+// when i enumerates rows fastest within a core matrix, then K chunks, then row
+// groups.
+constexpr int TM = 128, TK = 64, GEMM_NT = 128, kStages = 2;
+constexpr int kATile = TM * TK * 2;
 constexpr int kVecBNone = 0, kVecBk = 1, kVecBn = 2;   // how B may be loaded 8 elements at a time
 constexpr int kVecANone = 0, kVecAk = 1, kVecAm = 2;   // how A may be loaded 8 elements at a time
+constexpr int kVecAk4 = 3, kVecAm4 = 4;                 // ... or 4 elements (8 bytes) at a time
+constexpr long long kMmaWaitBudget = 4000000000LL;     // clock64 cycles (~2 s) before a wait gives up
+
+template <int TN>
+struct TileCfg {
+    static constexpr int kBTile = TN * TK * 2;
+    static constexpr int kStageBytes = kATile + kBTile;
+    static constexpr int kSmem = kStages * kStageBytes + 128;   // + alignment slack
+    static constexpr uint32_t kCols = TN;                       // FP32 accumulator columns (a power of 2, >= 32)
+    // instruction descriptor of kind::f16: FP32 D (bits 4-5), bf16 A (7-9) and B (10-12),
+    // both K-major (bits 15, 16 clear), N >> 3 at bit 17, M >> 4 at bit 24
+    static constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
+                                       ((uint32_t)(TM >> 4) << 24);
+};
+
+__device__ unsigned int g_mma_timeouts;   // waits on the tensor core that ran out (0 in a healthy run)
 
 __device__ __forceinline__ uint4 ld16(const bf16* p) { return *reinterpret_cast<const uint4*>(p); }
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ uint32_t ld_pair(const bf16* p) { return *reinterpret_cast<const uint32_t*>(p); }
-
-__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-        "{%0, %1, %2, %3};"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+// shared-memory matrix descriptor: start >> 4 (bits 0-13), leading-dimension offset
+// >> 4 (16-29), stride-dimension offset >> 4 (32-45), descriptor version 1 (bit 46),
+// base offset 0, no swizzle (bits 61-63 = 0)
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)(1024u >> 4) << 32) |
+           (1ull << 46);
 }
 
-// C tile (blockIdx.x, blockIdx.y) over the K range of blockIdx.z; 4 warps in a
-// 2 x 2 arrangement, each 32 x 32 = 2 (m16) x 4 (n8) mma tiles.
-template <class P>
-__global__ void __launch_bounds__(GEMM_NT) gemm_bf16(P p, int M, int N, int K, int kchunk, float* scratch) {
-    __shared__ __align__(16) bf16 As[BM][LDS];
-    __shared__ __align__(16) bf16 Bs[BN][LDS];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = warp >> 1, wn = warp & 1;
-    const int g = lane >> 2, t = lane & 3;
-    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
-    const int kb0 = blockIdx.z * kchunk;
-    const int kb1 = min(K, kb0 + kchunk);
-    float acc[2][4][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+__device__ __forceinline__ void mbar_init1(unsigned long long* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(bar)) : "memory");
+}
 
-    // Vector loaders: 8 bf16 (16 bytes) per load where the operand is contiguous along
-    // k (A; B with kVecBk) or along n (B with kVecBn); the problem type says when its
-    // layout allows it (channel counts that are multiples of 8, so that every vector
-    // stays inside one tap and is 16-byte aligned, and K a multiple of 8, so that a
-    // vector that starts before the end of the K range ends before it too).
-    const bool vecAk = p.vecA() == kVecAk, vecAm = p.vecA() == kVecAm;
-    const bool vecBk = p.vecB() == kVecBk, vecBn = p.vecB() == kVecBn;
-    for (int k0 = kb0; k0 < kb1; k0 += BK) {
-        if (vecAk) {
-            for (int i = tid; i < BM * BK / 8; i += GEMM_NT) {
-                const int r = i >> 2, c8 = (i & 3) * 8;
-                const int m = m0 + r, k = k0 + c8;
-                *reinterpret_cast<uint4*>(&As[r][c8]) = (m < M && k < kb1) ? p.loadA8(m, k) : make_uint4(0u, 0u, 0u, 0u);
-            }
-        } else if (vecAm) {
-            // 8 consecutive rows m of one column k (the problem zero-fills rows from M on)
-            for (int i = tid; i < BK * BM / 8; i += GEMM_NT) {
-                const int c = i >> 3, m8 = (i & 7) * 8;
-                const int k = k0 + c, m = m0 + m8;
-                const uint4 v = (k < kb1 && m < M) ? p.loadA8(m, k) : make_uint4(0u, 0u, 0u, 0u);
-                const bf16* e = reinterpret_cast<const bf16*>(&v);
-#pragma unroll
-                for (int j = 0; j < 8; ++j) As[m8 + j][c] = e[j];
-            }
-        } else {
-            for (int i = tid; i < BM * BK; i += GEMM_NT) {
-                const int r = i >> 5, c = i & 31;
-                const int m = m0 + r, k = k0 + c;
-                As[r][c] = (m < M && k < kb1) ? p.loadA(m, k) : bz();
-            }
-        }
-        if (vecBk) {
-            for (int i = tid; i < BN * BK / 8; i += GEMM_NT) {
-                const int r = i >> 2, c8 = (i & 3) * 8;
-                const int n = n0 + r, k = k0 + c8;
-                *reinterpret_cast<uint4*>(&Bs[r][c8]) = (n < N && k < kb1) ? p.loadB8(k, n) : make_uint4(0u, 0u, 0u, 0u);
-            }
-        } else if (vecBn) {
-            for (int i = tid; i < BK * BN / 8; i += GEMM_NT) {
-                const int c = i >> 3, n8 = (i & 7) * 8;
-                const int k = k0 + c, n = n0 + n8;
-                const uint4 v = (k < kb1 && n < N) ? p.loadB8(k, n) : make_uint4(0u, 0u, 0u, 0u);
-                const bf16* e = reinterpret_cast<const bf16*>(&v);
-#pragma unroll
-                for (int j = 0; j < 8; ++j) Bs[n8 + j][c] = e[j];
-            }
-        } else {
-            for (int i = tid; i < BN * BK; i += GEMM_NT) {
-                const int r = i >> 5, c = i & 31;
-                const int n = n0 + r, k = k0 + c;
-                Bs[r][c] = (n < N && k < kb1) ? p.loadB(k, n) : bz();
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int ks = 0; ks < BK; ks += 16) {
-            uint32_t a[2][4], b[4][2];
-#pragma unroll
-            for (int mi = 0; mi < 2; ++mi) {
-                const int rb = wm * 32 + mi * 16;
-                a[mi][0] = ld_pair(&As[rb + g][ks + 2 * t]);
-                a[mi][1] = ld_pair(&As[rb + g + 8][ks + 2 * t]);
-                a[mi][2] = ld_pair(&As[rb + g][ks + 2 * t + 8]);
-                a[mi][3] = ld_pair(&As[rb + g + 8][ks + 2 * t + 8]);
-            }
-#pragma unroll
-            for (int ni = 0; ni < 4; ++ni) {
-                const int cb = wn * 32 + ni * 8;
-                b[ni][0] = ld_pair(&Bs[cb + g][ks + 2 * t]);
-                b[ni][1] = ld_pair(&Bs[cb + g][ks + 2 * t + 8]);
-            }
-#pragma unroll
-            for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-                for (int ni = 0; ni < 4; ++ni) mma_bf16(acc[mi][ni], a[mi], b[ni]);
-        }
-        __syncthreads();
+// waits until the phase of parity `parity` has completed; false if the budget ran out
+__device__ __forceinline__ bool mbar_wait_parity(unsigned long long* bar, uint32_t parity) {
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n"
+            " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(ok)
+            : "r"(su32(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > kMmaWaitBudget) return false;
     }
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// D[tmem] (+)= A[128 x 16] B[TN x 16]^T
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n"
+        " setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// arrives on `bar` once every tcgen05.mma this thread issued so far has completed
+__device__ __forceinline__ void umma_commit(unsigned long long* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+                 : "memory");
+}
+
+// 16 consecutive FP32 columns of this lane's accumulator row
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    // the registers are defined only once the load has completed
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15])
+                 :
+                 : "memory");
 #pragma unroll
-    for (int mi = 0; mi < 2; ++mi) {
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// byte offset of element (r, k) of an operand tile
+__device__ __forceinline__ int tile_off(int r, int k) { return (r >> 3) * 1024 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2; }
+
+// An operand tile is ROWS rows x TK columns: row r is operand row row0 + r (m of A or
+// n of B), column c is k0 + c.  The vector loaders move 16 bytes: 8 consecutive k of
+// one row (MODE 1; vector i lands at byte 16 i) or rows row .. row+7 of one k (MODE 2;
+// the 8 values go to one core matrix, 16 bytes apart).  fetch() issues a thread's
+// loads of one slice into registers, put() stores them into a stage.
+template <int ROWS>
+struct Vecs {
+    static constexpr int n = ROWS * TK / 8 / GEMM_NT;
+    uint4 v[n];
+};
+
+template <int ROWS, int MODE, class L8>
+__device__ __forceinline__ void fetch(Vecs<ROWS>& r, int row0, int nrows, int k0, int k1, int tid, L8 ld8) {
 #pragma unroll
-        for (int ni = 0; ni < 4; ++ni) {
-            const int r = m0 + wm * 32 + mi * 16 + g;
-            const int c = n0 + wn * 32 + ni * 8 + 2 * t;
+    for (int j = 0; j < Vecs<ROWS>::n; ++j) {
+        const int i = tid + j * GEMM_NT;
+        const int row = MODE == 1 ? row0 + ((i & 7) | ((i >> 6) << 3)) : row0 + (i >> 6) * 8;
+        const int k = MODE == 1 ? k0 + ((i >> 3) & 7) * 8 : k0 + (i & (TK - 1));
+        r.v[j] = (row < nrows && k < k1) ? ld8(row, k) : make_uint4(0u, 0u, 0u, 0u);
+    }
+}
+
+template <int ROWS, int MODE>
+__device__ __forceinline__ void put(unsigned char* t, const Vecs<ROWS>& r, int tid) {
+#pragma unroll
+    for (int j = 0; j < Vecs<ROWS>::n; ++j) {
+        const int i = tid + j * GEMM_NT;
+        if (MODE == 1) {
+            *reinterpret_cast<uint4*>(t + 16 * i) = r.v[j];
+        } else {
+            unsigned char* const base = t + tile_off((i >> 6) * 8, i & (TK - 1));
+            const uint32_t w[4] = {r.v[j].x, r.v[j].y, r.v[j].z, r.v[j].w};
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const int rr = r + (q >> 1) * 8, cc = c + (q & 1);
-                if (rr < M && cc < N) {
-                    if (scratch) scratch[((size_t)blockIdx.z * M + rr) * N + cc] = acc[mi][ni][q];
-                    else p.store(rr, cc, acc[mi][ni][q]);
-                }
+                *reinterpret_cast<unsigned short*>(base + 32 * q) = (unsigned short)(w[q] & 0xffffu);
+                *reinterpret_cast<unsigned short*>(base + 32 * q + 16) = (unsigned short)(w[q] >> 16);
             }
         }
     }
+}
+
+// 8-byte variants for operands whose channel count is a multiple of 4 but not of 8:
+// 4 consecutive k of one row (MODE 3; vector i lands at byte 8 i when i enumerates
+// the two halves of a 16-byte chunk fastest, then the 8 rows of a core matrix, then
+// K chunks, then row groups) or rows row .. row+3 of one k (MODE 4).
+struct Vecs4 {
+    static constexpr int n = TM * TK / 4 / GEMM_NT;
+    uint2 v[n];
+};
+
+template <int MODE, class L4>
+__device__ __forceinline__ void fetch4(Vecs4& r, int row0, int nrows, int k0, int k1, int tid, L4 ld4) {
+#pragma unroll
+    for (int j = 0; j < Vecs4::n; ++j) {
+        const int i = tid + j * GEMM_NT;
+        const int row = MODE == 3 ? row0 + (((i >> 1) & 7) | ((i >> 7) << 3)) : row0 + (i >> 6) * 4;
+        const int k = MODE == 3 ? k0 + ((i >> 4) & 7) * 8 + (i & 1) * 4 : k0 + (i & (TK - 1));
+        r.v[j] = (row < nrows && k < k1) ? ld4(row, k) : make_uint2(0u, 0u);
+    }
+}
+
+template <int MODE>
+__device__ __forceinline__ void put4(unsigned char* t, const Vecs4& r, int tid) {
+#pragma unroll
+    for (int j = 0; j < Vecs4::n; ++j) {
+        const int i = tid + j * GEMM_NT;
+        if (MODE == 3) {
+            *reinterpret_cast<uint2*>(t + 8 * i) = r.v[j];
+        } else {
+            unsigned char* const base = t + tile_off((i >> 6) * 4, i & (TK - 1));
+            *reinterpret_cast<unsigned short*>(base) = (unsigned short)(r.v[j].x & 0xffffu);
+            *reinterpret_cast<unsigned short*>(base + 16) = (unsigned short)(r.v[j].x >> 16);
+            *reinterpret_cast<unsigned short*>(base + 32) = (unsigned short)(r.v[j].y & 0xffffu);
+            *reinterpret_cast<unsigned short*>(base + 48) = (unsigned short)(r.v[j].y >> 16);
+        }
+    }
+}
+
+// whether a problem type has the 8-byte A loader
+template <class P, class = void>
+struct HasA4 : std::false_type {};
+template <class P>
+struct HasA4<P, decltype((void)std::declval<const P&>().loadA4(0, 0))> : std::true_type {};
+
+// element-wise loader (operands whose layout allows no 16-byte vectors)
+template <int ROWS, class L1>
+__device__ __forceinline__ void load_elements(unsigned char* t, int row0, int nrows, int k0, int k1, int tid, L1 ld1) {
+#pragma unroll 4
+    for (int i = tid; i < ROWS * TK; i += GEMM_NT) {
+        const int c = i & (TK - 1), r = i >> 6;
+        const int row = row0 + r, k = k0 + c;
+        *reinterpret_cast<bf16*>(t + tile_off(r, c)) = (row < nrows && k < k1) ? ld1(row, k) : bz();
+    }
+}
+
+// ---------------------------------------------------------------- epilogue helpers
+// A lane's 16 accumulator columns c0 .. c0+15 of one row, of which the first nv exist,
+// go out as 16-byte vectors where the row segment is whole and aligned.
+__device__ __forceinline__ bool al16(const void* p) { return !((uintptr_t)p & 15u); }
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(lo)) |
+           ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(hi)) << 16);
+}
+
+__device__ __forceinline__ void put_bf16_row(bf16* dst, const float (&z)[16], int nv) {
+    if (nv == 16 && al16(dst)) {
+        uint4 a, b;
+        a.x = pack_bf16(z[0], z[1]);
+        a.y = pack_bf16(z[2], z[3]);
+        a.z = pack_bf16(z[4], z[5]);
+        a.w = pack_bf16(z[6], z[7]);
+        b.x = pack_bf16(z[8], z[9]);
+        b.y = pack_bf16(z[10], z[11]);
+        b.z = pack_bf16(z[12], z[13]);
+        b.w = pack_bf16(z[14], z[15]);
+        reinterpret_cast<uint4*>(dst)[0] = a;
+        reinterpret_cast<uint4*>(dst)[1] = b;
+    } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            if (j < nv) dst[j] = __float2bfloat16_rn(z[j]);
+    }
+}
+
+__device__ __forceinline__ void put_f32_row(float* dst, const float (&z)[16], int nv) {
+    if (nv == 16 && al16(dst)) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) reinterpret_cast<float4*>(dst)[q] = make_float4(z[4 * q], z[4 * q + 1], z[4 * q + 2], z[4 * q + 3]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            if (j < nv) dst[j] = z[j];
+    }
+}
+
+// upstream gradient masked by the ReLU of the layer's input (its stored value > 0)
+__device__ __forceinline__ void put_masked_row(bf16* gin, const bf16* act, const float (&v)[16], int nv) {
+    if (nv == 16 && al16(gin) && al16(act)) {
+        const uint4 a0 = __ldg(reinterpret_cast<const uint4*>(act)), a1 = __ldg(reinterpret_cast<const uint4*>(act) + 1);
+        const uint32_t w[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        float z[16];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const float lo = __bfloat162float(__ushort_as_bfloat16((unsigned short)(w[q] & 0xffffu)));
+            const float hi = __bfloat162float(__ushort_as_bfloat16((unsigned short)(w[q] >> 16)));
+            z[2 * q] = lo > 0.f ? v[2 * q] : 0.f;
+            z[2 * q + 1] = hi > 0.f ? v[2 * q + 1] : 0.f;
+        }
+        put_bf16_row(gin, z, 16);
+    } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            if (j < nv) gin[j] = __bfloat162float(act[j]) > 0.f ? __float2bfloat16_rn(v[j]) : bz();
+    }
+}
+
+__device__ __forceinline__ void add_f32_row(float* dst, const float (&v)[16], int nv) {
+    if (nv == 16 && al16(dst)) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            atomicAdd(reinterpret_cast<float4*>(dst) + q, make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
+    } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            if (j < nv) atomicAdd(dst + j, v[j]);
+    }
+}
+
+// C tile (blockIdx.x, blockIdx.y) over the K range of blockIdx.z
+template <class P, int TN>
+__global__ void __launch_bounds__(GEMM_NT) gemm_tc(P p, int M, int N, int K, int kchunk, float* scratch) {
+    using Cfg = TileCfg<TN>;
+    extern __shared__ unsigned char gemm_smem[];
+    __shared__ __align__(8) unsigned long long mbar[kStages];
+    __shared__ uint32_t tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * TM, n0 = blockIdx.y * TN;
+    const int kb0 = blockIdx.z * kchunk;
+    const int kb1 = min(K, kb0 + kchunk);
+    const int nk = (kb1 - kb0 + TK - 1) / TK;
+    unsigned char* const sm =
+        reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(gemm_smem) + 127) & ~(uintptr_t)127);
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_slot)),
+                     "r"(Cfg::kCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 32) {
+        mbar_init1(&mbar[0]);
+        mbar_init1(&mbar[1]);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+
+    const int va = p.vecA(), vb = p.vecB();
+    auto la1 = [&](int m, int k) { return p.loadA(m, k); };
+    auto la8 = [&](int m, int k) { return p.loadA8(m, k); };
+    auto lb1 = [&](int n, int k) { return p.loadB(k, n); };
+    // B's rows are n: loadB8(k, n) gives k .. k+7 of row n (kVecBk) or rows n .. n+7 of column k (kVecBn)
+    auto lb8 = [&](int n, int k) { return p.loadB8(k, n); };
+    Vecs<TM> ra;
+    Vecs<TN> rb;
+    Vecs4 ra4;
+    auto fetch_slice = [&](int k0) {
+        if (va == kVecAk) fetch<TM, 1>(ra, m0, M, k0, kb1, tid, la8);
+        else if (va == kVecAm) fetch<TM, 2>(ra, m0, M, k0, kb1, tid, la8);
+        if constexpr (HasA4<P>::value) {
+            auto la4 = [&](int m, int k) { return p.loadA4(m, k); };
+            if (va == kVecAk4) fetch4<3>(ra4, m0, M, k0, kb1, tid, la4);
+            else if (va == kVecAm4) fetch4<4>(ra4, m0, M, k0, kb1, tid, la4);
+        }
+        if (vb == kVecBk) fetch<TN, 1>(rb, n0, N, k0, kb1, tid, lb8);
+        else if (vb == kVecBn) fetch<TN, 2>(rb, n0, N, k0, kb1, tid, lb8);
+    };
+    fetch_slice(kb0);   // in flight during the set-up barrier
+
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    bool ok = true;
+    for (int kt = 0; kt < nk; ++kt) {
+        const int s = kt & 1;
+        // the stage's previous MMAs (slice kt - 2) have finished reading it
+        if (kt >= 2 && !mbar_wait_parity(&mbar[s], (uint32_t)((kt >> 1) - 1) & 1u)) ok = false;
+        unsigned char* const As = sm + s * Cfg::kStageBytes;
+        unsigned char* const Bs = As + kATile;
+        const int k0 = kb0 + kt * TK;
+        if (va == kVecAk) put<TM, 1>(As, ra, tid);
+        else if (va == kVecAm) put<TM, 2>(As, ra, tid);
+        else if (HasA4<P>::value && va == kVecAk4) put4<3>(As, ra4, tid);
+        else if (HasA4<P>::value && va == kVecAm4) put4<4>(As, ra4, tid);
+        else load_elements<TM>(As, m0, M, k0, kb1, tid, la1);
+        if (vb == kVecBk) put<TN, 1>(Bs, rb, tid);
+        else if (vb == kVecBn) put<TN, 2>(Bs, rb, tid);
+        else load_elements<TN>(Bs, n0, N, k0, kb1, tid, lb1);
+        // the next slice's loads stay in flight across the barrier and the MMAs
+        if (kt + 1 < nk) fetch_slice(k0 + TK);
+        // the generic-proxy stores must be visible to the tensor core's (async-proxy) reads
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t a0 = su32(As), b0 = su32(Bs);
+#pragma unroll
+            for (int ks = 0; ks < TK / 16; ++ks)   // K = 16 is two core matrices along K: 256 bytes
+                umma_f16(tmem, umma_desc(a0 + 256u * ks), umma_desc(b0 + 256u * ks), Cfg::kIdesc, (kt | ks) != 0);
+            umma_commit(&mbar[s]);
+        }
+    }
+    // the last commit covers every MMA of the tile
+    if (!mbar_wait_parity(&mbar[(nk - 1) & 1], (uint32_t)((nk - 1) >> 1) & 1u)) ok = false;
+    tc_fence_after();
+    if (!ok && lane == 0) atomicAdd(&g_mma_timeouts, 1u);
+
+    const int rr = m0 + warp * 32 + lane;
+#pragma unroll 1
+    for (int c0 = 0; c0 < TN; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+        const int nv = min(16, N - (n0 + c0));
+        if (rr < M && nv > 0) {
+            if (scratch) put_f32_row(scratch + ((size_t)blockIdx.z * M + rr) * N + n0 + c0, v, nv);
+            else p.store_row(rr, n0 + c0, v, nv);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Cfg::kCols) : "memory");
 }
 
 // ---------------------------------------------------------------- problem types
@@ -212,6 +474,17 @@ struct ConvGeo {
         const int y = 2 * i + kh - 1, x = 2 * j + kw - 1;
         if (y < 0 || y >= H || x < 0 || x >= W) return bz();
         return in[((size_t)(b * H + y) * W + x) * C + ci];
+    }
+    // patch elements k .. k+3 (C a multiple of 4, k a multiple of 4: one tap)
+    __device__ __forceinline__ uint2 patch4(const bf16* in, int m, int k) const {
+        const int hw = Ho * Wo;
+        const int b = m / hw, r = m - b * hw;
+        const int i = r / Wo, j = r - i * Wo;
+        const int tap = k / C, ci = k - tap * C;
+        const int kh = tap / 3, kw = tap - kh * 3;
+        const int y = 2 * i + kh - 1, x = 2 * j + kw - 1;
+        if (y < 0 || y >= H || x < 0 || x >= W) return make_uint2(0u, 0u);
+        return *reinterpret_cast<const uint2*>(in + ((size_t)(b * H + y) * W + x) * C + ci);
     }
     // patch elements k .. k+7 (C a multiple of 8, k a multiple of 8: one tap)
     __device__ __forceinline__ uint4 patch8(const bf16* in, int m, int k) const {
@@ -234,12 +507,22 @@ struct ConvFwd {
     bf16* out;
     __device__ __forceinline__ bf16 loadA(int m, int k) const { return geo.patch(in, m, k); }
     __device__ __forceinline__ bf16 loadB(int k, int n) const { return W[(size_t)k * geo.Co + n]; }
-    __device__ __forceinline__ int vecA() const { return geo.C % 8 == 0 ? kVecAk : kVecANone; }
+    // (the 8-byte loads need the input 8-byte aligned; the caller's input is checked for 4 only)
+    __device__ __forceinline__ int vecA() const {
+        return geo.C % 8 == 0 ? kVecAk : (geo.C % 4 == 0 && !((uintptr_t)in & 7u) ? kVecAk4 : kVecANone);
+    }
     __device__ __forceinline__ uint4 loadA8(int m, int k) const { return geo.patch8(in, m, k); }
+    __device__ __forceinline__ uint2 loadA4(int m, int k) const { return geo.patch4(in, m, k); }
     __device__ __forceinline__ int vecB() const { return geo.Co % 8 == 0 ? kVecBn : kVecBNone; }
     __device__ __forceinline__ uint4 loadB8(int k, int n) const { return ld16(W + (size_t)k * geo.Co + n); }
     __device__ __forceinline__ void store(int m, int n, float v) const {
         out[(size_t)m * geo.Co + n] = __float2bfloat16_rn(fmaxf(v + bias[n], 0.f));
+    }
+    __device__ __forceinline__ void store_row(int m, int c0, const float (&v)[16], int nv) const {
+        float z[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) z[j] = fmaxf(v[j] + (j < nv ? __ldg(bias + c0 + j) : 0.f), 0.f);
+        put_bf16_row(out + (size_t)m * geo.Co + c0, z, nv);
     }
 };
 
@@ -260,6 +543,18 @@ struct FcFwd {
         const float z = v + bias[n];
         if (outf) outf[(size_t)m * Nout + n] = z;
         else out[(size_t)m * Nout + n] = __float2bfloat16_rn(fmaxf(z, 0.f));
+    }
+    __device__ __forceinline__ void store_row(int m, int c0, const float (&v)[16], int nv) const {
+        float z[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) z[j] = v[j] + (j < nv ? __ldg(bias + c0 + j) : 0.f);
+        if (outf) {
+            put_f32_row(outf + (size_t)m * Nout + c0, z, nv);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) z[j] = fmaxf(z[j], 0.f);
+            put_bf16_row(out + (size_t)m * Nout + c0, z, nv);
+        }
     }
 };
 
@@ -309,6 +604,10 @@ struct ConvDgrad {
         const size_t o = (size_t)m * geo.C + n;
         gin[o] = __bfloat162float(act_in[o]) > 0.f ? __float2bfloat16_rn(v) : bz();
     }
+    __device__ __forceinline__ void store_row(int m, int c0, const float (&v)[16], int nv) const {
+        const size_t o = (size_t)m * geo.C + c0;
+        put_masked_row(gin + o, act_in + o, v, nv);
+    }
 };
 
 struct FcDgrad {
@@ -331,6 +630,10 @@ struct FcDgrad {
         const size_t o = (size_t)m * Kin + n;
         gin[o] = __bfloat162float(act_in[o]) > 0.f ? __float2bfloat16_rn(v) : bz();
     }
+    __device__ __forceinline__ void store_row(int m, int c0, const float (&v)[16], int nv) const {
+        const size_t o = (size_t)m * Kin + c0;
+        put_masked_row(gin + o, act_in + o, v, nv);
+    }
 };
 
 // weight (rows < 9 C) and bias (row 9 C) gradients of a convolution, split-K over pixels
@@ -346,16 +649,26 @@ struct ConvWgrad {
     }
     __device__ __forceinline__ bf16 loadB(int k, int n) const { return gout[(size_t)k * geo.Co + n]; }
     // rows m .. m+7 of pixel k: channels of one tap, or the bias row of ones (m = 9 C, the last)
-    __device__ __forceinline__ int vecA() const { return geo.C % 8 == 0 ? kVecAm : kVecANone; }
+    __device__ __forceinline__ int vecA() const {
+        return geo.C % 8 == 0 ? kVecAm : (geo.C % 4 == 0 && !((uintptr_t)in & 7u) ? kVecAm4 : kVecANone);
+    }
     __device__ __forceinline__ uint4 loadA8(int m, int k) const {
         if (m == 9 * geo.C) return make_uint4((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(1.f)), 0u, 0u, 0u);
         return geo.patch8(in, k, m);
+    }
+    // rows m .. m+3 of pixel k (C a multiple of 4)
+    __device__ __forceinline__ uint2 loadA4(int m, int k) const {
+        if (m == 9 * geo.C) return make_uint2((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(1.f)), 0u);
+        return geo.patch4(in, k, m);
     }
     __device__ __forceinline__ int vecB() const { return geo.Co % 8 == 0 ? kVecBn : kVecBNone; }
     __device__ __forceinline__ uint4 loadB8(int k, int n) const { return ld16(gout + (size_t)k * geo.Co + n); }
     __device__ __forceinline__ void store(int m, int n, float v) const {
         if (m == 9 * geo.C) atomicAdd(&db[n], v);
         else atomicAdd(&dW[(size_t)m * geo.Co + n], v);
+    }
+    __device__ __forceinline__ void store_row(int m, int c0, const float (&v)[16], int nv) const {
+        add_f32_row(m == 9 * geo.C ? db + c0 : dW + (size_t)m * geo.Co + c0, v, nv);
     }
 };
 
@@ -384,6 +697,9 @@ struct FcWgrad {
         if (m == Kin) atomicAdd(&db[n], v);
         else atomicAdd(&dW[(size_t)m * Nout + n], v);
     }
+    __device__ __forceinline__ void store_row(int m, int c0, const float (&v)[16], int nv) const {
+        add_f32_row(m == Kin ? db + c0 : dW + (size_t)m * Nout + c0, v, nv);
+    }
 };
 
 // second stage of a split-K GEMM whose epilogue is not additive: the partial
@@ -400,16 +716,51 @@ __global__ void splitk_reduce(P p, const float* scratch, int M, int N, int split
 
 // scratch of the split-K forward GEMMs: at most kFwdSplitCtas partial tiles of 64 x 64
 constexpr int kFwdSplitCtas = 2 * 152;
-constexpr size_t kSplitScratchFloats = (size_t)kFwdSplitCtas * BM * BN;
+constexpr size_t kSplitScratchFloats = (size_t)kFwdSplitCtas * 64 * 64;
+
+// The GEMM's shared memory exceeds the default 48 KB, so each problem type's kernel
+// needs the attribute once per device.  Set outside any stream capture: the
+// workspace-size query does it first, and the passes only read the cached verdict.
+template <class P>
+static bool gemm_attr() {
+    return cudaFuncSetAttribute(gemm_tc<P, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, TileCfg<32>::kSmem) ==
+               cudaSuccess &&
+           cudaFuncSetAttribute(gemm_tc<P, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, TileCfg<64>::kSmem) ==
+               cudaSuccess;
+}
+
+static bool gemm_prepared() {
+    static std::atomic<int> cached[64];   // 0 unknown, 1 set, 2 failed
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    int c = cached[dev].load(std::memory_order_relaxed);
+    if (c == 0) {
+        const bool ok = gemm_attr<ConvFwd>() && gemm_attr<FcFwd>() && gemm_attr<ConvDgrad>() && gemm_attr<FcDgrad>() &&
+                        gemm_attr<ConvWgrad>() && gemm_attr<FcWgrad>();
+        (void)cudaGetLastError();
+        c = ok ? 1 : 2;
+        cached[dev].store(c, std::memory_order_relaxed);
+    }
+    return c == 1;
+}
+
+static int tile_n(int N) { return N <= 32 ? 32 : 64; }
 
 template <class P>
 static cudaError_t gemm(const P& p, int M, int N, int K, int splits, cudaStream_t s, float* scratch = nullptr) {
+    if (!gemm_prepared()) return cudaErrorInvalidDeviceFunction;
     if (splits < 1) splits = 1;
-    int kchunk = ((K + splits - 1) / splits + BK - 1) / BK * BK;
-    if (kchunk < BK) kchunk = BK;
+    int kchunk = ((K + splits - 1) / splits + TK - 1) / TK * TK;
+    if (kchunk < TK) kchunk = TK;
     splits = (K + kchunk - 1) / kchunk;
-    dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((N + BN - 1) / BN), (unsigned)splits);
-    gemm_bf16<P><<<grid, GEMM_NT, 0, s>>>(p, M, N, K, kchunk, splits > 1 ? scratch : nullptr);
+    const int tn = tile_n(N);
+    dim3 grid((unsigned)((M + TM - 1) / TM), (unsigned)((N + tn - 1) / tn), (unsigned)splits);
+    float* const sc = splits > 1 ? scratch : nullptr;
+    if (tn == 32) gemm_tc<P, 32><<<grid, GEMM_NT, TileCfg<32>::kSmem, s>>>(p, M, N, K, kchunk, sc);
+    else gemm_tc<P, 64><<<grid, GEMM_NT, TileCfg<64>::kSmem, s>>>(p, M, N, K, kchunk, sc);
     if (splits > 1 && scratch) {
         const size_t MN = (size_t)M * N;
         splitk_reduce<P><<<(unsigned)((MN + 255) / 256 < 1024 ? (MN + 255) / 256 : 1024), 256, 0, s>>>(p, scratch, M, N,
@@ -419,22 +770,26 @@ static cudaError_t gemm(const P& p, int M, int N, int K, int splits, cudaStream_
 }
 
 // split-K factor of a forward GEMM: enough CTAs to cover the GPU when the output
-// tile grid is small, each split at least one 32-wide K-step, partial tiles
+// tile grid is small, each split at least one 64-wide K-slice, partial tiles
 // within the scratch
 static int fwd_splits(int M, int N, int K) {
-    const long long tiles = (long long)((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+    const long long tiles = (long long)((M + TM - 1) / TM) * ((N + tile_n(N) - 1) / tile_n(N));
     if (tiles >= 152) return 1;
     long long s = (152 + tiles - 1) / tiles;
-    const long long ksteps = (K + BK - 1) / BK;
+    const long long ksteps = (K + TK - 1) / TK;
     if (s > ksteps) s = ksteps;
     while (s > 1 && s * M * (long long)N > (long long)kSplitScratchFloats) --s;
     return (int)(s < 1 ? 1 : s);
 }
 
-// split-K factor for a weight-gradient GEMM: about 1024 reduction elements per CTA, at most 512 slices
-static int wgrad_splits(long long K) {
-    long long s = (K + 1023) / 1024;
-    return (int)(s < 1 ? 1 : (s > 512 ? 512 : s));
+// split-K factor for a weight-gradient GEMM (FP32 atomics sum the slices): about four
+// waves of CTAs (four fit an SM), each at least two 64-wide K-slices
+static int wgrad_splits(int M, int N, long long K) {
+    const long long tiles = (long long)((M + TM - 1) / TM) * ((N + tile_n(N) - 1) / tile_n(N));
+    long long s = (4 * 152 + tiles - 1) / tiles;
+    const long long most = (K + 2 * TK - 1) / (2 * TK);
+    if (s > most) s = most;
+    return (int)(s < 1 ? 1 : s);
 }
 
 // ---------------------------------------------------------------- elementwise kernels
@@ -677,7 +1032,17 @@ extern "C" size_t rgbid_net_param_offset(int layer, int what) {
 
 extern "C" size_t rgbid_net_workspace_bytes(int batch) {
     if (batch < 1 || batch > 65536) return 0;
+    (void)gemm_prepared();   // the kernels' attributes, before the passes can be captured
     return ws_layout(batch, nullptr, nullptr);
+}
+
+extern "C" unsigned int rgbid_net_wait_timeouts(void) {
+    unsigned int n = 0;
+    if (cudaDeviceSynchronize() != cudaSuccess || cudaMemcpyFromSymbol(&n, g_mma_timeouts, sizeof(n)) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return (unsigned int)-1;
+    }
+    return n;
 }
 
 extern "C" int rgbid_net_init(float* params, unsigned long long seed, void* stream) {
@@ -756,7 +1121,7 @@ extern "C" int rgbid_net_backward(const float* params, const void* x, int batch,
             const ConvGeo geo = geo_of(l);
             const long long K = (long long)batch * d.hout * d.wout;
             ConvWgrad pw{geo, a_in, gout, dW, db};
-            e = gemm(pw, 9 * d.cin + 1, d.cout, (int)K, wgrad_splits(K), s);
+            e = gemm(pw, 9 * d.cin + 1, d.cout, (int)K, wgrad_splits(9 * d.cin + 1, d.cout, K), s);
             if (e == cudaSuccess && l > 0) {
                 ConvDgrad pd{geo, gout, W, a_in, gin};
                 e = gemm(pd, batch * d.hin * d.win, d.cin, 9 * d.cout, 1, s);
@@ -764,7 +1129,7 @@ extern "C" int rgbid_net_backward(const float* params, const void* x, int batch,
         } else {
             const float* goutf = gout ? nullptr : dy;
             FcWgrad pw{a_in, gout, goutf, dW, db, d.cin, d.cout};
-            e = gemm(pw, d.cin + 1, d.cout, batch, wgrad_splits(batch), s);
+            e = gemm(pw, d.cin + 1, d.cout, batch, wgrad_splits(d.cin + 1, d.cout, batch), s);
             if (e == cudaSuccess && l > 0) {
                 FcDgrad pd{gout, goutf, W, a_in, gin, d.cin, d.cout};
                 e = gemm(pd, batch, d.cin, d.cout, 1, s);

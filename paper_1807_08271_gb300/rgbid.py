@@ -138,6 +138,7 @@ SIGNATURES = [
     ("rgbid_net_param_count", c_size_t, []),
     ("rgbid_net_param_offset", c_size_t, [c_int, c_int]),
     ("rgbid_net_workspace_bytes", c_size_t, [c_int]),
+    ("rgbid_net_wait_timeouts", ctypes.c_uint, []),
     ("rgbid_net_init", c_int, [c_void_p, ctypes.c_ulonglong, c_void_p]),
     ("rgbid_net_inputs", c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p]),
     ("rgbid_net_forward", c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_size_t, c_void_p]),
@@ -461,6 +462,11 @@ def rgbid_net_param_offset(layer: int, what: int) -> int:
 
 def rgbid_net_workspace_bytes(batch: int) -> int:
     return int(lib().rgbid_net_workspace_bytes(batch))
+
+
+def rgbid_net_wait_timeouts() -> int:
+    """Tensor-core waits of the network's GEMMs that ran out on the current device (0 when healthy)."""
+    return int(lib().rgbid_net_wait_timeouts())
 
 
 def rgbid_net_init(params, seed: int, stream=None):

@@ -175,3 +175,8 @@ def test_training_lowers_the_loss_on_labelled_pairs():
     net = InitNet(max_batch=64, seed=2)
     hist = train(net, X, Y, epochs=6, batch=64, lr=1e-3, seed=0, log=lambda m: None)
     assert hist[-1] < hist[0] - 0.5, hist
+
+
+def test_no_tensor_core_wait_ran_out():
+    # every GEMM above waited on its tcgen05 commits; none may have given up
+    assert R.rgbid_net_wait_timeouts() == 0
