@@ -508,6 +508,20 @@ int rgbid_nu_constant_series(double nu_lo, double nu_hi, float* out, int n_out);
  * Errors: INVALID_ARG, CUDA. */
 int rgbid_probe_wait_timeout(long long budget_cycles, int* d_timeouts, void* stream);
 
+/* Diagnostic of the split level kernel's failure detection (the paper has no
+ * counterpart).  The split kernel's roles wait on counters in the workspace's
+ * mailbox; this launches one CTA that clears a mailbox in `d_scratch` (device,
+ * 16-byte aligned, >= 1024 bytes, owned by the caller and not in use by an
+ * alignment) and waits on a counter nothing advances: the first wait runs out of
+ * `budget_cycles` (clock64 cycles, <= 2e10), counts a timeout and raises the
+ * mailbox's error flag; the second wait, with the kernels' full ~2 s budget, must
+ * give up at once because the flag is raised.  Writes 4 ints to d_out (device):
+ * the timeouts counted, the two waits' verdicts (1 = the counter arrived), and the
+ * error flag; then clears the mailbox.  Nothing faults or hangs.
+ * Errors: INVALID_ARG, CUDA. */
+int rgbid_probe_mailbox_timeout(long long budget_cycles, void* d_scratch, size_t scratch_bytes, int* d_out,
+                                void* stream);
+
 /* ---------------------------------------------------------------- fusion
  * Keyframe fusion ("Keyframe fusion", section "RGB-ID SLAM system"): every
  * keyframe pixel with W_kf > 0 is warped into frame k with T_kf_k = kf_T_k

@@ -462,7 +462,8 @@ __device__ __forceinline__ void st_release_u32(unsigned int* p, unsigned int v) 
 // Thread 0 waits until *word >= target; every thread of the CTA gets the verdict
 // through its own shared slot.  A wait that runs out counts a timeout and raises the
 // mailbox's error flag; a raised flag makes every later wait give up at once.
-__device__ __forceinline__ bool cta_wait(AlignState* st, const unsigned int* word, unsigned int target, int* slot) {
+__device__ __forceinline__ bool cta_wait(AlignState* st, const unsigned int* word, unsigned int target, int* slot,
+                                         long long budget = kWaitBudgetCycles) {
     if (threadIdx.x == 0) {
         int ok = 1;
         const long long t0 = clock64();
@@ -471,7 +472,7 @@ __device__ __forceinline__ bool cta_wait(AlignState* st, const unsigned int* wor
                 ok = 0;
                 break;
             }
-            if (clock64() - t0 > kWaitBudgetCycles) {
+            if (clock64() - t0 > budget) {
                 atomicAdd(&st->timeouts, 1);
                 atomicExch(&st->mb.error, 1);
                 ok = 0;
@@ -932,6 +933,32 @@ __global__ void __launch_bounds__(kRobustNT, 1) split_kernel(SplitArgs a) {
     }
 }
 
+// ---------------------------------------------------------------- mailbox wait probe
+// The split kernel's mailbox wait on a counter that nothing advances: the first wait
+// (budget `budget`) runs out, counts a timeout and raises the error flag; the second
+// (the full ~2 s budget) must then give up at once.  out = {timeouts, verdict of the
+// first wait, verdict of the second, error flag}.  The mailbox is left clear.
+__global__ void mailbox_probe_kernel(AlignState* st, long long budget, int* out) {
+    __shared__ int go[2];
+    if (threadIdx.x == 0) {
+        st->timeouts = 0;
+        st->mb.pose_flag = 0u;
+        st->mb.error = 0;
+        __threadfence();
+    }
+    __syncthreads();
+    const bool first = cta_wait(st, &st->mb.pose_flag, 1u, &go[0], budget);
+    const bool second = cta_wait(st, &st->mb.pose_flag, 1u, &go[1]);
+    if (threadIdx.x == 0) {
+        out[0] = st->timeouts;
+        out[1] = first ? 1 : 0;
+        out[2] = second ? 1 : 0;
+        out[3] = ld_relaxed_s32(&st->mb.error);
+        st->mb.error = 0;
+        st->timeouts = 0;
+    }
+}
+
 // ---------------------------------------------------------------- host side
 template <int PREC, int MAXP>
 static cudaError_t level_attributes() {
@@ -1119,3 +1146,15 @@ cudaError_t launch_split(int precision, const SplitArgs& sa, cudaStream_t stream
 }
 
 }  // namespace rgbid
+
+extern "C" int rgbid_probe_mailbox_timeout(long long budget_cycles, void* d_scratch, size_t scratch_bytes, int* d_out,
+                                           void* stream) {
+    static_assert(sizeof(rgbid::AlignState) <= 1024, "probe scratch");
+    if (!d_scratch || !d_out || scratch_bytes < 1024 || budget_cycles < 0 || budget_cycles > 20000000000LL)
+        return RGBID_ERR_INVALID_ARG;
+    if (((uintptr_t)d_scratch & 15u) || ((uintptr_t)d_out & 3u)) return RGBID_ERR_INVALID_ARG;
+    rgbid::mailbox_probe_kernel<<<1, 64, 0, (cudaStream_t)stream>>>(reinterpret_cast<rgbid::AlignState*>(d_scratch),
+                                                                    budget_cycles, d_out);
+    if (cudaGetLastError() != cudaSuccess) return RGBID_ERR_CUDA;
+    return RGBID_OK;
+}

@@ -134,6 +134,7 @@ SIGNATURES = [
     ("rgbid_batch_autotune", c_int, [c_void_p, c_int, c_int, POINTER(AlignParams), c_void_p, c_size_t, c_int,
                                      POINTER(BatchConfig), POINTER(ctypes.c_float), c_void_p]),
     ("rgbid_probe_wait_timeout", c_int, [ctypes.c_longlong, c_void_p, c_void_p]),
+    ("rgbid_probe_mailbox_timeout", c_int, [ctypes.c_longlong, c_void_p, c_size_t, c_void_p, c_void_p]),
     ("rgbid_nu_constant_series", c_int, [c_double, c_double, POINTER(ctypes.c_float), c_int]),
     ("rgbid_net_param_count", c_size_t, []),
     ("rgbid_net_param_offset", c_size_t, [c_int, c_int]),
@@ -446,6 +447,14 @@ def rgbid_probe_wait_timeout(budget_cycles: int, d_timeouts, stream=None):
     """One cluster-reduction round with the partials withheld: every wait runs out (see rgbid.h)."""
     _check("rgbid_probe_wait_timeout", lib().rgbid_probe_wait_timeout(budget_cycles, _ptr(d_timeouts),
                                                                       _stream_ptr(stream)))
+
+
+def rgbid_probe_mailbox_timeout(budget_cycles: int, d_scratch, d_out, stream=None):
+    """The split level kernel's mailbox wait on a counter nothing advances (see rgbid.h):
+    d_out (4 device ints) gets the timeouts, both waits' verdicts and the error flag."""
+    _check("rgbid_probe_mailbox_timeout",
+           lib().rgbid_probe_mailbox_timeout(budget_cycles, _ptr(d_scratch), d_scratch.numel() * d_scratch.element_size(),
+                                             _ptr(d_out), _stream_ptr(stream)))
 
 
 NET_IN_H, NET_IN_W, NET_IN_C, NET_OUT, NET_LAYERS = 60, 80, 4, 7, 6

@@ -280,6 +280,11 @@ def test_misaligned_and_nonfinite_arguments_are_rejected_on_the_host(binding):
     # the wait-timeout probe's own arguments
     assert L.rgbid_probe_wait_timeout(-1, f[0], None) == b.ERR_INVALID_ARG
     assert L.rgbid_probe_wait_timeout(1000, None, None) == b.ERR_INVALID_ARG
+    # ... and the mailbox probe's (scratch too small, misaligned, NULL output, bad budget)
+    assert L.rgbid_probe_mailbox_timeout(1000, f[0], 512, f[0], None) == b.ERR_INVALID_ARG
+    assert L.rgbid_probe_mailbox_timeout(1000, V(base + 4), 1024, f[0], None) == b.ERR_INVALID_ARG
+    assert L.rgbid_probe_mailbox_timeout(1000, f[0], 1024, None, None) == b.ERR_INVALID_ARG
+    assert L.rgbid_probe_mailbox_timeout(-1, f[0], 1024, f[0], None) == b.ERR_INVALID_ARG
 
 
 def test_nu_constant_series_matches_digamma(binding):

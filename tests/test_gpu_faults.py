@@ -163,3 +163,33 @@ def test_a_wait_with_nothing_to_wait_for_runs_out_and_reports():
     torch.cuda.synchronize()
     g = R.parse_result(res)
     assert g["status"] == R.OK and g["iters_done"] == 20
+
+
+def test_a_mailbox_wait_with_nothing_to_wait_for_gives_up_and_raises_the_flag():
+    # the split level kernel's roles wait on workspace counters; a wait that runs out
+    # raises the error flag and every later wait of the launch gives up at once
+    import time
+    scratch = torch.zeros(256, dtype=torch.int32, device="cuda")
+    out = torch.full((4,), -1, dtype=torch.int32, device="cuda")
+    t0 = time.perf_counter()
+    R.rgbid_probe_mailbox_timeout(200_000, scratch, out)     # ~0.1 ms at 2 GHz
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    # (timeouts, first wait, second wait, error flag): the second wait did not spend its ~2 s budget
+    assert tuple(int(v) for v in out.cpu()) == (1, 0, 0, 1)
+    assert dt < 1.0
+    assert int(scratch.abs().sum()) == 0                     # the mailbox is left clear
+    out.fill_(-1)
+    R.rgbid_probe_mailbox_timeout(0, scratch, out)
+    torch.cuda.synchronize()
+    assert tuple(int(v) for v in out.cpu()) == (1, 0, 0, 1)
+    # the context is still usable: a 640x480 alignment, whose two finest levels run in
+    # the split kernel, completes every iteration
+    pair = synth.make_pair(3, width=640, height=480)
+    PA, PB = _pyr(pair["I_A"], pair["W_A"], pair["K"], 4), _pyr(pair["I_B"], pair["W_B"], pair["K"], 4)
+    p = R.rgbid_default_params(levels=4, iters=[5, 5, 5, 10])
+    res = R.result_tensor()
+    R.rgbid_align(PA.desc, PB.desc, None, p, R.new_workspace(PA.desc, p), res)
+    torch.cuda.synchronize()
+    g = R.parse_result(res)
+    assert g["status"] == R.OK and g["iters_done"] == 25
