@@ -69,10 +69,10 @@ def alu_roofline(kernel: str, units_per_launch: float, ms_per_launch: float) -> 
 # DRAM bytes (read + write) per unit (level pixel for the sweep, sample pixel for
 # the robust-scale kernel, level pixel x iteration for the level kernel) from one ncu
 # capture of each kernel on this workload (the sweep and robust-scale kernels at
-# level 0, the level kernel's two launches of a frame; cold caches); set to None
-# whenever those kernels change.
+# level 0, the level kernel's 80x60 launch, the one it gets in a frame; cold caches);
+# set to None whenever those kernels change.
 TRAFFIC_PER_UNIT = {"robust_kernel": None, "sweep_kernel": 4847616 / 307200,
-                    "level_kernel": (166912 + 511232) / (4800 * 10 + 19200 * 5), "split_kernel": None}
+                    "level_kernel": 166912 / (4800 * 10), "split_kernel": None}
 
 
 # ----------------------------------------------------------------------------- ranks

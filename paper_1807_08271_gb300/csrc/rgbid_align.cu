@@ -980,15 +980,26 @@ static RobustArgs robust_args(const rgbid_pyramid* ref, const rgbid_pyramid* cur
     return ra;
 }
 
-// A level whose systematic sample is every pixel runs in the persistent level kernel.
+// A small level whose systematic sample is every pixel runs in the persistent level
+// kernel.  Above two pixels per thread of its cluster (80x60 takes it, 160x120 does
+// not) the split kernel is faster: its helpers take the pixel pass with the Jacobians
+// off the cluster's chain (measured on the 640x480 sequence: 160x120 at 24.5 us per
+// iteration in the split kernel against 28.4 us in the level kernel, 80x60 the other
+// way round), so the level kernel keeps such a level only where the split kernel
+// cannot take it.
+constexpr long long kLevelKernelPreferredPixels = (long long)kLevelCL * kRobustNT * 2;
+
 static bool use_level_kernel(const rgbid_pyramid* ref, const rgbid_align_params* p, int l) {
     if (p->no_level_kernel || p->warp_mode != RGBID_WARP_PER_LEVEL) return false;
     const rgbid_level& L = ref->lv[l];
+    if ((long long)L.width * L.height > kLevelKernelPreferredPixels &&
+        split_kernel_takes(ref->precision, L.width, L.height))
+        return false;
     return level_kernel_takes(ref->precision, L.width, L.height, p->sample_cap);
 }
 
-// A level whose sample is a strict subset of its pixels runs in the split kernel when
-// its tiles fit the helper CTAs.
+// Any other level runs in the split kernel when its tiles fit the helper CTAs (its
+// sample may be every pixel too).
 static bool use_split_kernel(const rgbid_pyramid* ref, const rgbid_align_params* p, int l) {
     if (p->no_level_kernel || p->warp_mode != RGBID_WARP_PER_LEVEL) return false;
     const rgbid_level& L = ref->lv[l];

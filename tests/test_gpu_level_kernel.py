@@ -57,7 +57,7 @@ def _both_paths(pair, levels, iters, precision=R.PLANES_F32, T_init=None):
 @pytest.mark.parametrize("precision", [R.PLANES_F32, R.PLANES_BF16_F16])
 def test_level_kernel_matches_the_per_iteration_kernels_and_the_oracle(pair640, precision):
     a, b, (PA, _, pa, pb) = _both_paths(pair640, 4, (5, 5, 5, 10), precision)
-    # two level-kernel launches (80x60, 160x120) and two split launches (320x240,
+    # one level-kernel launch (80x60) and three split launches (160x120, 320x240,
     # 640x480) replace 2 x 25 per-iteration launches
     assert R.rgbid_align_launches(PA.desc, pa) == 2 + 4
     assert R.rgbid_align_launches(PA.desc, pb) == 2 + 2 * 25
@@ -76,13 +76,19 @@ def test_level_kernel_matches_the_per_iteration_kernels_and_the_oracle(pair640, 
 
 
 @pytest.mark.parametrize("seed", [0, 6])
-def test_every_level_in_the_level_kernel(seed):
-    """160x120: every level's sample is every pixel, so the whole alignment is three
-    level-kernel launches and the closing launch."""
+def test_every_level_in_one_launch(seed):
+    """160x120: every level's sample is every pixel; the finest level runs in the split
+    kernel (its sample at stride 1), the two coarser in the level kernel, then the
+    closing launch."""
     pair = synth.make_pair(seed)
     T0 = O.se3_exp([0.004, -0.003, 0.002, 0.01, -0.006, 0.003])
-    a, b, (PA, _, pa, _) = _both_paths(pair, 3, (5, 5, 10), T_init=T0)
+    a, b, (PA, PB, pa, _) = _both_paths(pair, 3, (5, 5, 10), T_init=T0)
     assert R.rgbid_align_launches(PA.desc, pa) == 2 + 3
+    lvl, spl = R.KernelTimer(R.KERNEL_LEVEL, 8), R.KernelTimer(R.KERNEL_SPLIT, 8)
+    _align(PA, PB, 3, (5, 5, 10), True, T_init=T0, timer=lvl)
+    _align(PA, PB, 3, (5, 5, 10), True, T_init=T0, timer=spl)
+    assert (lvl.t.count, spl.t.count) == (2, 1)
+    assert spl.t.units == 160 * 120 * 5
     er, et = pose_error(a["T"], b["T"])
     assert er <= PATHS_TOL and et <= PATHS_TOL, (er, et)
     A, B = oracle_pair(pair, 3)
@@ -116,13 +122,13 @@ def test_level_kernel_timing_counts_its_launches_and_units(pair640):
     (PA, _, _), (PB, _, _) = gpu_pair(pair640, 4)
     timer = R.KernelTimer(R.KERNEL_LEVEL, 8)
     _align(PA, PB, 4, (5, 5, 5, 10), True, timer=timer)
-    assert timer.t.count == 2
-    assert timer.t.units == 160 * 120 * 5 + 80 * 60 * 10
+    assert timer.t.count == 1
+    assert timer.t.units == 80 * 60 * 10
     assert timer.total_ms() > 0.0
     split = R.KernelTimer(R.KERNEL_SPLIT, 8)
     _align(PA, PB, 4, (5, 5, 5, 10), True, timer=split)
-    assert split.t.count == 2
-    assert split.t.units == 640 * 480 * 5 + 320 * 240 * 5
+    assert split.t.count == 3
+    assert split.t.units == 640 * 480 * 5 + 320 * 240 * 5 + 160 * 120 * 5
     assert split.total_ms() > 0.0
 
 
