@@ -340,6 +340,60 @@ struct ClusterSum {
         return receive<NV>(t);
     }
 
+    // The same round by loads instead of pushes: every CTA leaves its partial of value
+    // t < NSEND in its own receive buffer, one hardware cluster barrier (arrive.release /
+    // wait.acquire) publishes them, and each reader (every CTA, or CTA 0 alone with ROOT)
+    // reads the CL partials of each value with ld.shared::cluster and sums them in the
+    // same pairwise tree, so the totals equal the pushed round's bit for bit.  Faster
+    // than the push for wide rounds (a 16-CTA probe: 1.32 against 1.83 us for 96 values,
+    // slower for 4-6), so only the Chebyshev round uses it.  Every CTA still completes its
+    // mbarrier's phase of the round (an arrival with no bytes), so the phases of the
+    // pushed rounds keep counting.  A CTA overwrites its own partial of this parity only
+    // two rounds later, after every reader has finished this round.
+    template <int NV, int NSEND, bool ROOT>
+    __device__ __forceinline__ void run_by_loads(float (&v)[NV]) {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        static_assert(NV % 32 == 0 && NSEND <= NV && NSEND <= kRobustMaxNV, "chunks of 32");
+#pragma unroll
+        for (int c = 0; c < NV / 32; ++c) {
+            float chunk[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) chunk[i] = v[c * 32 + i];
+            red_w[warp][c * 32 + lane] = warp_reduce_scatter32(chunk);
+        }
+        __syncthreads();
+        const int t = threadIdx.x, par = round & 1;
+        if (t < NSEND) {
+            const F2 p = warp_tree<kRobustNT / 32>(red_w, t);
+            recv[par][rank][t] = make_float2(p.hi, p.lo);
+        }
+        if (t == 0) mbar_arrive(&mbar[par]);
+        asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+        asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+        if ((!ROOT || rank == 0) && t < NSEND) {
+            const uint32_t a = smem_addr(&recv[par][0][t]);
+            F2 acc[CL];
+#pragma unroll
+            for (int r = 0; r < CL; ++r) {
+                float2 q;
+                // source r's partial sits at [par][r][t] of CTA r's own buffer
+                asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];"
+                             : "=f"(q.x), "=f"(q.y)
+                             : "r"(map_to_rank(a + (uint32_t)(r * kRobustMaxNV * sizeof(float2)), (uint32_t)r))
+                             : "memory");
+                acc[r] = F2{q.x, q.y};
+            }
+#pragma unroll
+            for (int step = 1; step < CL; step <<= 1)
+#pragma unroll
+                for (int r = 0; r < CL; ++r)
+                    if (r % (2 * step) == 0 && r + step < CL) acc[r].add(acc[r + step]);
+            out[t] = acc[0].value();
+        }
+        __syncthreads();
+        next();
+    }
+
     // Block reduction of per-thread partials v[0..NV) (NV <= 8: one warp sum each;
     // a multiple of 32: reduce-scatter chunks) into per-warp partials, summed over the
     // warps in a fixed pairwise tree; then values t < NSEND go through the cluster: to

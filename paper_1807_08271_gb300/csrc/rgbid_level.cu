@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(kRobustNT, 1) level_kernel(LevelArgs a) {
             }
 #pragma unroll
             for (int i = 2 * kChebVals; i < 96; ++i) v[i] = 0.f;
-            R.template run<96, 2 * kChebVals, false>(v);
+            R.template run_by_loads<96, 2 * kChebVals, false>(v);
             if (tid < 64) {
                 // warp c solves channel c, in every CTA on the same totals
                 const int c = tid >> 5;
@@ -485,6 +485,8 @@ __device__ __forceinline__ bool cta_wait(AlignState* st, const unsigned int* wor
     return *slot != 0;
 }
 
+static_assert((offsetof(AlignState, mb) + offsetof(SplitMailbox, wp)) % 16 == 0, "the pose is published as float4");
+
 constexpr int kSampleTerms = 13;   // a sample's cached keyframe-side stage: 5 taps (10), a, b, interior
 
 template <int PREC>
@@ -500,7 +502,7 @@ __global__ void __launch_bounds__(kRobustNT, 1) split_kernel(SplitArgs a) {
     __shared__ float2 recv[2][CL][kRobustMaxNV];
     __shared__ float tot[kRobustMaxNV];
     __shared__ __align__(8) unsigned long long mbar[2];
-    __shared__ WarpPose sh_wp;
+    __shared__ __align__(16) WarpPose sh_wp;
     __shared__ RobustParams sh_rob;
     __shared__ double T_sh[16];
     __shared__ float nu_out[2];
@@ -579,35 +581,36 @@ __global__ void __launch_bounds__(kRobustNT, 1) split_kernel(SplitArgs a) {
             if (it > 0 && !cta_wait(st, &mb->arrived, (unsigned)a.n_helpers * (unsigned)it, &go[0])) break;
             const unsigned int nb = it == 0 ? nb0 : (unsigned)a.n_helpers;
             if (nb) {
+                // every CTA of the cluster sums all nb partials itself in one fixed order
+                // (warp w takes partials w, w + 8, ...; then the warps' sums in a fixed
+                // tree), so every CTA holds bit-identical totals without an exchange round
                 F2 acc{0.f, 0.f};
-                constexpr unsigned kStride = (unsigned)CL * NW;
-                for (unsigned int b0 = (unsigned)rank + (unsigned)CL * (unsigned)warp; b0 < nb; b0 += 4u * kStride) {
-                    float2 v[4];
+                constexpr int Q = 12;                // loads in flight per lane (96 helpers: one batch)
+                for (unsigned int b0 = (unsigned)warp; b0 < nb; b0 += (unsigned)(Q * NW)) {
+                    float2 v[Q];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const unsigned int b = b0 + (unsigned)q * kStride;
+                    for (int q = 0; q < Q; ++q) {
+                        const unsigned int b = b0 + (unsigned)(q * NW);
                         v[q] = b < nb ? __ldcg(a.partials + (size_t)b * kSlots + lane) : make_float2(0.f, 0.f);
                     }
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) acc.add(F2{v[q].x, v[q].y});
+                    for (int q = 0; q < Q; ++q) acc.add(F2{v[q].x, v[q].y});
                 }
                 fin2[warp][lane] = acc;
                 __syncthreads();
-                if (tid < kSlots) tot[tid] = R.template exchange<kSlots>(tid, warp_tree<NW>(fin2, tid)).value();
+                if (tid < kSlots) tot[tid] = warp_tree<NW>(fin2, tid).value();
                 __syncthreads();
-                R.next();
                 if (warp == 0)
                     level_solve_update<PREC>(tot, a.min_valid, T_sh, &sh_wp, xi_f, d_f, rho_d, xi_d, &ok_flag, sh_cnt);
                 __syncthreads();
             }
-            // ---- publish this iteration's pose to the helpers
-            if (rank == 0 && warp == 0) {
-                if (lane < 16) {
-                    __stcg(reinterpret_cast<float*>(&mb->wp) + lane, reinterpret_cast<const float*>(&sh_wp)[lane]);
-                    __threadfence();
-                }
-                __syncwarp();
-                if (lane == 0) st_release_u32(&mb->pose_flag, (unsigned)it + 1u);
+            // ---- publish this iteration's pose to the helpers: one thread stores the pose
+            //      and then releases the flag, so the release orders the pose before it
+            if (rank == 0 && tid == 0) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    __stcg(reinterpret_cast<float4*>(&mb->wp) + q, reinterpret_cast<const float4*>(&sh_wp)[q]);
+                st_release_u32(&mb->pose_flag, (unsigned)it + 1u);
             }
             const WarpPose wp = sh_wp;
 
@@ -791,7 +794,7 @@ __global__ void __launch_bounds__(kRobustNT, 1) split_kernel(SplitArgs a) {
 #pragma unroll
                     for (int q = 0; q < (int)(sizeof(RobustParams) / 4); ++q)
                         __stcg(reinterpret_cast<int*>(&mb->rob) + q, src[q]);
-                    __threadfence();
+                    // the same thread releases the flag: the release orders the stores above
                     st_release_u32(&mb->rob_flag, (unsigned)it + 1u);
                 }
             }
