@@ -508,6 +508,15 @@ int rgbid_nu_constant_series(double nu_lo, double nu_hi, float* out, int n_out);
  * Errors: INVALID_ARG, CUDA. */
 int rgbid_probe_wait_timeout(long long budget_cycles, int* d_timeouts, void* stream);
 
+/* Diagnostic of the bounds-checked test build (the paper has no counterpart): a
+ * library compiled with -DRGBID_BOUNDS_CHECK checks every index it gathers from an
+ * image plane (level planes, frames, keyframes, the filtered plane) against the
+ * plane's allocation, counts an index outside it and reads element 0 instead.  Writes
+ * the count since the library was loaded, over every kernel, to *count (host) after a
+ * device synchronisation.  The product build does not check: it writes 0 and returns
+ * RGBID_ERR_UNSUPPORTED.  Errors: INVALID_ARG (NULL count), CUDA. */
+int rgbid_debug_bounds_violations(unsigned long long* count);
+
 /* Diagnostic of the split level kernel's failure detection (the paper has no
  * counterpart).  The split kernel's roles wait on counters in the workspace's
  * mailbox; this launches one CTA that clears a mailbox in `d_scratch` (device,

@@ -1059,6 +1059,38 @@ static LevelArgs level_args(const rgbid_pyramid* ref, const rgbid_pyramid* cur, 
 
 using namespace rgbid;
 
+namespace rgbid {
+unsigned int oob_count_level();
+unsigned int oob_count_batch_f32();
+unsigned int oob_count_batch_bf16();
+unsigned int oob_count_covariance();
+unsigned int oob_count_fuse();
+unsigned int oob_count_pyramid();
+}  // namespace rgbid
+
+extern "C" int rgbid_debug_bounds_violations(unsigned long long* count) {
+    if (!count) return RGBID_ERR_INVALID_ARG;
+#ifdef RGBID_BOUNDS_CHECK
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        (void)cudaGetLastError();
+        return RGBID_ERR_CUDA;
+    }
+    const unsigned int c[7] = {oob_count_this_unit(), rgbid::oob_count_level(), rgbid::oob_count_batch_f32(),
+                               rgbid::oob_count_batch_bf16(), rgbid::oob_count_covariance(), rgbid::oob_count_fuse(),
+                               rgbid::oob_count_pyramid()};
+    unsigned long long n = 0;
+    for (unsigned int v : c) {
+        if (v == ~0u) return RGBID_ERR_CUDA;
+        n += v;
+    }
+    *count = n;
+    return RGBID_OK;
+#else
+    *count = 0;
+    return RGBID_ERR_UNSUPPORTED;
+#endif
+}
+
 extern "C" size_t rgbid_align_workspace_bytes(const rgbid_pyramid* ref, const rgbid_align_params* params) {
     if (!ref || ref->levels < 1 || ref->levels > RGBID_MAX_LEVELS) return 0;
     return workspace_bytes_for(*ref, params && params->warp_mode == RGBID_WARP_FULL_RESOLUTION);

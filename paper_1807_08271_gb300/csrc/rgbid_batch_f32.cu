@@ -5,3 +5,8 @@
 namespace rgbid {
 template cudaError_t batch_dispatch<RGBID_PLANES_F32>(int, int, const BatchArgs*, int, int*, cudaStream_t);
 }  // namespace rgbid
+
+namespace rgbid {
+// out-of-plane gathers counted by this translation unit's kernels (bounds-checked builds)
+unsigned int oob_count_batch_f32() { return oob_count_this_unit(); }
+}  // namespace rgbid

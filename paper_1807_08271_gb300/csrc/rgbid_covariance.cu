@@ -55,7 +55,8 @@ __global__ void __launch_bounds__(kBilTW * kBilTH) bilateral_kernel(BilateralArg
         const int ty = i / tw, tx = i - ty * tw;
         const int u = u0 + tx, v = v0 + ty;
         float2 q = make_float2(0.f, 0.f);
-        if (u >= 0 && v >= 0 && u < a.w && v < a.h) q = Pix<PREC>::load(a.IW, v * a.pitch + u);
+        if (u >= 0 && v >= 0 && u < a.w && v < a.h)
+            q = Pix<PREC>::load(a.IW, (int)in_plane(v * a.pitch + u, (long long)a.pitch * a.h));
         tile[ty][tx] = q;
     }
     for (int i = t; i < (2 * R + 1) * (2 * R + 1); i += kBilTW * kBilTH) {
@@ -207,3 +208,8 @@ extern "C" int rgbid_covariance(const rgbid_pyramid* ref, const rgbid_pyramid* c
     cov_inverse_kernel<<<1, 32, 0, stream>>>(d_result, d_sigma, p.min_valid);
     return cudaGetLastError() == cudaSuccess ? RGBID_OK : RGBID_ERR_CUDA;
 }
+
+namespace rgbid {
+// out-of-plane gathers counted by this translation unit's kernels (bounds-checked builds)
+unsigned int oob_count_covariance() { return oob_count_this_unit(); }
+}  // namespace rgbid

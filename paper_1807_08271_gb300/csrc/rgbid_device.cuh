@@ -108,6 +108,48 @@ struct Pix<RGBID_PLANES_BF16_F16> {
     }
 };
 
+// ---------------------------------------------------------------- bounds-checked builds
+// Built with -DRGBID_BOUNDS_CHECK (build(checked=True): librgbid_checked.so), every
+// index gathered from an image plane is checked against the plane's allocation (rows x
+// pitch elements).  An index outside it is counted in this translation unit's counter
+// and replaced by element 0, so the kernel goes on without touching memory outside the
+// plane; rgbid_debug_bounds_violations adds up the counters.  This stands in for a
+// memory checker the GPUs do not offer here.  Without the macro the check compiles away.
+#ifdef RGBID_BOUNDS_CHECK
+static __device__ unsigned int g_oob_count;
+#endif
+
+__device__ __forceinline__ long long in_plane(long long idx, long long n) {
+#ifdef RGBID_BOUNDS_CHECK
+    if (idx < 0 || idx >= n) {
+        atomicAdd(&g_oob_count, 1u);
+        return 0;
+    }
+#endif
+    return idx;
+}
+
+// pixel idx of a level's interleaved (I, W) plane
+template <int PREC>
+__device__ __forceinline__ float2 pix(const LevelDev& L, int idx) {
+    return Pix<PREC>::load(L.IW, (int)in_plane(idx, (long long)L.pitch * L.h));
+}
+
+// This translation unit's count of out-of-plane indices since the library was loaded
+// (0 in a build without the check; (unsigned)-1 if it cannot be read).
+static inline unsigned int oob_count_this_unit() {
+#ifdef RGBID_BOUNDS_CHECK
+    unsigned int n = 0;
+    if (cudaMemcpyFromSymbol(&n, g_oob_count, sizeof(n)) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return ~0u;
+    }
+    return n;
+#else
+    return 0u;
+#endif
+}
+
 // ---------------------------------------------------------------- per-pixel terms
 struct PixelTerms {
     float rI, rW;        // residuals r(p, 0)
@@ -144,11 +186,11 @@ __device__ __forceinline__ void stage_a(const LevelDev& A, int u, int v, PxA& s)
     s.ok = !(u < 1 || v < 1 || u > A.w - 2 || v > A.h - 2);     // no central gradient on the border
     if (!s.ok) return;
     const int idx = v * A.pitch + u;
-    s.c = Pix<PREC>::load(A.IW, idx);
-    s.nl = Pix<PREC>::load(A.IW, idx - 1);
-    s.nr = Pix<PREC>::load(A.IW, idx + 1);
-    s.nu = Pix<PREC>::load(A.IW, idx - A.pitch);
-    s.nd = Pix<PREC>::load(A.IW, idx + A.pitch);
+    s.c = pix<PREC>(A, idx);
+    s.nl = pix<PREC>(A, idx - 1);
+    s.nr = pix<PREC>(A, idx + 1);
+    s.nu = pix<PREC>(A, idx - A.pitch);
+    s.nd = pix<PREC>(A, idx + A.pitch);
     s.a = ((float)u - A.cx) * A.ifx;
     s.b = ((float)v - A.cy) * A.ify;
 }
@@ -178,11 +220,12 @@ __device__ __forceinline__ void stage_a_grad(const LevelDev& A, const float2* G,
     s.ok = !(u < 1 || v < 1 || u > A.w - 2 || v > A.h - 2);
     if (!s.ok) return;
     const int idx = v * A.pitch + u;
-    s.c = Pix<PREC>::load(A.IW, idx);
-    s.nl = __ldg(G + idx - 1);
-    s.nr = __ldg(G + idx + 1);
-    s.nu = __ldg(G + idx - A.pitch);
-    s.nd = __ldg(G + idx + A.pitch);
+    const long long n = (long long)A.pitch * A.h;
+    s.c = pix<PREC>(A, idx);
+    s.nl = __ldg(G + in_plane(idx - 1, n));
+    s.nr = __ldg(G + in_plane(idx + 1, n));
+    s.nu = __ldg(G + in_plane(idx - A.pitch, n));
+    s.nd = __ldg(G + in_plane(idx + A.pitch, n));
     s.a = ((float)u - A.cx) * A.ifx;
     s.b = ((float)v - A.cy) * A.ify;
 }
@@ -215,10 +258,10 @@ __device__ __forceinline__ void stage_w(const LevelDev& A, const LevelDev& B, co
 template <int PREC>
 __device__ __forceinline__ void stage_b(const LevelDev& B, const PxW& w, PxB& t) {
     if (!w.ok) return;
-    t.t00 = Pix<PREC>::load(B.IW, w.bi);
-    t.t10 = Pix<PREC>::load(B.IW, w.bi + 1);
-    t.t01 = Pix<PREC>::load(B.IW, w.bi + B.pitch);
-    t.t11 = Pix<PREC>::load(B.IW, w.bi + B.pitch + 1);
+    t.t00 = pix<PREC>(B, w.bi);
+    t.t10 = pix<PREC>(B, w.bi + 1);
+    t.t01 = pix<PREC>(B, w.bi + B.pitch);
+    t.t11 = pix<PREC>(B, w.bi + B.pitch + 1);
 }
 
 // Jacobians (eq. DeltaX with the gradient terms of eqs. res_int / res_depth) and
@@ -337,7 +380,7 @@ __device__ __forceinline__ Warped warp_leaf(const LevelDev& A0, const LevelDev& 
     Warped r{0.f, 0.f, false, false};
     PxA s;
     s.ok = true;
-    s.c = Pix<PREC>::load(A0.IW, v0 * A0.pitch + u0);
+    s.c = pix<PREC>(A0, v0 * A0.pitch + u0);
     s.a = ((float)u0 - A0.cx) * A0.ifx;
     s.b = ((float)v0 - A0.cy) * A0.ify;
     PxW w;

@@ -95,11 +95,14 @@ __global__ void __launch_bounds__(256) fuse_kernel(FuseArgs a) {
     if (x0 < 0 || y0 < 0 || x0 > a.w - 2 || y0 > a.h - 2) return;
     const float ax = du - fdu, ay = dv - fdv;
     const size_t bi = (size_t)y0 * a.pitch_k + x0;
-    const float w00 = __ldg(a.W_k + bi), w10 = __ldg(a.W_k + bi + 1);
-    const float w01 = __ldg(a.W_k + bi + a.pitch_k), w11 = __ldg(a.W_k + bi + a.pitch_k + 1);
+    const long long nk = (long long)a.pitch_k * a.h;
+    const long long b00 = in_plane((long long)bi, nk), b10 = in_plane((long long)bi + 1, nk);
+    const long long b01 = in_plane((long long)bi + a.pitch_k, nk), b11 = in_plane((long long)bi + a.pitch_k + 1, nk);
+    const float w00 = __ldg(a.W_k + b00), w10 = __ldg(a.W_k + b10);
+    const float w01 = __ldg(a.W_k + b01), w11 = __ldg(a.W_k + b11);
     if (!(w00 > 0.f && w10 > 0.f && w01 > 0.f && w11 > 0.f)) return;
-    const float i00 = __ldg(a.I_k + bi), i10 = __ldg(a.I_k + bi + 1);
-    const float i01 = __ldg(a.I_k + bi + a.pitch_k), i11 = __ldg(a.I_k + bi + a.pitch_k + 1);
+    const float i00 = __ldg(a.I_k + b00), i10 = __ldg(a.I_k + b10);
+    const float i01 = __ldg(a.I_k + b01), i11 = __ldg(a.I_k + b11);
     // a tap is a measurement only if both of its values are finite (w > 0 is checked above)
     if (!(isfinite(w00) && isfinite(w10) && isfinite(w01) && isfinite(w11) && isfinite(i00) && isfinite(i10) &&
           isfinite(i01) && isfinite(i11)))
@@ -273,7 +276,8 @@ __global__ void __launch_bounds__(256) covisibility_kernel(CovisArgs a) {
     const int ps = a.pitch[dir], pd = a.pitch[dir ^ 1];
     bool valid = false, visible = false;
     if (u < a.w && v < a.h) {
-        const float Ws_ = __ldg(Ws + (size_t)v * ps + u), Is_ = __ldg(Is + (size_t)v * ps + u);
+        const long long os = in_plane((long long)v * ps + u, (long long)ps * a.h);
+        const float Ws_ = __ldg(Ws + os), Is_ = __ldg(Is + os);
         valid = Ws_ > 0.f && isfinite(Ws_) && isfinite(Is_);
         if (valid) {
             const WarpPose& wp = sh_wp;
@@ -291,7 +295,8 @@ __global__ void __launch_bounds__(256) covisibility_kernel(CovisArgs a) {
                 if (fabsf(ru) < 1.0e7f && fabsf(rv) < 1.0e7f) {
                     const int xn = u + (int)ru, yn = v + (int)rv;
                     if (xn >= 0 && yn >= 0 && xn < a.w && yn < a.h) {
-                        const float Wn = __ldg(Wd + (size_t)yn * pd + xn), In = __ldg(Id + (size_t)yn * pd + xn);
+                        const long long od = in_plane((long long)yn * pd + xn, (long long)pd * a.h);
+                        const float Wn = __ldg(Wd + od), In = __ldg(Id + od);
                         visible = Wn > 0.f && isfinite(Wn) && isfinite(In) && fabsf(Wn - Ws_ * imz) < sh_gate;
                     }
                 }
@@ -513,3 +518,8 @@ extern "C" void rgbid_default_params(rgbid_align_params* p) {
     p->nu_lo = 2.0;
     p->nu_hi = 10.0;
 }
+
+namespace rgbid {
+// out-of-plane gathers counted by this translation unit's kernels (bounds-checked builds)
+unsigned int oob_count_fuse() { return oob_count_this_unit(); }
+}  // namespace rgbid

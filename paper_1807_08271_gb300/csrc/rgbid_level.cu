@@ -1161,3 +1161,8 @@ extern "C" int rgbid_probe_mailbox_timeout(long long budget_cycles, void* d_scra
     if (cudaGetLastError() != cudaSuccess) return RGBID_ERR_CUDA;
     return RGBID_OK;
 }
+
+namespace rgbid {
+// out-of-plane gathers counted by this translation unit's kernels (bounds-checked builds)
+unsigned int oob_count_level() { return oob_count_this_unit(); }
+}  // namespace rgbid

@@ -19,7 +19,7 @@ namespace rgbid {
 struct PyrSrc {
     const float* I;
     const float* W;
-    int pitch;
+    int pitch, rows;
 };
 
 struct IWf {
@@ -53,7 +53,7 @@ struct Down {
 template <>
 struct Down<0> {
     static __device__ __forceinline__ IWf at(const PyrSrc& s, int x, int y) {
-        const size_t o = (size_t)y * s.pitch + x;
+        const long long o = in_plane((long long)y * s.pitch + x, (long long)s.pitch * s.rows);
         const float i = __ldg(s.I + o), w = __ldg(s.W + o);
         const bool fi = isfinite(i);
         IWf r;
@@ -167,7 +167,7 @@ extern "C" int rgbid_build_pyramid(const float* I0, const float* W0, int pitch0,
     P.precision = precision;
     PyrAll all;
     memset(&all, 0, sizeof(all));
-    all.src = PyrSrc{I0, W0, pitch0};
+    all.src = PyrSrc{I0, W0, pitch0, height};
     all.levels = levels;
     char* base = (char*)storage;
     int w = width, h = height;
@@ -200,3 +200,8 @@ extern "C" int rgbid_build_pyramid(const float* I0, const float* W0, int pitch0,
     *out = P;
     return RGBID_OK;
 }
+
+namespace rgbid {
+// out-of-plane gathers counted by this translation unit's kernels (bounds-checked builds)
+unsigned int oob_count_pyramid() { return oob_count_this_unit(); }
+}  // namespace rgbid

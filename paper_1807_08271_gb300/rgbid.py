@@ -9,6 +9,7 @@ fallback: if the library cannot be built or loaded, every call raises.
 from __future__ import annotations
 
 import ctypes
+import os
 import threading
 from ctypes import POINTER, Structure, c_char_p, c_double, c_int, c_size_t, c_uint8, c_void_p
 
@@ -140,6 +141,7 @@ SIGNATURES = [
     ("rgbid_net_param_offset", c_size_t, [c_int, c_int]),
     ("rgbid_net_workspace_bytes", c_size_t, [c_int]),
     ("rgbid_net_wait_timeouts", ctypes.c_uint, []),
+    ("rgbid_debug_bounds_violations", c_int, [POINTER(ctypes.c_ulonglong)]),
     ("rgbid_net_init", c_int, [c_void_p, ctypes.c_ulonglong, c_void_p]),
     ("rgbid_net_inputs", c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p]),
     ("rgbid_net_forward", c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_size_t, c_void_p]),
@@ -159,11 +161,12 @@ class RgbidError(RuntimeError):
 
 
 def lib():
-    """Load (building first if needed) the in-tree librgbid.so."""
+    """Load (building first if needed) the in-tree librgbid.so, or with the environment
+    variable RGBID_LIBRARY=checked the bounds-checked test build librgbid_checked.so."""
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.build()
+            path = _build.build(checked=os.environ.get("RGBID_LIBRARY") == "checked")
             L = ctypes.CDLL(path)
             for name, res, args in SIGNATURES:
                 f = getattr(L, name)
@@ -471,6 +474,17 @@ def rgbid_net_param_offset(layer: int, what: int) -> int:
 
 def rgbid_net_workspace_bytes(batch: int) -> int:
     return int(lib().rgbid_net_workspace_bytes(batch))
+
+
+def rgbid_debug_bounds_violations() -> int | None:
+    """Out-of-plane gather indices counted since the library was loaded (the
+    bounds-checked build); None for the product library, which does not check."""
+    n = ctypes.c_ulonglong(0)
+    rc = lib().rgbid_debug_bounds_violations(ctypes.byref(n))
+    if rc == ERR_UNSUPPORTED:
+        return None
+    _check("rgbid_debug_bounds_violations", rc)
+    return int(n.value)
 
 
 def rgbid_net_wait_timeouts() -> int:

@@ -11,3 +11,16 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built librgbid")
     config.addinivalue_line("markers", "slow: long-running CPU test")
+
+
+def pytest_sessionfinish(session, exitstatus):
+    # A run against the bounds-checked build (RGBID_LIBRARY=checked) reports how many
+    # out-of-plane gather indices its kernels met, for the test that drives it.
+    report = os.environ.get("RGBID_BOUNDS_REPORT")
+    if not report or os.environ.get("RGBID_LIBRARY") != "checked":
+        return
+    from paper_1807_08271_gb300 import rgbid as R
+    if R._lib is None:
+        return
+    with open(report, "w") as f:
+        f.write(str(R.rgbid_debug_bounds_violations()))
