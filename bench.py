@@ -72,7 +72,7 @@ def alu_roofline(kernel: str, units_per_launch: float, ms_per_launch: float) -> 
 # level 0, the level kernel's 80x60 launch, the one it gets in a frame; cold caches);
 # set to None whenever those kernels change.
 TRAFFIC_PER_UNIT = {"robust_kernel": None, "sweep_kernel": 4847616 / 307200,
-                    "level_kernel": 166912 / (4800 * 10), "split_kernel": None}
+                    "level_kernel": 169472 / (4800 * 10), "split_kernel": None}
 
 
 # ----------------------------------------------------------------------------- ranks
@@ -240,6 +240,9 @@ import numpy as np
 import oracle as O
 from paper_1807_08271_gb300 import synth
 seq = synth.render_sequence(0, n_frames={N})
+if {warm} > 0:      # untimed warm-up: the same tracker over the first frames
+    O.track_sequence(seq["I"], seq["W"], seq["K"], levels={levels}, iters={iters}, kf_every={kf},
+                     n_frames={warm} + 1, reduced={reduced})
 t0 = time.perf_counter()
 r = O.track_sequence(seq["I"], seq["W"], seq["K"], levels={levels}, iters={iters}, kf_every={kf}, n_frames={nf},
                      reduced={reduced})
@@ -248,13 +251,14 @@ print(json.dumps({{"frames": {nf} - 1, "seconds": dt, "T_world": r["T_world"].to
 """
 
 
-def run_oracle_sample(n_frames: int, reduced: bool = False) -> dict:
-    """Time the FP64 oracle (one thread) on frames 0..n_frames-1 of the sequence."""
+def run_oracle_sample(n_frames: int, reduced: bool = False, warmup: int = 0) -> dict:
+    """Time the FP64 oracle (one thread) on frames 0..n_frames-1 of the sequence, after
+    `warmup` untimed frames of the same tracker."""
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
         env[k] = "1"
     code = CPU_SNIPPET.format(root=ROOT, N=N_FRAMES, nf=n_frames, levels=LEVELS, iters=tuple(ITERS), kf=KF_EVERY,
-                              reduced=reduced)
+                              reduced=reduced, warm=int(warmup))
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, check=True)
     return json.loads(out.stdout.strip().splitlines()[-1])
 
@@ -264,16 +268,18 @@ def reference(args):
     if ranks_from_env()[0] != 0:      # rank 0 alone runs the reference arm
         return
     n_timed = max(1, min(args.steps, 24))
-    r = run_oracle_sample(n_timed + 1, reduced=(args.precision == "bf16"))
+    n_warm = max(3, min(args.warmup, 8))
+    r = run_oracle_sample(n_timed + 1, reduced=(args.precision == "bf16"), warmup=n_warm)
     value = r["frames"] / r["seconds"]
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": r["frames"], "warmup": 0, "ms_per_step": 1000.0 * r["seconds"] / r["frames"],
+        "steps": r["frames"], "warmup": n_warm, "ms_per_step": 1000.0 * r["seconds"] / r["frames"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": config_dict("oracle frames 1..%d of the sequence" % r["frames"],
                                                     precision=args.precision),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"frames 1..{r['frames']} of the 300-frame sequence, one thread (numpy float64)"},
+                         "sample": f"frames 1..{r['frames']} of the 300-frame sequence after {n_warm} untimed "
+                                   "warm-up frames, one thread (numpy float64)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
