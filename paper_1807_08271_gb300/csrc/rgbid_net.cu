@@ -68,6 +68,31 @@ constexpr size_t kMaxGradPerSample = act_per_sample(0);   // the largest activat
 
 __device__ __forceinline__ bf16 bz() { return __float2bfloat16_rn(0.f); }
 
+// Programmatic dependent launch between the passes' kernels: each kernel lets its
+// successor be scheduled at once and waits for its predecessor's completion (and
+// memory) before it reads anything, so the launches overlap and the data never does.
+__device__ __forceinline__ void pdl_start() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// launch with programmatic stream serialisation (the kernel calls pdl_start first)
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 // ---------------------------------------------------------------- GEMM core
 // One CTA of 128 threads computes a 128 x TN tile of C (TN = 32 or 64, the
 // smallest that covers N) on the fifth-generation tensor cores: the four warps
@@ -387,6 +412,7 @@ __global__ void __launch_bounds__(GEMM_NT) gemm_tc(P p, int M, int N, int K, int
     auto lb1 = [&](int n, int k) { return p.loadB(k, n); };
     // B's rows are n: loadB8(k, n) gives k .. k+7 of row n (kVecBk) or rows n .. n+7 of column k (kVecBn)
     auto lb8 = [&](int n, int k) { return p.loadB8(k, n); };
+    pdl_start();   // the operands come from the preceding pass
     Vecs<TM> ra;
     Vecs<TN> rb;
     Vecs4 ra4;
@@ -706,6 +732,7 @@ struct FcWgrad {
 // tiles are summed in split order (deterministic) and the epilogue applied
 template <class P>
 __global__ void splitk_reduce(P p, const float* scratch, int M, int N, int splits) {
+    pdl_start();
     const size_t MN = (size_t)M * N;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < MN; i += (size_t)gridDim.x * blockDim.x) {
         float acc = 0.f;
@@ -759,12 +786,14 @@ static cudaError_t gemm(const P& p, int M, int N, int K, int splits, cudaStream_
     const int tn = tile_n(N);
     dim3 grid((unsigned)((M + TM - 1) / TM), (unsigned)((N + tn - 1) / tn), (unsigned)splits);
     float* const sc = splits > 1 ? scratch : nullptr;
-    if (tn == 32) gemm_tc<P, 32><<<grid, GEMM_NT, TileCfg<32>::kSmem, s>>>(p, M, N, K, kchunk, sc);
-    else gemm_tc<P, 64><<<grid, GEMM_NT, TileCfg<64>::kSmem, s>>>(p, M, N, K, kchunk, sc);
+    cudaError_t e = tn == 32 ? launch_pdl(gemm_tc<P, 32>, grid, dim3(GEMM_NT), TileCfg<32>::kSmem, s, p, M, N, K, kchunk, sc)
+                             : launch_pdl(gemm_tc<P, 64>, grid, dim3(GEMM_NT), TileCfg<64>::kSmem, s, p, M, N, K, kchunk, sc);
+    if (e != cudaSuccess) return e;
     if (splits > 1 && scratch) {
         const size_t MN = (size_t)M * N;
-        splitk_reduce<P><<<(unsigned)((MN + 255) / 256 < 1024 ? (MN + 255) / 256 : 1024), 256, 0, s>>>(p, scratch, M, N,
-                                                                                                    splits);
+        const unsigned nb = (unsigned)((MN + 255) / 256 < 1024 ? (MN + 255) / 256 : 1024);
+        e = launch_pdl(splitk_reduce<P>, dim3(nb), dim3(256), 0, s, p, (const float*)scratch, M, N, splits);
+        if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
 }
@@ -794,6 +823,7 @@ static int wgrad_splits(int M, int N, long long K) {
 
 // ---------------------------------------------------------------- elementwise kernels
 __global__ void to_bf16_kernel(const float* src, bf16* dst, size_t n) {
+    pdl_start();
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         dst[i] = __float2bfloat16_rn(src[i]);
 }
@@ -869,6 +899,7 @@ __global__ void adam_kernel(float* p, const float* g, float* m, float* v, size_t
 
 // one block per item; x[n][v][u][c] from the 80x60 level of its ref (A) and cur (B) pyramids
 __global__ void inputs_kernel(const rgbid_batch_item* items, int precision, bf16* x) {
+    pdl_start();
     const rgbid_batch_item* it = items + blockIdx.x;
     __shared__ int lv;
     if (threadIdx.x == 0) {
@@ -925,6 +956,7 @@ struct Tiers {
 
 __global__ void plan_kernel(const float* y, int n, Tiers tiers, const rgbid_batch_item* d_in, rgbid_batch_item* d_out,
                             int* skipped) {
+    pdl_start();
     const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (i >= n) return;
@@ -1062,8 +1094,10 @@ extern "C" int rgbid_net_inputs(const rgbid_batch_item* d_items, int n, int prec
     if (misaligned(d_items, 8) || misaligned(x, 4)) return RGBID_ERR_INVALID_ARG;
     if (precision != RGBID_PLANES_F32 && precision != RGBID_PLANES_BF16_F16) return RGBID_ERR_UNSUPPORTED;
     if (n == 0) return RGBID_OK;
-    inputs_kernel<<<(unsigned)n, 256, 0, (cudaStream_t)stream>>>(d_items, precision, (bf16*)x);
-    return cudaGetLastError() == cudaSuccess ? RGBID_OK : RGBID_ERR_CUDA;
+    return launch_pdl(inputs_kernel, dim3((unsigned)n), dim3(256), 0, (cudaStream_t)stream, d_items, precision,
+                      (bf16*)x) == cudaSuccess
+               ? RGBID_OK
+               : RGBID_ERR_CUDA;
 }
 
 extern "C" int rgbid_net_forward(const float* params, const void* x, int batch, float* y, void* workspace,
@@ -1074,8 +1108,7 @@ extern "C" int rgbid_net_forward(const float* params, const void* x, int batch, 
     const int rc = check_ws(batch, workspace, workspace_bytes, &w);
     if (rc != RGBID_OK) return rc;
     cudaStream_t s = (cudaStream_t)stream_;
-    to_bf16_kernel<<<256, 256, 0, s>>>(params, w.wb, kParams);
-    if (cudaGetLastError() != cudaSuccess) return RGBID_ERR_CUDA;
+    if (launch_pdl(to_bf16_kernel, dim3(256), dim3(256), 0, s, params, w.wb, kParams) != cudaSuccess) return RGBID_ERR_CUDA;
     const bf16* in = (const bf16*)x;
     for (int l = 0; l < RGBID_NET_LAYERS; ++l) {
         const LayerDef& d = kLayers[l];
@@ -1172,6 +1205,8 @@ extern "C" int rgbid_net_plan(const float* y, int n, const float* max_log_var, i
     Tiers tiers;
     tiers.n = n_tiers;
     for (int t = 0; t < RGBID_NET_MAX_TIERS; ++t) tiers.thr[t] = t < n_tiers ? max_log_var[t] : -3.0e38f;
-    plan_kernel<<<(unsigned)((n + 7) / 8), 256, 0, (cudaStream_t)stream>>>(y, n, tiers, d_in, d_out, skipped);
-    return cudaGetLastError() == cudaSuccess ? RGBID_OK : RGBID_ERR_CUDA;
+    return launch_pdl(plan_kernel, dim3((unsigned)((n + 7) / 8)), dim3(256), 0, (cudaStream_t)stream, y, n, tiers,
+                      d_in, d_out, skipped) == cudaSuccess
+               ? RGBID_OK
+               : RGBID_ERR_CUDA;
 }
