@@ -1152,10 +1152,11 @@ def native_learned(args):
                     "learned_alignments_per_s": LEARNED_N / (ms_l / 1000.0),
                     "plain_converged": float(np.mean(ev.converged(res_p))),
                     "learned_converged": float(np.mean(ev.converged(res_l)))},
-        # per learned alignment: input packing, bf16 weights, 6 GEMMs and their 6 split-K reductions,
-        # the plan, the alignment's init kernel, 2 launches per scheduled iteration (skipped ones
-        # included) and the closing reduction
-        "cpu_baseline": cpu, "clocks": clk, "gpu_launches": n_steps * (15 + 1 + 2 * 25 + 1),
+        # per learned alignment: input packing, bf16 weights, 6 GEMMs and the split-K reductions
+        # of the five that split at batch 1, the plan, then the alignment's launches (a skipped
+        # level's launch included)
+        "cpu_baseline": cpu, "clocks": clk,
+        "gpu_launches": n_steps * (14 + R.rgbid_align_launches(ev.pyr[0][0].desc, la.params)),
     }
     print(json.dumps(line))
     if dist:

@@ -144,7 +144,8 @@ typedef struct {
                                     and solves inside the cluster.  A larger level runs in the split
                                     kernel, a cooperative launch of one such cluster (solve, sample,
                                     robust parameters) and helper CTAs that evaluate every pixel's
-                                    terms while the cluster estimates the parameters.  1: every level
+                                    terms while the cluster estimates the parameters; consecutive
+                                    such levels share one launch.  1: every level
                                     by the per-iteration robust-scale and sweep kernels.  All compute
                                     the same steps (sums in another order). */
     int pad2_;

@@ -1006,19 +1006,13 @@ static bool use_split_kernel(const rgbid_pyramid* ref, const rgbid_align_params*
     return split_kernel_takes(ref->precision, L.width, L.height);
 }
 
+// The launch-wide arguments of a split-kernel launch; its levels are added by add_split_level.
 static SplitArgs split_args(const RobustArgs& ra, const rgbid_align_params* p, float* partials) {
     SplitArgs sp;
     memset(&sp, 0, sizeof(sp));
-    sp.A = ra.A;
-    sp.B = ra.B;
     sp.st = ra.st;
     sp.partials = reinterpret_cast<float2*>(partials);
-    sp.iters = p->iters[ra.level];
     sp.level_iters = p->level_iters;
-    sp.level = ra.level;
-    sp.s = ra.s;
-    sp.nsx = ra.nsx;
-    sp.nsamp = ra.nsamp;
     sp.scale_iters = p->scale_iters;
     sp.bisect_steps = p->bisect_steps;
     sp.estimate_nu = p->estimate_nu;
@@ -1028,9 +1022,22 @@ static SplitArgs split_args(const RobustArgs& ra, const rgbid_align_params* p, f
     sp.nu_hi = p->nu_hi;
     memcpy(sp.nu_g, ra.nu_g, sizeof(sp.nu_g));
     sp.n_helpers = 0;         // set by the caller for the device
-    sp.tiles_x = (ra.A.w + kSplitTileW - 1) / kSplitTileW;
-    sp.tiles_y = (ra.A.h + kSplitTileH - 1) / kSplitTileH;
+    sp.n_levels = 0;
     return sp;
+}
+
+// One more level of a split-kernel launch (levels are added coarse to fine).
+static void add_split_level(SplitArgs& sp, const RobustArgs& ra, const rgbid_align_params* p) {
+    SplitLevel& L = sp.lv[sp.n_levels++];
+    L.A = ra.A;
+    L.B = ra.B;
+    L.level = ra.level;
+    L.iters = p->iters[ra.level];
+    L.s = ra.s;
+    L.nsx = ra.nsx;
+    L.nsamp = ra.nsamp;
+    L.tiles_x = (ra.A.w + kSplitTileW - 1) / kSplitTileW;
+    L.tiles_y = (ra.A.h + kSplitTileH - 1) / kSplitTileH;
 }
 
 static LevelArgs level_args(const rgbid_pyramid* ref, const rgbid_pyramid* cur, int l, const rgbid_align_params* p,
@@ -1099,9 +1106,18 @@ extern "C" size_t rgbid_align_workspace_bytes(const rgbid_pyramid* ref, const rg
 extern "C" int rgbid_align_launches(const rgbid_pyramid* ref, const rgbid_align_params* params) {
     if (check_pyramids(ref, ref, params) != RGBID_OK) return -1;
     int n = 2;   // the initialisation and the closing launch
+    bool in_split = false;   // consecutive split-kernel levels share one launch
     for (int l = params->levels - 1; l >= 0; --l) {
         if (params->iters[l] <= 0) continue;
-        n += (use_level_kernel(ref, params, l) || use_split_kernel(ref, params, l)) ? 1 : 2 * params->iters[l];
+        const bool lk = use_level_kernel(ref, params, l);
+        const bool sk = !lk && use_split_kernel(ref, params, l);
+        if (sk) {
+            if (!in_split) ++n;
+            in_split = true;
+            continue;
+        }
+        in_split = false;
+        n += lk ? 1 : 2 * params->iters[l];
     }
     return n;
 }
@@ -1133,12 +1149,46 @@ extern "C" int rgbid_align(const rgbid_pyramid* ref, const rgbid_pyramid* cur, c
     rgbid_timing* tm = params->timing;
     RobustArgs ra{};
     bool after_level_kernel = false;   // the next robust-scale launch follows a level kernel
+    // consecutive levels that run in the split kernel go in one launch (coarse to fine)
+    SplitArgs group;
+    memset(&group, 0, sizeof(group));
+    long long group_units = 0;
+    auto flush_split = [&]() -> int {
+        if (group.n_levels == 0) return RGBID_OK;
+        group.n_helpers = split_kernel_helpers(ref->precision);
+        group.max_tiles = 1;
+        for (int q = 0; q < group.n_levels; ++q)
+            group.max_tiles =
+                std::max(group.max_tiles, split_tiles_per_helper(group.lv[q].A.w, group.lv[q].A.h, group.n_helpers));
+        const bool tl = tm && tm->kernel == RGBID_KERNEL_SPLIT && tm->count < tm->capacity;
+        if (tl && cudaEventRecord((cudaEvent_t)tm->ev_start[tm->count], stream) != cudaSuccess) return RGBID_ERR_CUDA;
+        if (launch_split(ref->precision, group, stream) != cudaSuccess) return RGBID_ERR_CUDA;
+        if (tl) {
+            if (cudaEventRecord((cudaEvent_t)tm->ev_end[tm->count], stream) != cudaSuccess) return RGBID_ERR_CUDA;
+            tm->count += 1;
+            tm->units += group_units;
+        }
+        group.n_levels = 0;
+        group_units = 0;
+        after_level_kernel = true;
+        return RGBID_OK;
+    };
     for (int l = params->levels - 1; l >= 0; --l) {
         ra = robust_args(ref, cur, l, params, st);
         // set before any level kernel: the closing launch takes `ra` of the finest level
         ra.partials = reinterpret_cast<const float2*>(partials);
         ra.res = d_result;
         ra.level_iters = params->level_iters;
+        if (params->iters[l] > 0 && use_split_kernel(ref, params, l) && !use_level_kernel(ref, params, l)) {
+            if (group.n_levels == 0) group = split_args(ra, params, partials);
+            add_split_level(group, ra, params);
+            group_units += (long long)ra.A.w * ra.A.h * params->iters[l];
+            continue;
+        }
+        if (params->iters[l] > 0) {
+            const int fe = flush_split();
+            if (fe != RGBID_OK) return fe;
+        }
         if (params->iters[l] > 0 && use_level_kernel(ref, params, l)) {
             const LevelArgs la = level_args(ref, cur, l, params, st, partials);
             const bool tl = tm && tm->kernel == RGBID_KERNEL_LEVEL && tm->count < tm->capacity;
@@ -1148,21 +1198,6 @@ extern "C" int rgbid_align(const rgbid_pyramid* ref, const rgbid_pyramid* cur, c
                 if (cudaEventRecord((cudaEvent_t)tm->ev_end[tm->count], stream) != cudaSuccess) return RGBID_ERR_CUDA;
                 tm->count += 1;
                 tm->units += (long long)la.A.w * la.A.h * params->iters[l];
-            }
-            after_level_kernel = true;
-            continue;
-        }
-        if (params->iters[l] > 0 && use_split_kernel(ref, params, l)) {
-            SplitArgs sp = split_args(ra, params, partials);
-            sp.n_helpers = split_kernel_helpers(ref->precision);
-            sp.max_tiles = (sp.tiles_x * sp.tiles_y + sp.n_helpers - 1) / sp.n_helpers;
-            const bool tl = tm && tm->kernel == RGBID_KERNEL_SPLIT && tm->count < tm->capacity;
-            if (tl && cudaEventRecord((cudaEvent_t)tm->ev_start[tm->count], stream) != cudaSuccess) return RGBID_ERR_CUDA;
-            if (launch_split(ref->precision, sp, stream) != cudaSuccess) return RGBID_ERR_CUDA;
-            if (tl) {
-                if (cudaEventRecord((cudaEvent_t)tm->ev_end[tm->count], stream) != cudaSuccess) return RGBID_ERR_CUDA;
-                tm->count += 1;
-                tm->units += (long long)sp.A.w * sp.A.h * params->iters[l];
             }
             after_level_kernel = true;
             continue;
@@ -1200,6 +1235,10 @@ extern "C" int rgbid_align(const rgbid_pyramid* ref, const rgbid_pyramid* cur, c
                 tm->units += (long long)sa.A.w * sa.A.h;
             }
         }
+    }
+    {
+        const int fe = flush_split();
+        if (fe != RGBID_OK) return fe;
     }
     // the last sweep's (or level kernel's) pending step: reduction, solve and update
     ra.finalize_only = 1;

@@ -515,8 +515,14 @@ __global__ void __launch_bounds__(kRobustNT, 1) split_kernel(SplitArgs a) {
     __shared__ int sh_cnt[3];                        // iterations done, skipped, status
     __shared__ int go[3];                            // verdicts of the CTA's mailbox waits, one per site
 
-    const int n_it = a.level_iters ? min(a.iters, __ldg(a.level_iters + a.level)) : a.iters;
-    if (n_it <= 0) {
+    // the launch runs its levels coarse to fine, each for its iteration count; `git`
+    // below counts the launch's iterations over all levels (the mailbox's flags)
+    auto level_its = [&](int l) {
+        return a.level_iters ? min(a.lv[l].iters, __ldg(a.level_iters + a.lv[l].level)) : a.lv[l].iters;
+    };
+    int n_total = 0;
+    for (int l = 0; l < a.n_levels; ++l) n_total += max(level_its(l), 0);
+    if (n_total <= 0) {
         pdl_wait();   // keeps the chain of dependent launches ordered; never triggers
         return;
     }
@@ -533,24 +539,30 @@ __global__ void __launch_bounds__(kRobustNT, 1) split_kernel(SplitArgs a) {
             for (int k = 0; k < kNuGTerms; ++k) sh_g[k] = a.nu_g[k];
         }
         cluster_arrive();
-        // the keyframe-side stage of this thread's samples, kept for every iteration
-        // (A's planes do not change during an alignment)
+        // the keyframe-side stage of this thread's samples of a level, kept for all of the
+        // level's iterations (A's planes do not change during an alignment); each thread
+        // writes only its own slots
         float* const Sa = dyn + tid;                 // [MAXS][kSampleTerms][NT]
         const int gt = rank * NT + tid;
+        auto stage_samples = [&](const SplitLevel& L) {
 #pragma unroll
-        for (int k = 0; k < MAXS; ++k) {
-            const int i = gt + k * (CL * NT);
-            PxA p;
-            p.ok = false;
-            if (i < a.nsamp) {
-                const int sy = i / a.nsx, sx = i - sy * a.nsx;
-                stage_a<PREC>(a.A, sx * a.s, sy * a.s, p);
+            for (int k = 0; k < MAXS; ++k) {
+                const int i = gt + k * (CL * NT);
+                PxA p;
+                p.ok = false;
+                if (i < L.nsamp) {
+                    const int sy = i / L.nsx, sx = i - sy * L.nsx;
+                    stage_a<PREC>(L.A, sx * L.s, sy * L.s, p);
+                }
+                float* const q = Sa + k * (kSampleTerms * NT);
+                q[0] = p.c.x; q[NT] = p.c.y; q[2 * NT] = p.nl.x; q[3 * NT] = p.nl.y; q[4 * NT] = p.nr.x;
+                q[5 * NT] = p.nr.y; q[6 * NT] = p.nu.x; q[7 * NT] = p.nu.y; q[8 * NT] = p.nd.x; q[9 * NT] = p.nd.y;
+                q[10 * NT] = p.a; q[11 * NT] = p.b; q[12 * NT] = p.ok ? 1.f : 0.f;
             }
-            float* const q = Sa + k * (kSampleTerms * NT);
-            q[0] = p.c.x; q[NT] = p.c.y; q[2 * NT] = p.nl.x; q[3 * NT] = p.nl.y; q[4 * NT] = p.nr.x;
-            q[5 * NT] = p.nr.y; q[6 * NT] = p.nu.x; q[7 * NT] = p.nu.y; q[8 * NT] = p.nd.x; q[9 * NT] = p.nd.y;
-            q[10 * NT] = p.a; q[11 * NT] = p.b; q[12 * NT] = p.ok ? 1.f : 0.f;
-        }
+        };
+        int first = 0;                               // the first level that runs iterations
+        while (level_its(first) <= 0) ++first;
+        stage_samples(a.lv[first]);                  // A is complete before this launch
         pdl_wait();   // the state and the pending partials of the preceding launches are visible
         if (tid < 16) {
             T_sh[tid] = __ldcg(st->T + tid);
@@ -575,11 +587,21 @@ __global__ void __launch_bounds__(kRobustNT, 1) split_kernel(SplitArgs a) {
         const float lo0 = (float)a.nu_lo, hi0 = (float)a.nu_hi;
         const float m = 0.5f * (lo0 + hi0), h = 0.5f * (hi0 - lo0);
 
-        for (int it = 0; it < n_it; ++it) {
+        int git = 0;
+        bool broken = false;
+        for (int l = first; l < a.n_levels && !broken; ++l) {
+          const int n_it = level_its(l);
+          if (n_it <= 0) continue;
+          const SplitLevel& L = a.lv[l];
+          if (l != first) stage_samples(L);
+          for (int it = 0; it < n_it; ++it, ++git) {
             // ---- the previous step: the pending partials of the preceding launch, or the
-            //      helpers' partials of the previous iteration
-            if (it > 0 && !cta_wait(st, &mb->arrived, (unsigned)a.n_helpers * (unsigned)it, &go[0])) break;
-            const unsigned int nb = it == 0 ? nb0 : (unsigned)a.n_helpers;
+            //      helpers' partials of the previous iteration (of this level or the last)
+            if (git > 0 && !cta_wait(st, &mb->arrived, (unsigned)a.n_helpers * (unsigned)git, &go[0])) {
+                broken = true;
+                break;
+            }
+            const unsigned int nb = git == 0 ? nb0 : (unsigned)a.n_helpers;
             if (nb) {
                 // every CTA of the cluster sums all nb partials itself in one fixed order
                 // (warp w takes partials w, w + 8, ...; then the warps' sums in a fixed
@@ -610,7 +632,7 @@ __global__ void __launch_bounds__(kRobustNT, 1) split_kernel(SplitArgs a) {
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
                     __stcg(reinterpret_cast<float4*>(&mb->wp) + q, reinterpret_cast<const float4*>(&sh_wp)[q]);
-                st_release_u32(&mb->pose_flag, (unsigned)it + 1u);
+                st_release_u32(&mb->pose_flag, (unsigned)git + 1u);
             }
             const WarpPose wp = sh_wp;
 
@@ -633,18 +655,18 @@ __global__ void __launch_bounds__(kRobustNT, 1) split_kernel(SplitArgs a) {
                     sa[k].a = q[10 * NT];
                     sa[k].b = q[11 * NT];
                     sa[k].ok = q[12 * NT] != 0.f;
-                    const int sy = i < a.nsamp ? i / a.nsx : 0, sx = i < a.nsamp ? i - sy * a.nsx : 0;
-                    su[k] = sx * a.s;
-                    sv[k] = sy * a.s;
+                    const int sy = i < L.nsamp ? i / L.nsx : 0, sx = i < L.nsamp ? i - sy * L.nsx : 0;
+                    su[k] = sx * L.s;
+                    sv[k] = sy * L.s;
                 }
 #pragma unroll
-                for (int k = 0; k < MAXS; ++k) stage_w(a.A, a.B, wp, su[k], sv[k], sa[k], sw[k]);
+                for (int k = 0; k < MAXS; ++k) stage_w(L.A, L.B, wp, su[k], sv[k], sa[k], sw[k]);
 #pragma unroll
-                for (int k = 0; k < MAXS; ++k) stage_b<PREC>(a.B, sw[k], sb[k]);
+                for (int k = 0; k < MAXS; ++k) stage_b<PREC>(L.B, sw[k], sb[k]);
 #pragma unroll
                 for (int k = 0; k < MAXS; ++k) {
                     PixelTerms o;
-                    finish<false>(a.A, wp, sa[k], sw[k], sb[k], o);
+                    finish<false>(L.A, wp, sa[k], sw[k], sb[k], o);
                     rs[0][k] = o.mI ? o.rI : __int_as_float(0x7fc00000);
                     rs[1][k] = o.mW ? o.rW : __int_as_float(0x7fc00000);
                 }
@@ -795,12 +817,13 @@ __global__ void __launch_bounds__(kRobustNT, 1) split_kernel(SplitArgs a) {
                     for (int q = 0; q < (int)(sizeof(RobustParams) / 4); ++q)
                         __stcg(reinterpret_cast<int*>(&mb->rob) + q, src[q]);
                     // the same thread releases the flag: the release orders the stores above
-                    st_release_u32(&mb->rob_flag, (unsigned)it + 1u);
+                    st_release_u32(&mb->rob_flag, (unsigned)git + 1u);
                 }
             }
         }
-        // ---- the level's last step stays pending: the helpers' partials, weighted with
-        //      the parameters published last, at the pose published last
+        }
+        // ---- the last step stays pending: the helpers' partials, weighted with the
+        //      parameters published last, at the pose published last
         __syncthreads();
         if (rank == 0) {
             if (tid < 16) {
@@ -821,11 +844,20 @@ __global__ void __launch_bounds__(kRobustNT, 1) split_kernel(SplitArgs a) {
     } else {
         // ================================================================ helper CTAs
         const int hc = (int)blockIdx.x - CL;
-        const int ntiles = a.tiles_x * a.tiles_y;
         float* const Tm = dyn + tid;                 // [max_tiles][kSplitTerms][NT]
         pdl_wait();
-        for (int it = 0; it < n_it; ++it) {
-            if (!cta_wait(st, &mb->pose_flag, (unsigned)it + 1u, &go[1])) break;
+        int git = 0;
+        bool broken = false;
+        for (int l = 0; l < a.n_levels && !broken; ++l) {
+          const int n_it = level_its(l);
+          if (n_it <= 0) continue;
+          const SplitLevel& L = a.lv[l];
+          const int ntiles = L.tiles_x * L.tiles_y;
+          for (int it = 0; it < n_it; ++it, ++git) {
+            if (!cta_wait(st, &mb->pose_flag, (unsigned)git + 1u, &go[1])) {
+                broken = true;
+                break;
+            }
             if (tid < 16) reinterpret_cast<float*>(&sh_wp)[tid] = __ldcg(reinterpret_cast<const float*>(&mb->wp) + tid);
             __syncthreads();
             const WarpPose wp = sh_wp;
@@ -843,24 +875,24 @@ __global__ void __launch_bounds__(kRobustNT, 1) split_kernel(SplitArgs a) {
                     pv[g] = 0;
                     const int t = hc + (j0 + g) * a.n_helpers;
                     if (j0 + g < a.max_tiles && t < ntiles) {
-                        const int ty = t / a.tiles_x, tx = t - ty * a.tiles_x;
+                        const int ty = t / L.tiles_x, tx = t - ty * L.tiles_x;
                         const int u = tx * kSplitTileW + lane, v = ty * kSplitTileH + warp;
-                        if (u < a.A.w && v < a.A.h) {
+                        if (u < L.A.w && v < L.A.h) {
                             pu[g] = u;
                             pv[g] = v;
-                            stage_a<PREC>(a.A, u, v, sa[g]);
+                            stage_a<PREC>(L.A, u, v, sa[g]);
                         }
                     }
                 }
 #pragma unroll
-                for (int g = 0; g < G; ++g) stage_w(a.A, a.B, wp, pu[g], pv[g], sa[g], sw[g]);
+                for (int g = 0; g < G; ++g) stage_w(L.A, L.B, wp, pu[g], pv[g], sa[g], sw[g]);
 #pragma unroll
-                for (int g = 0; g < G; ++g) stage_b<PREC>(a.B, sw[g], sb[g]);
+                for (int g = 0; g < G; ++g) stage_b<PREC>(L.B, sw[g], sb[g]);
 #pragma unroll
                 for (int g = 0; g < G; ++g) {
                     if (j0 + g >= a.max_tiles) continue;
                     PixelTerms o;
-                    finish<true>(a.A, wp, sa[g], sw[g], sb[g], o);
+                    finish<true>(L.A, wp, sa[g], sw[g], sb[g], o);
                     float* const T = Tm + (j0 + g) * (kSplitTerms * NT);
                     T[0] = o.mI ? o.rI : __int_as_float(0x7fc00000);
                     T[NT] = o.mW ? o.rW : __int_as_float(0x7fc00000);
@@ -876,7 +908,10 @@ __global__ void __launch_bounds__(kRobustNT, 1) split_kernel(SplitArgs a) {
                 }
             }
             // ---- weighted normal equations once the parameters are published
-            if (!cta_wait(st, &mb->rob_flag, (unsigned)it + 1u, &go[2])) break;
+            if (!cta_wait(st, &mb->rob_flag, (unsigned)git + 1u, &go[2])) {
+                broken = true;
+                break;
+            }
             if (tid < (int)(sizeof(RobustParams) / 4))
                 reinterpret_cast<int*>(&sh_rob)[tid] = __ldcg(reinterpret_cast<const int*>(&mb->rob) + tid);
             __syncthreads();
@@ -918,6 +953,7 @@ __global__ void __launch_bounds__(kRobustNT, 1) split_kernel(SplitArgs a) {
                 __syncwarp();
                 if (lane == 0) atomicAdd(&mb->arrived, 1u);
             }
+          }
         }
     }
     // ---- the last CTA to leave resets the mailbox for the next launch
@@ -1105,11 +1141,15 @@ int split_kernel_helpers(int precision) {
                                          : split_helpers_t<RGBID_PLANES_BF16_F16>();
 }
 
+int split_tiles_per_helper(int w, int h, int n_helpers) {
+    const long long tiles = (long long)((w + kSplitTileW - 1) / kSplitTileW) * ((h + kSplitTileH - 1) / kSplitTileH);
+    return n_helpers > 0 ? (int)((tiles + n_helpers - 1) / n_helpers) : 0x7fffffff;
+}
+
 bool split_kernel_takes(int precision, int w, int h) {
     const int nh = split_kernel_helpers(precision);
     if (nh <= 0) return false;
-    const long long tiles = (long long)((w + kSplitTileW - 1) / kSplitTileW) * ((h + kSplitTileH - 1) / kSplitTileH);
-    return (tiles + nh - 1) / nh <= kSplitMaxTiles;
+    return split_tiles_per_helper(w, h, nh) <= kSplitMaxTiles;
 }
 
 template <int PREC>
@@ -1139,11 +1179,14 @@ cudaError_t launch_split(int precision, const SplitArgs& sa, cudaStream_t stream
     if (sa.n_helpers <= 0 || sa.n_helpers > kSplitMaxHelpers || sa.n_helpers % kLevelCL ||
         sa.n_helpers != split_kernel_helpers(precision))
         return cudaErrorInvalidValue;
-    if (sa.max_tiles < 1 || sa.max_tiles > kSplitMaxTiles ||
-        (long long)sa.max_tiles * sa.n_helpers < (long long)sa.tiles_x * sa.tiles_y)
-        return cudaErrorInvalidValue;
-    if (sa.tiles_x * kSplitTileW < sa.A.w || sa.tiles_y * kSplitTileH < sa.A.h) return cudaErrorInvalidValue;
-    if (sa.nsamp < 1 || sa.nsamp > RGBID_MAX_SAMPLES) return cudaErrorInvalidValue;
+    if (sa.max_tiles < 1 || sa.max_tiles > kSplitMaxTiles) return cudaErrorInvalidValue;
+    if (sa.n_levels < 1 || sa.n_levels > kSplitMaxLevels) return cudaErrorInvalidValue;
+    for (int l = 0; l < sa.n_levels; ++l) {
+        const SplitLevel& L = sa.lv[l];
+        if ((long long)sa.max_tiles * sa.n_helpers < (long long)L.tiles_x * L.tiles_y) return cudaErrorInvalidValue;
+        if (L.tiles_x * kSplitTileW < L.A.w || L.tiles_y * kSplitTileH < L.A.h) return cudaErrorInvalidValue;
+        if (L.nsamp < 1 || L.nsamp > RGBID_MAX_SAMPLES) return cudaErrorInvalidValue;
+    }
     return precision == RGBID_PLANES_F32 ? launch_split_t<RGBID_PLANES_F32>(sa, stream)
                                          : launch_split_t<RGBID_PLANES_BF16_F16>(sa, stream);
 }

@@ -36,27 +36,36 @@ constexpr int kSplitTerms = 15;                    // per pixel in shared memory
 constexpr int kSplitMaxTiles = 13;                 // tiles per helper CTA (shared memory)
 constexpr int kSplitMaxHelpers = 8 * 16;           // helper CTAs at most (8 clusters)
 
-struct SplitArgs {
+// One level of a split-kernel launch (consecutive levels run in one launch, coarse to fine).
+struct SplitLevel {
     LevelDev A, B;
+    int level;                // pyramid level (the index into level_iters)
+    int iters;                // Gauss-Newton iterations of the level (host count)
+    int s, nsx, nsamp;        // the systematic sample
+    int tiles_x, tiles_y;     // kSplitTileW x kSplitTileH tiles of the level
+};
+constexpr int kSplitMaxLevels = RGBID_MAX_LEVELS;
+
+struct SplitArgs {
+    SplitLevel lv[kSplitMaxLevels];
+    int n_levels;             // levels of the launch, coarsest first
     AlignState* st;
     float2* partials;         // pending partials of the previous launch, then one per helper CTA
-    int iters;
     const int* level_iters;
-    int level;
-    int s, nsx, nsamp;        // the systematic sample
     int scale_iters, bisect_steps, estimate_nu, min_valid;
     float nu0;
     double nu_lo, nu_hi;
     float nu_g[kNuGTerms];
     int n_helpers;            // helper CTAs (the grid's CTAs after the first cluster)
-    int tiles_x, tiles_y;     // kSplitTileW x kSplitTileH tiles of the level
-    int max_tiles;            // tiles per helper CTA
+    int max_tiles;            // tiles per helper CTA (the largest level's)
 };
 
 // Helper CTAs the split kernel launches on the current device (0: not available).
 int split_kernel_helpers(int precision);
 // Whether a w x h level runs in the split kernel (its tiles fit the helpers).
 bool split_kernel_takes(int precision, int w, int h);
+// Tiles per helper CTA that a w x h level needs with n_helpers helpers.
+int split_tiles_per_helper(int w, int h, int n_helpers);
 cudaError_t launch_split(int precision, const SplitArgs& sa, cudaStream_t stream);
 
 // Whether a w x h level with sample cap `cap` runs in the level kernel on the current
