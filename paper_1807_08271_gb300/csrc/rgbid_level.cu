@@ -595,6 +595,9 @@ __global__ void __launch_bounds__(kRobustNT, 1) split_kernel(SplitArgs a) {
           const SplitLevel& L = a.lv[l];
           if (l != first) stage_samples(L);
           for (int it = 0; it < n_it; ++it, ++git) {
+            // the next launch may be scheduled while the last iteration runs (on the SMs this
+            // launch leaves free); it reads the state only after this grid has completed
+            if (git == n_total - 1) pdl_trigger();
             // ---- the previous step: the pending partials of the preceding launch, or the
             //      helpers' partials of the previous iteration (of this level or the last)
             if (git > 0 && !cta_wait(st, &mb->arrived, (unsigned)a.n_helpers * (unsigned)git, &go[0])) {
@@ -854,6 +857,7 @@ __global__ void __launch_bounds__(kRobustNT, 1) split_kernel(SplitArgs a) {
           const SplitLevel& L = a.lv[l];
           const int ntiles = L.tiles_x * L.tiles_y;
           for (int it = 0; it < n_it; ++it, ++git) {
+            if (git == n_total - 1) pdl_trigger();
             if (!cta_wait(st, &mb->pose_flag, (unsigned)git + 1u, &go[1])) {
                 broken = true;
                 break;
