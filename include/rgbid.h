@@ -518,6 +518,18 @@ int rgbid_probe_wait_timeout(long long budget_cycles, int* d_timeouts, void* str
  * RGBID_ERR_UNSUPPORTED.  Errors: INVALID_ARG (NULL count), CUDA. */
 int rgbid_debug_bounds_violations(unsigned long long* count);
 
+/* Diagnostic of the phase-stamped build (the paper has no counterpart): a library
+ * compiled with -DRGBID_PHASE_STAMPS has thread 0 of the split kernel's cluster CTA 0
+ * and of its first helper CTA record the global timer (ns) as each phase of an
+ * iteration ends: out[(level * 16 + iteration) * 16 + phase], iterations < 16 of every
+ * pyramid level, the phases 0-8 of the cluster (iteration start, partials arrived,
+ * solved, pose published, sample residuals, counts, fixed-point rounds, nu sums,
+ * parameters published) and 9-12 of the helper (pose seen, pixel pass done,
+ * parameters seen, partial posted).  Copies RGBID_MAX_LEVELS * 256 values (n at least
+ * that) to host memory after a device synchronisation.  The product build returns
+ * RGBID_ERR_UNSUPPORTED.  Errors: INVALID_ARG, CUDA. */
+int rgbid_debug_phase_stamps(long long* out, int n);
+
 /* Diagnostic of the split level kernel's failure detection (the paper has no
  * counterpart).  The split kernel's roles wait on counters in the workspace's
  * mailbox; this launches one CTA that clears a mailbox in `d_scratch` (device,

@@ -24,6 +24,10 @@ LIB = os.path.join(PKG, "librgbid.so")
 # rgbid_debug_bounds_violations); a test build, not the product library
 BUILD_CHECKED = os.path.join(PKG, "_build_checked")
 LIB_CHECKED = os.path.join(PKG, "librgbid_checked.so")
+# the phase-stamped variant (the split kernel records when each phase of an iteration
+# ends, see rgbid_debug_phase_stamps); a diagnostic build, not the product library
+BUILD_PHASES = os.path.join(PKG, "_build_phases")
+LIB_PHASES = os.path.join(PKG, "librgbid_phases.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 
@@ -62,14 +66,18 @@ def _compile(src: str, extra: list[str], build_dir: str = BUILD) -> str:
     return obj
 
 
-def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None, checked: bool = False) -> str:
-    """Compile librgbid.so (checked=True: librgbid_checked.so with -DRGBID_BOUNDS_CHECK)
-    if needed and return its path."""
-    lib, build_dir = (LIB_CHECKED, BUILD_CHECKED) if checked else (LIB, BUILD)
+def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None, checked: bool = False,
+          phases: bool = False) -> str:
+    """Compile librgbid.so (checked=True: librgbid_checked.so with -DRGBID_BOUNDS_CHECK;
+    phases=True: librgbid_phases.so with -DRGBID_PHASE_STAMPS) if needed and return its path."""
+    if checked and phases:
+        raise ValueError("one variant at a time")
+    lib, build_dir = (LIB_CHECKED, BUILD_CHECKED) if checked else ((LIB_PHASES, BUILD_PHASES) if phases else (LIB, BUILD))
     if not force and up_to_date(lib):
         return lib
     os.makedirs(build_dir, exist_ok=True)
-    extra = list(extra or []) + (["-DRGBID_BOUNDS_CHECK"] if checked else [])
+    extra = list(extra or []) + (["-DRGBID_BOUNDS_CHECK"] if checked else []) + \
+        (["-DRGBID_PHASE_STAMPS"] if phases else [])
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(sources()), os.cpu_count() or 1))) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra, build_dir), sources()))
     tmp = lib + ".tmp"

@@ -28,6 +28,29 @@
 #include "rgbid_device.cuh"
 #include "rgbid_level.h"
 
+// Phase stamps of the split kernel (a diagnostic build, -DRGBID_PHASE_STAMPS): thread 0
+// of cluster 0's CTA 0 and of the first helper CTA record %globaltimer (ns) at the
+// phases of each iteration, per pyramid level; rgbid_debug_phase_stamps copies them
+// out.  Without the macro the stamps compile away.
+#ifdef RGBID_PHASE_STAMPS
+__device__ long long g_phase[RGBID_MAX_LEVELS][16][16];
+__device__ __forceinline__ long long global_ns() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+#define RGBID_STAMP(role_ok, k)                                                                \
+    do {                                                                                       \
+        if ((role_ok) && threadIdx.x == 0 && it < 16) g_phase[L.level % RGBID_MAX_LEVELS][it][k] = global_ns(); \
+    } while (0)
+#else
+#define RGBID_STAMP(role_ok, k) \
+    do {                        \
+    } while (0)
+#endif
+#define STAMP_C(k) RGBID_STAMP(blockIdx.x == 0, k)
+#define STAMP_H(k) RGBID_STAMP((int)blockIdx.x == kLevelCL, k)
+
 namespace cg = cooperative_groups;
 
 namespace rgbid {
@@ -600,10 +623,12 @@ __global__ void __launch_bounds__(kRobustNT, 1) split_kernel(SplitArgs a) {
             if (git == n_total - 1) pdl_trigger();
             // ---- the previous step: the pending partials of the preceding launch, or the
             //      helpers' partials of the previous iteration (of this level or the last)
+            STAMP_C(0);
             if (git > 0 && !cta_wait(st, &mb->arrived, (unsigned)a.n_helpers * (unsigned)git, &go[0])) {
                 broken = true;
                 break;
             }
+            STAMP_C(1);
             const unsigned int nb = git == 0 ? nb0 : (unsigned)a.n_helpers;
             if (nb) {
                 // every CTA of the cluster sums all nb partials itself in one fixed order
@@ -629,6 +654,7 @@ __global__ void __launch_bounds__(kRobustNT, 1) split_kernel(SplitArgs a) {
                     level_solve_update<PREC>(tot, a.min_valid, T_sh, &sh_wp, xi_f, d_f, rho_d, xi_d, &ok_flag, sh_cnt);
                 __syncthreads();
             }
+            STAMP_C(2);
             // ---- publish this iteration's pose to the helpers: one thread stores the pose
             //      and then releases the flag, so the release orders the pose before it
             if (rank == 0 && tid == 0) {
@@ -638,6 +664,7 @@ __global__ void __launch_bounds__(kRobustNT, 1) split_kernel(SplitArgs a) {
                 st_release_u32(&mb->pose_flag, (unsigned)git + 1u);
             }
             const WarpPose wp = sh_wp;
+            STAMP_C(3);
 
             // ---- systematic sample residuals at this pose (NaN = masked out)
             float rs[2][MAXS];
@@ -675,6 +702,7 @@ __global__ void __launch_bounds__(kRobustNT, 1) split_kernel(SplitArgs a) {
                 }
             }
 
+            STAMP_C(4);
             // ---- counts and mean square -> sigma0 (mu0 = 0)
             {
                 float v4[4] = {0.f, 0.f, 0.f, 0.f};
@@ -701,6 +729,7 @@ __global__ void __launch_bounds__(kRobustNT, 1) split_kernel(SplitArgs a) {
                 sig[c] = ms > 0.f ? ms * rsqrtf(ms) : 0.f;
                 live[c] = n[c] > 0.f && sig[c] >= 1e-12f;
             }
+            STAMP_C(5);
             // ---- (mu, sigma) fixed point at nu0 with lagged weights
             for (int si = 0; si < a.scale_iters; ++si) {
                 if (!live[0] && !live[1]) break;
@@ -739,6 +768,7 @@ __global__ void __launch_bounds__(kRobustNT, 1) split_kernel(SplitArgs a) {
 #pragma unroll
             for (int c = 0; c < 2; ++c) ok[c] = n[c] > 0.f && sig[c] >= 1e-12f;
 
+            STAMP_C(6);
             // ---- nu: the Chebyshev power sums gathered to CTA 0, which bisects
             float nu[2] = {nu0, nu0};
             const bool do_nu = a.estimate_nu && (ok[0] || ok[1]);
@@ -791,6 +821,7 @@ __global__ void __launch_bounds__(kRobustNT, 1) split_kernel(SplitArgs a) {
                 for (int i = 2 * kChebVals; i < 96; ++i) v[i] = 0.f;
                 R.template run<96, 2 * kChebVals, true>(v);   // only CTA 0 bisects
             }
+            STAMP_C(7);
             if (rank == 0) {
                 if (do_nu && tid < 64) {
                     const int c = tid >> 5;
@@ -821,6 +852,7 @@ __global__ void __launch_bounds__(kRobustNT, 1) split_kernel(SplitArgs a) {
                         __stcg(reinterpret_cast<int*>(&mb->rob) + q, src[q]);
                     // the same thread releases the flag: the release orders the stores above
                     st_release_u32(&mb->rob_flag, (unsigned)git + 1u);
+                    STAMP_C(8);
                 }
             }
         }
@@ -856,18 +888,20 @@ __global__ void __launch_bounds__(kRobustNT, 1) split_kernel(SplitArgs a) {
           if (n_it <= 0) continue;
           const SplitLevel& L = a.lv[l];
           const int ntiles = L.tiles_x * L.tiles_y;
+          const int mt = min(a.max_tiles, (ntiles + a.n_helpers - 1) / a.n_helpers);   // this level's tiles per CTA
           for (int it = 0; it < n_it; ++it, ++git) {
             if (git == n_total - 1) pdl_trigger();
             if (!cta_wait(st, &mb->pose_flag, (unsigned)git + 1u, &go[1])) {
                 broken = true;
                 break;
             }
+            STAMP_H(9);
             if (tid < 16) reinterpret_cast<float*>(&sh_wp)[tid] = __ldcg(reinterpret_cast<const float*>(&mb->wp) + tid);
             __syncthreads();
             const WarpPose wp = sh_wp;
             // ---- the terms of every pixel of this CTA's tiles at the published pose
 #pragma unroll 1
-            for (int j0 = 0; j0 < a.max_tiles; j0 += G) {
+            for (int j0 = 0; j0 < mt; j0 += G) {
                 PxA sa[G];
                 PxW sw[G];
                 PxB sb[G];
@@ -878,7 +912,7 @@ __global__ void __launch_bounds__(kRobustNT, 1) split_kernel(SplitArgs a) {
                     pu[g] = 0;
                     pv[g] = 0;
                     const int t = hc + (j0 + g) * a.n_helpers;
-                    if (j0 + g < a.max_tiles && t < ntiles) {
+                    if (j0 + g < mt && t < ntiles) {
                         const int ty = t / L.tiles_x, tx = t - ty * L.tiles_x;
                         const int u = tx * kSplitTileW + lane, v = ty * kSplitTileH + warp;
                         if (u < L.A.w && v < L.A.h) {
@@ -894,7 +928,7 @@ __global__ void __launch_bounds__(kRobustNT, 1) split_kernel(SplitArgs a) {
                 for (int g = 0; g < G; ++g) stage_b<PREC>(L.B, sw[g], sb[g]);
 #pragma unroll
                 for (int g = 0; g < G; ++g) {
-                    if (j0 + g >= a.max_tiles) continue;
+                    if (j0 + g >= mt) continue;
                     PixelTerms o;
                     finish<true>(L.A, wp, sa[g], sw[g], sb[g], o);
                     float* const T = Tm + (j0 + g) * (kSplitTerms * NT);
@@ -911,11 +945,13 @@ __global__ void __launch_bounds__(kRobustNT, 1) split_kernel(SplitArgs a) {
                     }
                 }
             }
+            STAMP_H(10);
             // ---- weighted normal equations once the parameters are published
             if (!cta_wait(st, &mb->rob_flag, (unsigned)git + 1u, &go[2])) {
                 broken = true;
                 break;
             }
+            STAMP_H(11);
             if (tid < (int)(sizeof(RobustParams) / 4))
                 reinterpret_cast<int*>(&sh_rob)[tid] = __ldcg(reinterpret_cast<const int*>(&mb->rob) + tid);
             __syncthreads();
@@ -924,7 +960,7 @@ __global__ void __launch_bounds__(kRobustNT, 1) split_kernel(SplitArgs a) {
 #pragma unroll
             for (int i = 0; i < kSlots; ++i) acc[i] = 0.f;
 #pragma unroll 1
-            for (int j = 0; j < a.max_tiles; ++j) {
+            for (int j = 0; j < mt; ++j) {
                 const float* const T = Tm + j * (kSplitTerms * NT);
                 const float rI = T[0], rW = T[NT];
                 if (rI == rI) {
@@ -956,6 +992,7 @@ __global__ void __launch_bounds__(kRobustNT, 1) split_kernel(SplitArgs a) {
                 __threadfence();
                 __syncwarp();
                 if (lane == 0) atomicAdd(&mb->arrived, 1u);
+                if (lane == 0) STAMP_H(12);
             }
           }
         }
@@ -1213,3 +1250,20 @@ namespace rgbid {
 // out-of-plane gathers counted by this translation unit's kernels (bounds-checked builds)
 unsigned int oob_count_level() { return oob_count_this_unit(); }
 }  // namespace rgbid
+
+extern "C" int rgbid_debug_phase_stamps(long long* out, int n) {
+#ifdef RGBID_PHASE_STAMPS
+    constexpr int kN = RGBID_MAX_LEVELS * 16 * 16;
+    if (!out || n < kN) return RGBID_ERR_INVALID_ARG;
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpyFromSymbol(out, g_phase, sizeof(long long) * kN) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return RGBID_ERR_CUDA;
+    }
+    return RGBID_OK;
+#else
+    (void)out;
+    (void)n;
+    return RGBID_ERR_UNSUPPORTED;
+#endif
+}

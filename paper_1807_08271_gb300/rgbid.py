@@ -142,6 +142,7 @@ SIGNATURES = [
     ("rgbid_net_workspace_bytes", c_size_t, [c_int]),
     ("rgbid_net_wait_timeouts", ctypes.c_uint, []),
     ("rgbid_debug_bounds_violations", c_int, [POINTER(ctypes.c_ulonglong)]),
+    ("rgbid_debug_phase_stamps", c_int, [POINTER(ctypes.c_longlong), c_int]),
     ("rgbid_net_init", c_int, [c_void_p, ctypes.c_ulonglong, c_void_p]),
     ("rgbid_net_inputs", c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p]),
     ("rgbid_net_forward", c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_size_t, c_void_p]),
@@ -162,11 +163,13 @@ class RgbidError(RuntimeError):
 
 def lib():
     """Load (building first if needed) the in-tree librgbid.so, or with the environment
-    variable RGBID_LIBRARY=checked the bounds-checked test build librgbid_checked.so."""
+    variable RGBID_LIBRARY=checked the bounds-checked test build librgbid_checked.so
+    (RGBID_LIBRARY=phases: the phase-stamped diagnostic build librgbid_phases.so)."""
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.build(checked=os.environ.get("RGBID_LIBRARY") == "checked")
+            variant = os.environ.get("RGBID_LIBRARY")
+            path = _build.build(checked=variant == "checked", phases=variant == "phases")
             L = ctypes.CDLL(path)
             for name, res, args in SIGNATURES:
                 f = getattr(L, name)
@@ -485,6 +488,18 @@ def rgbid_debug_bounds_violations() -> int | None:
         return None
     _check("rgbid_debug_bounds_violations", rc)
     return int(n.value)
+
+
+def rgbid_debug_phase_stamps():
+    """The split kernel's phase stamps of the phase-stamped build as a [levels, 16, 16]
+    int64 array (ns), or None for a build without them."""
+    n = MAX_LEVELS * 16 * 16
+    buf = (ctypes.c_longlong * n)()
+    rc = lib().rgbid_debug_phase_stamps(buf, n)
+    if rc == ERR_UNSUPPORTED:
+        return None
+    _check("rgbid_debug_phase_stamps", rc)
+    return np.array(buf, dtype=np.int64).reshape(MAX_LEVELS, 16, 16)
 
 
 def rgbid_net_wait_timeouts() -> int:
