@@ -452,8 +452,11 @@ __global__ void __launch_bounds__(kRobustNT, 1) level_kernel(LevelArgs a) {
 }
 
 // ---------------------------------------------------------------- split level kernel
-// A level whose systematic sample is a strict subset of its pixels (640x480 and
-// 320x240 of the sequence).  One launch runs all of the level's iterations:
+// Levels with more than two pixels per thread of the cluster (160x120, 320x240 and
+// 640x480 of the sequence; the sample is every pixel at 160x120, a strict subset
+// above).  One launch runs consecutive such levels in turn, coarse to fine, each for
+// all of its iterations (a level's last step is taken at the next level's first
+// iteration, like any other step):
 //   cluster 0 (16 CTAs)  reduces the previous step's partials, solves and updates the
 //                        pose in every CTA, publishes the pose, evaluates the sample
 //                        residuals at it, estimates (mu, sigma, nu) as the robust-scale
@@ -466,7 +469,7 @@ __global__ void __launch_bounds__(kRobustNT, 1) level_kernel(LevelArgs a) {
 // following it.  The roles hand over through the workspace's mailbox: a release store
 // of a counter after the data, an acquire load before reading it, every wait bounded.
 // The launch is cooperative, so every CTA is resident while others wait on it.  The
-// level's last step stays pending (one partial per helper), as a sweep leaves it.
+// last level's last step stays pending (one partial per helper), as a sweep leaves it.
 
 __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
     unsigned int v;
