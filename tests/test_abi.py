@@ -87,6 +87,24 @@ def test_host_side_calls_without_a_gpu(binding):
     assert code == b.ERR_INVALID_ARG
 
 
+def test_the_product_build_has_no_diagnostic_counters(binding):
+    """The bounds-checked and phase-stamped builds are separate libraries; the product
+    library answers their queries with RGBID_ERR_UNSUPPORTED without touching a device."""
+    import os
+    if os.environ.get("RGBID_LIBRARY") in ("checked", "phases"):
+        pytest.skip("running against a diagnostic build")
+    L = binding.lib()
+    n = ctypes.c_ulonglong(7)
+    assert L.rgbid_debug_bounds_violations(ctypes.byref(n)) == binding.ERR_UNSUPPORTED and n.value == 0
+    assert L.rgbid_debug_bounds_violations(None) == binding.ERR_INVALID_ARG
+    buf = (ctypes.c_longlong * (binding.MAX_LEVELS * 256))()
+    assert L.rgbid_debug_phase_stamps(buf, len(buf)) == binding.ERR_UNSUPPORTED
+    assert binding.rgbid_debug_bounds_violations() is None and binding.rgbid_debug_phase_stamps() is None
+    from paper_1807_08271_gb300 import build
+    with pytest.raises(ValueError):
+        build.build(checked=True, phases=True)
+
+
 def test_batch_struct_layouts_match_header(binding, tmp_path):
     src = tmp_path / "abi_batch.c"
     src.write_text(f'''#include <stdio.h>
