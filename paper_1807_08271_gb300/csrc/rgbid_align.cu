@@ -835,10 +835,10 @@ static cudaError_t launch_robust_cl(const RobustArgs& ra, cudaStream_t stream) {
 // The answer is a fixed property of the device, cached per device ordinal.
 template <int PREC>
 static cudaError_t launch_robust(const RobustArgs& ra, cudaStream_t stream) {
-    static int cached[64];     // 0 = unknown, 8 or 16
+    static std::atomic<int> cached[64];   // 0 = unknown, 8 or 16
     int dev = 0;
     cudaGetDevice(&dev);
-    int cl = (dev >= 0 && dev < 64) ? cached[dev] : 0;
+    int cl = (dev >= 0 && dev < 64) ? cached[dev].load(std::memory_order_relaxed) : 0;
     if (cl == 0) {
         cl = 8;
         if (cudaFuncSetAttribute(robust_kernel<PREC, 16, false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
@@ -859,7 +859,7 @@ static cudaError_t launch_robust(const RobustArgs& ra, cudaStream_t stream) {
                 cl = 16;
         }
         (void)cudaGetLastError();
-        if (dev >= 0 && dev < 64) cached[dev] = cl;
+        if (dev >= 0 && dev < 64) cached[dev].store(cl, std::memory_order_relaxed);
     }
     if (ra.full_level > 0)
         return cl == 16 ? launch_robust_cl<PREC, 16, true>(ra, stream) : launch_robust_cl<PREC, 8, true>(ra, stream);
